@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Throughput of the hybrid LB / Beris-Edwards step on GB300.
+
+Workload: the spherical nematic droplet, 256^3 D3Q19 lattice, R = 48,
+director along z, noise 1e-4, gamma = 2.705, FP32 (populations as deviations
+from w_i rho0), synthetic seeded input.  One "step" is one full time step
+(force, LB collide-and-stream, predictor-corrector for Q) of the whole
+lattice.  Metric: MLUPS (million lattice-cell updates per second).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With N > 1 (launched by torchrun) every rank advances its own lattice
+(independent replicas, weak scaling); value = all ranks' updates / max time.
+Prints one JSON line on rank 0.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("MLUPS of fused LB+Beris-Edwards step, % of HBM roofline; "
+          "adjoint/forward time")
+UNIT = "MLUPS"
+WORD = 4  # FP32
+Q3 = 19
+
+# Algorithmic bytes per lattice update (LUP), FP32:
+#   whole step     : read + write of the 19 populations and 5 Q components
+#   fused_lb kernel: read + write of the populations, read of Q
+#   fused_be kernel: read + write of Q
+ALG_BYTES_STEP = 2 * (Q3 + 5) * WORD          # 192 B
+ALG_BYTES = {"fused_lb": (2 * Q3 + 5) * WORD,  # 172 B
+             "fused_be": 2 * 5 * WORD}         # 40 B
+
+# DRAM traffic per LUP of each kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, divided by the cells of the
+# captured launch), keyed by the SHA-256 of the kernel sources it was taken
+# on; reported as null once those sources change.
+NCU_TRAFFIC = {}
+
+KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",
+                  "paper_1907_13415_gb300/csrc/physics.cuh",
+                  "paper_1907_13415_gb300/csrc/step_unfused.cuh",
+                  "paper_1907_13415_gb300/csrc/lattice.cuh",
+                  "paper_1907_13415_gb300/csrc/common.cuh"]
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# -- clocks -----------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev),
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -- distributed helpers -------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value, ws):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# -- the oracle as CPU baseline / reference arm ------------------------------
+
+def oracle_sample_rate(w, steps, shape=None):
+    """Time the FP64 CPU oracle on a bounded sample of the workload.  Returns
+    (MLUPS, threads, description)."""
+    import oracle
+    from paper_1907_13415_gb300 import workloads as wl
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    orc = oracle.get()
+    ws = w if shape is None else wl.scaled(w, shape)
+    Q = ws.initial_q5()
+    f = orc.init_equilibrium(ws.lattice, ws.shape)
+    p = wl.param_vector(ws.params)
+    t0 = time.perf_counter()
+    orc.step(ws.lattice, p, f, Q, steps)
+    dt = time.perf_counter() - t0
+    nz, ny, nx = ws.shape
+    desc = (f"{steps} step(s) of the oracle on a {nx}x{ny}x{nz} D3Q19 lattice "
+            f"with the droplet recipe, FP64, OpenMP")
+    return nx * ny * nz * steps / dt / 1e6, int(os.environ["OMP_NUM_THREADS"]), desc
+
+
+def mem_available_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 0.0
+
+
+def baseline_shape(w):
+    """Full lattice when the host has room for the oracle's ~80 doubles per
+    cell (plus copies), else a z slab of it."""
+    nz, ny, nx = w.shape
+    need_gb = 110 * 8 * nx * ny * nz / 1e9
+    if mem_available_gb() > 2 * need_gb:
+        return w.shape
+    return (max(8, nz // 8), ny, nx)
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    # one reference step: one oracle step on a z slab of the workload, sized
+    # so that warm-up + timed steps end within a few minutes
+    nz, ny, nx = w.shape
+    shape = (8, ny, nx)
+    from paper_1907_13415_gb300 import workloads as wl
+    import oracle
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    orc = oracle.get()
+    ws_ = wl.scaled(w, shape)
+    Q = ws_.initial_q5()
+    f = orc.init_equilibrium(ws_.lattice, ws_.shape)
+    p = wl.param_vector(ws_.params)
+    for _ in range(args.warmup):
+        f, Q = orc.step(ws_.lattice, p, f, Q, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, Q = orc.step(ws_.lattice, p, f, Q, 1)
+    dt = time.perf_counter() - t0
+    cells = shape[0] * shape[1] * shape[2]
+    value = cells * args.steps / dt / 1e6
+    sample = (f"{args.steps} oracle steps of a {nx}x{ny}x{shape[0]} slab of the "
+              f"256^3 droplet lattice (FP64 CPU, OpenMP)")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "lattice": "D3Q19",
+                   "shape": [nx, ny, shape[0]], "note": "CPU oracle sample"},
+        "cpu_baseline": {"value": value, "unit": UNIT,
+                         "cores": int(os.environ["OMP_NUM_THREADS"]),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# -- our arm -------------------------------------------------------------------
+
+def run_ours(args, w):
+    import torch
+    from paper_1907_13415_gb300 import nlc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                         stream=stream.cuda_stream)
+    Q0 = w.initial_q5()
+    sim.set_fields(Q0)
+    cells = w.n_cells
+
+    # warm-up
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, per-kernel events recorded by the library
+    nlc.nlc_set_timing(sim.ctx, True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sim.step(1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    kt = nlc.nlc_get_timing(sim.ctx)
+    nlc.nlc_set_timing(sim.ctx, False)
+    clocks = clk.summary()
+    t_max = max_over_ranks(elapsed_ms, ws)
+    value = cells * args.steps * ws / (t_max * 1e-3) / 1e6
+    launches = sum(n for _, n in kt.values())
+
+    # roofline of the dominant kernel
+    peak, peak_src = hbm_peak()
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms, dom_n = kt[dom]
+    per_launch_s = dom_ms / max(dom_n, 1) * 1e-3
+    alg = ALG_BYTES.get(dom, ALG_BYTES_STEP) * cells
+    achieved = alg / per_launch_s / 1e9
+    tr = NCU_TRAFFIC.get(dom)
+    traffic = (tr[0] * cells if tr and tr[1] == source_hash() else None)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "kernel": dom, "peak_source": peak_src,
+                "alg_bytes_per_lup": ALG_BYTES.get(dom, ALG_BYTES_STEP)}
+    step_s = t_max / args.steps * 1e-3
+    step_roofline = {"alg_bytes_per_lup": ALG_BYTES_STEP,
+                     "achieved": ALG_BYTES_STEP * cells / step_s / 1e9,
+                     "frac": ALG_BYTES_STEP * cells / step_s / 1e9 / peak}
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                   "share": v[0] / max(sum(x[0] for x in kt.values()), 1e-30)}
+               for k, v in kt.items() if v[1]}
+
+    # end to end through the public API with host buffers: upload Q from
+    # pinned host memory, one step, observables back to the host
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(Q0.shape, dtype=torch.float64, pin_memory=True)
+        pinned.numpy()[...] = Q0
+        qhost = pinned.numpy()
+        for _ in range(2):
+            sim.set_fields(qhost)
+            sim.step(1)
+            sim.observables()
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.set_fields(qhost)
+            sim.step(1)
+            sim.observables()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+        e2e = {"value": cells * args.e2e_steps * ws / e2e_s / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(Q0.nbytes),
+               "d2h_bytes_per_step": int(np.dtype(np.float64).itemsize * 8 + 32),
+               "steps": args.e2e_steps,
+               "what": "nlc_set_fields(Q from pinned host) + nlc_step(1) + "
+                       "nlc_observables() per step"}
+    sim.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        shape = baseline_shape(w)
+        rate, cores, desc = oracle_sample_rate(w, 1, shape)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        nz, ny, nx = w.shape
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "lattice": "D3Q19",
+                       "shape": [nx, ny, nz], "radius": w.size,
+                       "gamma": w.params["gamma"],
+                       "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2 (3.2 GB of state)"},
+            "roofline": roofline, "step_roofline": step_roofline,
+            "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks,
+            "kernel_source": source_hash(),
+        }
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    # at least three untimed warm-up steps (reported as the count used)
+    args.warmup = max(args.warmup, 3)
+    from paper_1907_13415_gb300 import workloads as wl
+    w = wl.sphere_256()
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

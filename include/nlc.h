@@ -1,0 +1,192 @@
+/*
+ * nlc.h -- C ABI of libnlc: one GPU time step of the hybrid lattice-Boltzmann
+ * (LB) / finite-difference Beris-Edwards method for nematic liquid crystals of
+ * Coelho, Araujo & Telo da Gama, "Lattice-Boltzmann simulation of free
+ * nematic-isotropic interfaces" (arxiv 1907.13415).
+ *
+ * The problem statement the calls follow (Sec. 1.1, Sec. 1.2, Sec. 2):
+ *   - a periodic lattice (Sec. 2: periodic boundaries in every direction),
+ *     D2Q9 (nz = 1) or D3Q19, lattice units (dx = dt = 1);
+ *   - parameters A0, K, gamma (Eq. 2), Gamma, xi (Eq. 1), the LB relaxation
+ *     time tau (Sec. 1.2.1) and the reference density rho0;
+ *   - initial fields Q (the order-parameter tensor of Eq. 1), rho and u
+ *     (Sec. 2: rho = 1, u = 0 by default);
+ *   - time stepping; read-back of Q, rho, u and of observables (scalar order
+ *     parameter profile, interface position, droplet radius, maximum speed).
+ *
+ * One call of nlc_step(ctx, 1) performs, on the GPU, per lattice cell:
+ *   H from Eq. 3, the stress of Eq. 5 (without P0) and its central-difference
+ *   divergence F (Sec. 1.2.1), rho and u from Eq. 6, BGK collision with the
+ *   source term S_i of Sec. 1.2.1 and streaming, and the predictor-corrector
+ *   update of Q by Eq. 1 with central differences (Sec. 1.2.2, steps 1-5),
+ *   using the velocity of Eq. 6 held fixed over both evaluations.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an nlc_status; nothing else crosses the ABI.  On
+ *     failure nlc_last_error(ctx) gives a message owned by the context.
+ *   - The caller owns every host array passed in or out; the library copies
+ *     what it needs before returning.  The context owns all device memory.
+ *   - Work is queued on the CUDA stream given to nlc_create (NULL = the legacy
+ *     default stream).  nlc_step does not synchronise; nlc_set_fields,
+ *     nlc_get_fields, nlc_get_populations and nlc_observables do.
+ *   - Host field arrays are float64, structure of arrays, x fastest:
+ *       Q5  [5][nz][ny][nx]   components (xx, xy, xz, yy, yz); Qzz = -Qxx-Qyy
+ *       rho [nz][ny][nx]
+ *       u   [3][nz][ny][nx]   (u_z is zero on D2Q9)
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef NLC_H
+#define NLC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NLC_API __attribute__((visibility("default")))
+#else
+#define NLC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NLC_OK = 0,
+  NLC_EINVAL = -1,      /* bad argument (sizes, parameters, null pointer)  */
+  NLC_ENOMEM = -2,      /* device or host allocation failed                */
+  NLC_ECUDA = -3,       /* a CUDA call or kernel launch failed             */
+  NLC_EUNSTABLE = -4,   /* non-finite values found in the state            */
+  NLC_ETIMEOUT = -5,    /* a bounded device wait ran out                   */
+  NLC_ECORRUPT = -6,    /* a saved state failed its checksum               */
+  NLC_EUNSUPPORTED = -7 /* valid request this build does not implement     */
+} nlc_status;
+
+enum { NLC_D2Q9 = 0, NLC_D3Q19 = 1 };
+
+/* Arithmetic and storage precision of the step.  Observables are always
+ * accumulated in FP64. */
+enum {
+  NLC_FP64 = 0, /* everything in double                                     */
+  NLC_FP32 = 1  /* populations (as deviations from w_i rho0) and Q stored
+                   and computed in float                                    */
+};
+
+/* Kernel schedule of one step.  Both compute the same step. */
+enum {
+  NLC_SCHED_FUSED = 0,  /* two tiled kernels per step (default)            */
+  NLC_SCHED_UNFUSED = 1 /* four one-cell-per-thread kernels per step        */
+};
+
+typedef struct {
+  int32_t nx, ny, nz; /* lattice extent; nz = 1 for D2Q9                    */
+  int32_t lattice;    /* NLC_D2Q9 | NLC_D3Q19                               */
+  int32_t precision;  /* NLC_FP64 | NLC_FP32                                */
+} nlc_grid;
+
+/* Eq. 2 (A0, K, gamma), Eq. 1 (Gamma, xi), Sec. 1.2.1 (tau), reference
+ * density rho0 (Sec. 2 uses rho = 1).  tau must exceed 1/2. */
+typedef struct {
+  double A0, K, gamma, Gamma, xi, tau, rho0;
+} nlc_params;
+
+/* Observables of the current state (all accumulated in FP64).
+ *   mass        sum of rho
+ *   mom         sum of rho u, with u of Eq. 6
+ *   s_area      sum of S / s_ref, S = sqrt(3/2 Tr Q^2), s_ref = 1/3 (the
+ *               nematic order at coexistence, Sec. 2.1)
+ *   radius      sqrt(s_area/pi) on a single plane, (3 s_area/(4 pi))^(1/3)
+ *               in 3D (droplet radius, Sec. 2.2)
+ *   x_iface     first x (scanning up from 0) where the y,z-mean of S falls
+ *               through s_ref/2, linearly interpolated; -1 if none (flat
+ *               interface position, Sec. 2.1)
+ *   max_u       largest |u| (spurious-velocity measure, Sec. 2.2)
+ *   free_energy Eq. 2 summed over cells, gradient term by forward differences
+ *   nonfinite   count of non-finite stored values (populations and Q)
+ *   step        time steps taken since the last nlc_set_fields             */
+typedef struct {
+  double mass, mom[3], s_area, radius, x_iface, max_u, free_energy;
+  int64_t nonfinite;
+  int64_t step;
+} nlc_obs;
+
+typedef struct nlc_ctx nlc_ctx;
+
+/* Creates a context for one lattice on the current CUDA device and
+ * allocates its device state (two copies of the q populations and of the 5 Q
+ * components, plus work arrays).  The state starts at Q = 0, rho = rho0,
+ * u = 0.  stream: a cudaStream_t (may be NULL).  *out is set on success.
+ * Errors: NLC_EINVAL (bad sizes or parameters, D2Q9 with nz != 1),
+ * NLC_ENOMEM, NLC_ECUDA. */
+NLC_API nlc_status nlc_create(const nlc_grid* grid, const nlc_params* params,
+                      void* stream, nlc_ctx** out);
+
+/* Selects the kernel schedule (NLC_SCHED_*) for later nlc_step calls. */
+NLC_API nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule);
+
+/* Replaces the state with Q5, rho and u (host float64, layouts above).  The
+ * populations are set to the equilibrium f_i^eq(rho, u) of Sec. 1.2.1.
+ * rho may be NULL (rho0 everywhere) and u may be NULL (at rest).  The step
+ * counter restarts at 0.  inst must be 0 for a single-lattice context.
+ * Synchronises the stream.  Errors: NLC_EINVAL (null Q5, inst out of range),
+ * NLC_EUNSTABLE (a non-finite input value; the state is then undefined),
+ * NLC_ECUDA. */
+NLC_API nlc_status nlc_set_fields(nlc_ctx* ctx, int32_t inst, const double* Q5,
+                          const double* rho, const double* u);
+
+/* Copies the current Q, rho and u (u of Eq. 6, including F/2) to host
+ * arrays; any output may be NULL.  Synchronises the stream. */
+NLC_API nlc_status nlc_get_fields(nlc_ctx* ctx, int32_t inst, double* Q5,
+                          double* rho, double* u);
+
+/* Copies the pre-collision populations f_i(x, t) of the current time to a
+ * host array f[q][nz][ny][nx], in the order nlc_lattice_velocities gives.
+ * Synchronises the stream. */
+NLC_API nlc_status nlc_get_populations(nlc_ctx* ctx, int32_t inst, double* f);
+
+/* Advances every lattice of the context by n time steps (n >= 0).  Queued
+ * on the context's stream; returns launch errors only. */
+NLC_API nlc_status nlc_step(nlc_ctx* ctx, int64_t n);
+
+/* Computes the observables of the current state of instance inst into *out
+ * and, if s_profile is not NULL, the y,z-mean of S for each x (nx values).
+ * Synchronises the stream. */
+NLC_API nlc_status nlc_observables(nlc_ctx* ctx, int32_t inst, nlc_obs* out,
+                           double* s_profile);
+
+/* Per-kernel device timing (CUDA events recorded on the context's stream
+ * around each kernel launch of nlc_step).  enable = 1 clears the log and
+ * starts recording; enable = 0 stops.  Meant for profiling: while enabled,
+ * each step records one extra event per kernel. */
+NLC_API nlc_status nlc_set_timing(nlc_ctx* ctx, int32_t enable);
+
+/* Totals since timing was enabled, per kernel id (0 .. NLC_N_KERNELS-1):
+ * total_ms[k] milliseconds and launches[k] launch counts (arrays of at least
+ * max_kernels entries; either may be NULL).  *n_kernels (may be NULL) gets
+ * NLC_N_KERNELS.  Synchronises the stream. */
+#define NLC_N_KERNELS 6
+NLC_API nlc_status nlc_get_timing(nlc_ctx* ctx, int32_t max_kernels,
+                                  double* total_ms, int64_t* launches,
+                                  int32_t* n_kernels);
+
+/* Name of kernel id k for nlc_get_timing ("?" when out of range). */
+NLC_API const char* nlc_timing_name(int32_t k);
+
+/* Message of the last failed call on ctx (empty if none).  Owned by ctx. */
+NLC_API const char* nlc_last_error(const nlc_ctx* ctx);
+
+/* Frees the context and its device memory.  NULL is allowed. */
+NLC_API void nlc_destroy(nlc_ctx* ctx);
+
+/* Velocity set of a lattice: writes q vectors c[i][3] and weights w[i] (both
+ * may be NULL) and returns q (9 or 19), or -1 for an unknown lattice. */
+NLC_API int32_t nlc_lattice_velocities(int32_t lattice, int32_t* c, double* w);
+
+/* Library version string. */
+NLC_API const char* nlc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLC_H */

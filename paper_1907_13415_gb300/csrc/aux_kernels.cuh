@@ -1,0 +1,218 @@
+// aux_kernels.cuh -- state set-up, read-back and FP64 observables.
+#pragma once
+#include "common.cuh"
+#include "lattice.cuh"
+#include "physics.cuh"
+#include "step_unfused.cuh"
+
+namespace nlc {
+
+// Q from float64 input; populations to the pull-layout image of f^eq(rho, u):
+// the deviation stored at y for direction i is g^eq_i evaluated at y + c_i,
+// so that pulling reproduces f^eq at every cell.  Counts non-finite inputs.
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_set_fields(
+    const double* __restrict__ q_in, const double* __restrict__ rho_in,
+    const double* __restrict__ u_in, T* __restrict__ Q, T* __restrict__ g,
+    Dims d, double rho0, unsigned long long* __restrict__ bad) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!decode(d, idx, x, y, z)) return;
+  int nbad = 0;
+#pragma unroll
+  for (int k = 0; k < 5; k++) {
+    const double v = q_in[k * d.n + idx];
+    nbad += !isfinite(v);
+    Q[k * d.n + idx] = (T)v;
+  }
+  if (rho_in) nbad += !isfinite(rho_in[idx]) || !(rho_in[idx] > 0.0);
+  if (u_in)
+    for (int a = 0; a < 3; a++) nbad += !isfinite(u_in[a * d.n + idx]);
+#pragma unroll
+  for (int i = 0; i < Lat::Q; i++) {
+    const int xs = wrap_add(x, Lat::c(i, 0), d.nx);
+    const int ys = wrap_add(y, Lat::c(i, 1), d.ny);
+    const int zs = Lat::DIM == 3 ? wrap_add(z, Lat::c(i, 2), d.nz) : z;
+    const int64_t src = cell_of(d, xs, ys, zs);
+    const double rho = rho_in ? rho_in[src] : rho0;
+    double u[3] = {0.0, 0.0, 0.0};
+    if (u_in)
+      for (int a = 0; a < Lat::DIM; a++) u[a] = u_in[a * d.n + src];
+    double cu = 0.0, uu = 0.0;
+    for (int a = 0; a < Lat::DIM; a++) {
+      cu += Lat::c(i, a) * u[a];
+      uu += u[a] * u[a];
+    }
+    const double w = Lat::w(i);
+    const double geq = w * ((rho - rho0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+    g[(int64_t)i * d.n + idx] = (T)geq;
+  }
+  if (nbad) atomicAdd(bad, (unsigned long long)nbad);
+}
+
+// rho and u of Eq. 6 (with F/2) at the current time, into float64 arrays
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_moments_out(
+    const T* __restrict__ gin, const T* __restrict__ Pi, Dims d, Par<T> p,
+    double* __restrict__ rho_out, double* __restrict__ u_out) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!decode(d, idx, x, y, z)) return;
+  T F[3], g[Lat::Q], rho, u[3];
+  force_at<T, Lat::DIM>(Pi, d, x, y, z, F);
+  pull<Lat, T>(gin, d, x, y, z, g);
+  moments<Lat, T>(g, F, p, rho, u);
+  rho_out[idx] = (double)rho;
+#pragma unroll
+  for (int a = 0; a < 3; a++) u_out[a * d.n + idx] = (double)u[a];
+}
+
+// pre-collision populations f_i = w_i rho0 + g*_i(x - c_i) as float64
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_populations_out(
+    const T* __restrict__ gin, Dims d, double rho0, double* __restrict__ f) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!decode(d, idx, x, y, z)) return;
+  T g[Lat::Q];
+  pull<Lat, T>(gin, d, x, y, z, g);
+#pragma unroll
+  for (int i = 0; i < Lat::Q; i++)
+    f[(int64_t)i * d.n + idx] = Lat::w(i) * rho0 + (double)g[i];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_to_double(const T* __restrict__ in,
+                                                   double* __restrict__ out,
+                                                   int64_t count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = (double)in[i];
+}
+
+// Observables, pass 1: per-block FP64 partial sums over cells.
+// partial[block][OBS_SLOTS]: mass, mom x/y/z, sum S/s_ref, free energy,
+// non-finite count, max |u|.
+constexpr int OBS_SLOTS = 8;
+
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_obs_partial(
+    const T* __restrict__ Q, const T* __restrict__ gpost,
+    const double* __restrict__ rho, const double* __restrict__ u, Dims d,
+    Par<T> p, double s_ref, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0};
+  double umax = 0.0;
+  const double A0 = (double)p.A0, K = (double)p.K, gam = (double)p.gamma;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < d.n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    decode(d, idx, x, y, z);
+    const double r = rho[idx];
+    double uu = 0.0;
+    acc[0] += r;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const double ua = u[a * d.n + idx];
+      acc[1 + a] += r * ua;
+      uu += ua * ua;
+    }
+    umax = fmax(umax, sqrt(uu));
+    double q[5];
+    int nbad = 0;
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+      q[k] = (double)Q[k * d.n + idx];
+      nbad += !isfinite(q[k]);
+    }
+#pragma unroll
+    for (int i = 0; i < Lat::Q; i++) nbad += !isfinite((double)gpost[(int64_t)i * d.n + idx]);
+    const double qzz = -q[0] - q[3];
+    const double tr2 = q[0] * q[0] + q[3] * q[3] + qzz * qzz +
+                       2.0 * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
+    // Tr Q^3 = det-free form via Q_ab Q_bc Q_ca
+    const double Qm[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], qzz}};
+    double tr3 = 0.0;
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++)
+        for (int c = 0; c < 3; c++) tr3 += Qm[a][b] * Qm[b][c] * Qm[c][a];
+    double e = A0 / 2.0 * (1.0 - gam / 3.0) * tr2 - A0 * gam / 3.0 * tr3 +
+               A0 * gam / 4.0 * tr2 * tr2;
+    // forward-difference gradient energy K/2 sum_g |Q(x+e_g) - Q(x)|^2
+    const int64_t nbs[3] = {cell_of(d, wrap_inc(x, d.nx), y, z),
+                            cell_of(d, x, wrap_inc(y, d.ny), z),
+                            cell_of(d, x, y, wrap_inc(z, d.nz))};
+    for (int gdir = 0; gdir < 3; gdir++) {
+      double dv[5];
+      for (int k = 0; k < 5; k++) dv[k] = (double)Q[k * d.n + nbs[gdir]] - q[k];
+      const double dzz = -dv[0] - dv[3];
+      e += K / 2.0 * (dv[0] * dv[0] + dv[3] * dv[3] + dzz * dzz +
+                      2.0 * (dv[1] * dv[1] + dv[2] * dv[2] + dv[4] * dv[4]));
+    }
+    acc[4] += sqrt(1.5 * tr2) / s_ref;
+    acc[5] += e;
+    acc[6] += (double)nbad;
+  }
+  double tot[OBS_SLOTS];
+  for (int k = 0; k < OBS_SLOTS - 1; k++) tot[k] = block_sum(acc[k], sh);
+  tot[OBS_SLOTS - 1] = block_max(umax, sh);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < OBS_SLOTS; k++) partial[blockIdx.x * OBS_SLOTS + k] = tot[k];
+}
+
+namespace {  // non-template kernels: one private copy per translation unit
+
+// pass 2: one block sums the partials in a fixed order
+__global__ void __launch_bounds__(256) k_obs_final(const double* __restrict__ partial,
+                                                   int nblocks,
+                                                   double* __restrict__ out) {
+  __shared__ double sh[32];
+  for (int k = 0; k < OBS_SLOTS; k++) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+      const double pv = partial[b * OBS_SLOTS + k];
+      v = (k == OBS_SLOTS - 1) ? fmax(v, pv) : v + pv;
+    }
+    const double t = (k == OBS_SLOTS - 1) ? block_max(v, sh) : block_sum(v, sh);
+    if (threadIdx.x == 0) out[k] = t;
+  }
+}
+
+}  // namespace
+
+// y,z-mean of S per x: partial sums over row chunks, then a fixed-order sum
+template <class T>
+__global__ void __launch_bounds__(128) k_profile_partial(
+    const T* __restrict__ Q, Dims d, int rows_per_chunk,
+    double* __restrict__ partial) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int chunk = blockIdx.y;
+  if (x >= d.nx) return;
+  const int64_t rows = (int64_t)d.ny * d.nz;
+  const int64_t r0 = (int64_t)chunk * rows_per_chunk;
+  const int64_t r1 = r0 + rows_per_chunk < rows ? r0 + rows_per_chunk : rows;
+  double s = 0.0;
+  for (int64_t r = r0; r < r1; r++) {
+    const int64_t c = r * d.nx + x;
+    double q[5];
+    for (int k = 0; k < 5; k++) q[k] = (double)Q[k * d.n + c];
+    const double qzz = -q[0] - q[3];
+    const double tr2 = q[0] * q[0] + q[3] * q[3] + qzz * qzz +
+                       2.0 * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
+    s += sqrt(1.5 * tr2);
+  }
+  partial[(int64_t)chunk * d.nx + x] = s;
+}
+
+namespace {
+__global__ void __launch_bounds__(128) k_profile_final(
+    const double* __restrict__ partial, int nchunks, Dims d,
+    double* __restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.nx) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; c++) s += partial[(int64_t)c * d.nx + x];
+  out[x] = s / ((double)d.ny * (double)d.nz);
+}
+}  // namespace
+
+}  // namespace nlc

@@ -1,0 +1,95 @@
+// engine.h -- host-side interface between the C ABI and the templated
+// per-lattice, per-precision engines.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/nlc.h"
+
+namespace nlc {
+
+// kernel ids of the timing log (names in nlc_timing_name)
+enum KernelId { KID_FUSED_LB = 0, KID_FUSED_BE, KID_STRESS, KID_LB, KID_PREDICT,
+                KID_CORRECT, KID_COUNT };
+
+// CUDA events recorded around kernel launches while timing is on.
+class KernelTimer {
+ public:
+  ~KernelTimer() {
+    for (cudaEvent_t e : pool_) cudaEventDestroy(e);
+  }
+  bool on = false;
+  void reset() {
+    used_ = 0;
+    spans_.clear();
+  }
+  // records an event on st and returns its index (or -1 when out of events)
+  int mark(cudaStream_t st) {
+    if (used_ == pool_.size()) {
+      if (pool_.size() >= kMaxEvents) return -1;
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      pool_.push_back(e);
+    }
+    if (cudaEventRecord(pool_[used_], st) != cudaSuccess) return -1;
+    return (int)used_++;
+  }
+  void span(int kid, int a, int b) {
+    if (a >= 0 && b >= 0) spans_.push_back({kid, a, b});
+  }
+  cudaError_t totals(double* ms, int64_t* launches) {
+    for (int k = 0; k < KID_COUNT; k++) {
+      ms[k] = 0.0;
+      launches[k] = 0;
+    }
+    for (const Span& s : spans_) {
+      float t = 0.f;
+      cudaError_t e = cudaEventSynchronize(pool_[s.b]);
+      if (e != cudaSuccess) return e;
+      e = cudaEventElapsedTime(&t, pool_[s.a], pool_[s.b]);
+      if (e != cudaSuccess) return e;
+      ms[s.kid] += t;
+      launches[s.kid] += 1;
+    }
+    return cudaSuccess;
+  }
+
+ private:
+  struct Span {
+    int kid, a, b;
+  };
+  static constexpr size_t kMaxEvents = 1 << 16;
+  std::vector<cudaEvent_t> pool_;
+  size_t used_ = 0;
+  std::vector<Span> spans_;
+};
+
+struct EngineBase {
+  virtual ~EngineBase() = default;
+  KernelTimer timer;
+  virtual nlc_status step(int64_t n, int schedule) = 0;
+  virtual nlc_status set_fields(const double* Q5, const double* rho,
+                                const double* u) = 0;
+  virtual nlc_status get_fields(double* Q5, double* rho, double* u) = 0;
+  virtual nlc_status get_populations(double* f) = 0;
+  virtual nlc_status observables(nlc_obs* out, double* s_profile) = 0;
+  std::string err;
+};
+
+struct EngineArgs {
+  nlc_grid grid;
+  nlc_params params;
+  cudaStream_t stream;
+};
+
+// factories, one per translation unit (lattice x precision)
+std::unique_ptr<EngineBase> make_engine_d2q9_f64(const EngineArgs&, nlc_status*, std::string*);
+std::unique_ptr<EngineBase> make_engine_d2q9_f32(const EngineArgs&, nlc_status*, std::string*);
+std::unique_ptr<EngineBase> make_engine_d3q19_f64(const EngineArgs&, nlc_status*, std::string*);
+std::unique_ptr<EngineBase> make_engine_d3q19_f32(const EngineArgs&, nlc_status*, std::string*);
+
+}  // namespace nlc

@@ -1,0 +1,240 @@
+// nlc_api.cpp -- the C ABI of libnlc (declared in include/nlc.h).
+//
+// Argument checking, context ownership and error reporting; the work is done
+// by the templated engines (engine.cuh), one per lattice and precision.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "../../include/nlc.h"
+#include "engine.h"
+#include "lattice.cuh"
+
+static_assert(nlc::KID_COUNT == NLC_N_KERNELS, "kernel id table out of sync");
+
+struct nlc_ctx {
+  nlc_grid grid;
+  nlc_params params;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int schedule = NLC_SCHED_FUSED;
+  int64_t steps = 0;
+  std::unique_ptr<nlc::EngineBase> eng;
+  std::string err;
+};
+
+namespace {
+
+nlc_status fail(nlc_ctx* ctx, nlc_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+bool finite(double v) { return std::isfinite(v); }
+
+nlc_status check_grid(const nlc_grid* g, std::string* msg) {
+  if (!g) {
+    *msg = "grid is NULL";
+    return NLC_EINVAL;
+  }
+  if (g->lattice != NLC_D2Q9 && g->lattice != NLC_D3Q19) {
+    *msg = "unknown lattice " + std::to_string(g->lattice);
+    return NLC_EINVAL;
+  }
+  if (g->precision != NLC_FP64 && g->precision != NLC_FP32) {
+    *msg = "unknown precision " + std::to_string(g->precision);
+    return NLC_EINVAL;
+  }
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) {
+    *msg = "lattice extents must be >= 1";
+    return NLC_EINVAL;
+  }
+  if (g->lattice == NLC_D2Q9 && g->nz != 1) {
+    *msg = "D2Q9 needs nz = 1";
+    return NLC_EINVAL;
+  }
+  const double cells = (double)g->nx * g->ny * g->nz;
+  if (cells > 4.0e9) {
+    *msg = "lattice too large";
+    return NLC_EINVAL;
+  }
+  return NLC_OK;
+}
+
+nlc_status check_params(const nlc_params* p, std::string* msg) {
+  if (!p) {
+    *msg = "params is NULL";
+    return NLC_EINVAL;
+  }
+  const double v[7] = {p->A0, p->K, p->gamma, p->Gamma, p->xi, p->tau, p->rho0};
+  for (double x : v)
+    if (!finite(x)) {
+      *msg = "parameters must be finite";
+      return NLC_EINVAL;
+    }
+  if (!(p->tau > 0.5)) {
+    *msg = "tau must exceed 1/2";
+    return NLC_EINVAL;
+  }
+  if (!(p->rho0 > 0.0)) {
+    *msg = "rho0 must be positive";
+    return NLC_EINVAL;
+  }
+  if (p->K < 0.0 || p->Gamma < 0.0) {
+    *msg = "K and Gamma must be non-negative";
+    return NLC_EINVAL;
+  }
+  return NLC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nlc_status nlc_create(const nlc_grid* grid, const nlc_params* params,
+                      void* stream, nlc_ctx** out) {
+  if (!out) return NLC_EINVAL;
+  *out = nullptr;
+  std::string msg;
+  nlc_status st = check_grid(grid, &msg);
+  if (st == NLC_OK) st = check_params(params, &msg);
+  if (st != NLC_OK) return st;
+  nlc_ctx* ctx = new (std::nothrow) nlc_ctx();
+  if (!ctx) return NLC_ENOMEM;
+  ctx->grid = *grid;
+  ctx->params = *params;
+  ctx->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return NLC_ECUDA;
+  }
+  nlc::EngineArgs a{*grid, *params, ctx->stream};
+  const bool d3 = grid->lattice == NLC_D3Q19;
+  const bool f64 = grid->precision == NLC_FP64;
+  st = NLC_OK;
+  if (d3)
+    ctx->eng = f64 ? nlc::make_engine_d3q19_f64(a, &st, &msg)
+                   : nlc::make_engine_d3q19_f32(a, &st, &msg);
+  else
+    ctx->eng = f64 ? nlc::make_engine_d2q9_f64(a, &st, &msg)
+                   : nlc::make_engine_d2q9_f32(a, &st, &msg);
+  if (!ctx->eng) {
+    delete ctx;
+    return st != NLC_OK ? st : NLC_ECUDA;
+  }
+  *out = ctx;
+  return NLC_OK;
+}
+
+nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule) {
+  if (!ctx) return NLC_EINVAL;
+  if (schedule != NLC_SCHED_FUSED && schedule != NLC_SCHED_UNFUSED)
+    return fail(ctx, NLC_EINVAL, "unknown schedule");
+  ctx->schedule = schedule;
+  return NLC_OK;
+}
+
+nlc_status nlc_set_fields(nlc_ctx* ctx, int32_t inst, const double* Q5,
+                          const double* rho, const double* u) {
+  if (!ctx) return NLC_EINVAL;
+  if (inst != 0) return fail(ctx, NLC_EINVAL, "instance out of range");
+  if (!Q5) return fail(ctx, NLC_EINVAL, "Q5 is NULL");
+  nlc_status st = ctx->eng->set_fields(Q5, rho, u);
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  ctx->steps = 0;
+  return NLC_OK;
+}
+
+nlc_status nlc_get_fields(nlc_ctx* ctx, int32_t inst, double* Q5, double* rho,
+                          double* u) {
+  if (!ctx) return NLC_EINVAL;
+  if (inst != 0) return fail(ctx, NLC_EINVAL, "instance out of range");
+  nlc_status st = ctx->eng->get_fields(Q5, rho, u);
+  return st == NLC_OK ? st : fail(ctx, st, ctx->eng->err);
+}
+
+nlc_status nlc_get_populations(nlc_ctx* ctx, int32_t inst, double* f) {
+  if (!ctx) return NLC_EINVAL;
+  if (inst != 0) return fail(ctx, NLC_EINVAL, "instance out of range");
+  if (!f) return fail(ctx, NLC_EINVAL, "f is NULL");
+  nlc_status st = ctx->eng->get_populations(f);
+  return st == NLC_OK ? st : fail(ctx, st, ctx->eng->err);
+}
+
+nlc_status nlc_step(nlc_ctx* ctx, int64_t n) {
+  if (!ctx) return NLC_EINVAL;
+  if (n < 0) return fail(ctx, NLC_EINVAL, "negative step count");
+  nlc_status st = ctx->eng->step(n, ctx->schedule);
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  ctx->steps += n;
+  return NLC_OK;
+}
+
+nlc_status nlc_observables(nlc_ctx* ctx, int32_t inst, nlc_obs* out,
+                           double* s_profile) {
+  if (!ctx) return NLC_EINVAL;
+  if (inst != 0) return fail(ctx, NLC_EINVAL, "instance out of range");
+  if (!out) return fail(ctx, NLC_EINVAL, "out is NULL");
+  nlc_status st = ctx->eng->observables(out, s_profile);
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  out->step = ctx->steps;
+  return NLC_OK;
+}
+
+nlc_status nlc_set_timing(nlc_ctx* ctx, int32_t enable) {
+  if (!ctx) return NLC_EINVAL;
+  if (enable) ctx->eng->timer.reset();
+  ctx->eng->timer.on = enable != 0;
+  return NLC_OK;
+}
+
+nlc_status nlc_get_timing(nlc_ctx* ctx, int32_t max_kernels, double* total_ms,
+                          int64_t* launches, int32_t* n_kernels) {
+  if (!ctx) return NLC_EINVAL;
+  if (max_kernels < 0) return fail(ctx, NLC_EINVAL, "max_kernels < 0");
+  double ms[nlc::KID_COUNT];
+  int64_t cnt[nlc::KID_COUNT];
+  cudaError_t e = ctx->eng->timer.totals(ms, cnt);
+  if (e != cudaSuccess)
+    return fail(ctx, NLC_ECUDA, std::string("timing: ") + cudaGetErrorString(e));
+  for (int k = 0; k < nlc::KID_COUNT && k < max_kernels; k++) {
+    if (total_ms) total_ms[k] = ms[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  if (n_kernels) *n_kernels = nlc::KID_COUNT;
+  return NLC_OK;
+}
+
+const char* nlc_timing_name(int32_t k) {
+  static const char* names[nlc::KID_COUNT] = {
+      "fused_lb", "fused_be", "stress", "lb", "predict", "correct"};
+  return (k >= 0 && k < nlc::KID_COUNT) ? names[k] : "?";
+}
+
+const char* nlc_last_error(const nlc_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "context is NULL";
+}
+
+void nlc_destroy(nlc_ctx* ctx) { delete ctx; }
+
+int32_t nlc_lattice_velocities(int32_t lattice, int32_t* c, double* w) {
+  if (lattice != NLC_D2Q9 && lattice != NLC_D3Q19) return -1;
+  const int q = lattice == NLC_D2Q9 ? nlc::LatD2Q9::Q : nlc::LatD3Q19::Q;
+  for (int i = 0; i < q; i++) {
+    for (int a = 0; a < 3; a++) {
+      const int v = lattice == NLC_D2Q9 ? nlc::LatD2Q9::c(i, a) : nlc::LatD3Q19::c(i, a);
+      if (c) c[3 * i + a] = v;
+    }
+    if (w) w[i] = lattice == NLC_D2Q9 ? nlc::LatD2Q9::w(i) : nlc::LatD3Q19::w(i);
+  }
+  return q;
+}
+
+const char* nlc_version(void) { return "nlc 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+"""Python binding of libnlc's C ABI (include/nlc.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Function names match the C entry points; `Simulation` is a
+small convenience wrapper over them.  There is no fallback: if libnlc.so
+cannot be loaded, every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NLC_OK = 0
+STATUS = {0: "NLC_OK", -1: "NLC_EINVAL", -2: "NLC_ENOMEM", -3: "NLC_ECUDA",
+          -4: "NLC_EUNSTABLE", -5: "NLC_ETIMEOUT", -6: "NLC_ECORRUPT",
+          -7: "NLC_EUNSUPPORTED"}
+NLC_D2Q9, NLC_D3Q19 = 0, 1
+NLC_FP64, NLC_FP32 = 0, 1
+NLC_SCHED_FUSED, NLC_SCHED_UNFUSED = 0, 1
+
+
+class NlcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nlc_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("lattice", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+class nlc_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("A0", "K", "gamma", "Gamma", "xi", "tau", "rho0")]
+
+
+class nlc_obs(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("mom", ctypes.c_double * 3),
+                ("s_area", ctypes.c_double), ("radius", ctypes.c_double),
+                ("x_iface", ctypes.c_double), ("max_u", ctypes.c_double),
+                ("free_energy", ctypes.c_double),
+                ("nonfinite", ctypes.c_int64), ("step", ctypes.c_int64)]
+
+    def as_dict(self):
+        return dict(mass=self.mass, mom_x=self.mom[0], mom_y=self.mom[1],
+                    mom_z=self.mom[2], s_area=self.s_area, radius=self.radius,
+                    x_iface=self.x_iface, max_u=self.max_u,
+                    free_energy=self.free_energy, nonfinite=self.nonfinite,
+                    step=self.step)
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libnlc.so (compiling it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise OSError(f"libnlc.so not found at {path}; run build()")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                      ctypes.c_double)
+    sig = {
+        "nlc_create": ([ctypes.POINTER(nlc_grid), ctypes.POINTER(nlc_params),
+                        P, ctypes.POINTER(P)], I32),
+        "nlc_set_schedule": ([P, I32], I32),
+        "nlc_set_fields": ([P, I32, P, P, P], I32),
+        "nlc_get_fields": ([P, I32, P, P, P], I32),
+        "nlc_get_populations": ([P, I32, P], I32),
+        "nlc_step": ([P, I64], I32),
+        "nlc_observables": ([P, I32, ctypes.POINTER(nlc_obs), P], I32),
+        "nlc_last_error": ([P], ctypes.c_char_p),
+        "nlc_destroy": ([P], None),
+        "nlc_lattice_velocities": ([I32, P, P], I32),
+        "nlc_set_timing": ([P, I32], I32),
+        "nlc_get_timing": ([P, I32, P, P, P], I32),
+        "nlc_timing_name": ([I32], ctypes.c_char_p),
+        "nlc_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return ["nlc_create", "nlc_set_schedule", "nlc_set_fields",
+            "nlc_get_fields", "nlc_get_populations", "nlc_step",
+            "nlc_observables", "nlc_last_error", "nlc_destroy",
+            "nlc_lattice_velocities", "nlc_version", "nlc_set_timing",
+            "nlc_get_timing", "nlc_timing_name"]
+
+
+def _check(ctx, status):
+    if status != NLC_OK:
+        msg = load().nlc_last_error(ctx).decode() if ctx else ""
+        raise NlcError(status, msg)
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _f64(a, shape):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {shape}, got {a.shape}")
+    return a
+
+
+# -- thin wrappers with the C names ------------------------------------------
+
+def nlc_create(grid, params, stream=None):
+    lib = load()
+    ctx = ctypes.c_void_p()
+    st = lib.nlc_create(ctypes.byref(grid), ctypes.byref(params),
+                        ctypes.c_void_p(stream or 0), ctypes.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def nlc_set_schedule(ctx, schedule):
+    _check(ctx, load().nlc_set_schedule(ctx, schedule))
+
+
+def nlc_set_fields(ctx, inst, Q5, rho=None, u=None):
+    _check(ctx, load().nlc_set_fields(ctx, inst, _ptr(Q5), _ptr(rho), _ptr(u)))
+
+
+def nlc_get_fields(ctx, inst, Q5=None, rho=None, u=None):
+    _check(ctx, load().nlc_get_fields(ctx, inst, _ptr(Q5), _ptr(rho), _ptr(u)))
+
+
+def nlc_get_populations(ctx, inst, f):
+    _check(ctx, load().nlc_get_populations(ctx, inst, _ptr(f)))
+
+
+def nlc_step(ctx, n):
+    _check(ctx, load().nlc_step(ctx, int(n)))
+
+
+def nlc_observables(ctx, inst, s_profile=None):
+    out = nlc_obs()
+    _check(ctx, load().nlc_observables(ctx, inst, ctypes.byref(out),
+                                       _ptr(s_profile)))
+    return out
+
+
+def nlc_last_error(ctx):
+    return load().nlc_last_error(ctx).decode()
+
+
+def nlc_destroy(ctx):
+    load().nlc_destroy(ctx)
+
+
+def nlc_lattice_velocities(lattice):
+    q = 9 if lattice == NLC_D2Q9 else 19
+    c = np.zeros((q, 3), dtype=np.int32)
+    w = np.zeros(q, dtype=np.float64)
+    r = load().nlc_lattice_velocities(lattice, _ptr(c), _ptr(w))
+    if r != q:
+        raise NlcError(-1, "bad lattice")
+    return c, w
+
+
+def nlc_set_timing(ctx, enable):
+    _check(ctx, load().nlc_set_timing(ctx, int(bool(enable))))
+
+
+def nlc_get_timing(ctx):
+    """{kernel name: (total ms, launches)} since timing was enabled."""
+    ms = np.zeros(16)
+    cnt = np.zeros(16, dtype=np.int64)
+    n = ctypes.c_int32()
+    _check(ctx, load().nlc_get_timing(ctx, 16, _ptr(ms), _ptr(cnt),
+                                      ctypes.byref(n)))
+    lib = load()
+    return {lib.nlc_timing_name(k).decode(): (float(ms[k]), int(cnt[k]))
+            for k in range(n.value)}
+
+
+def nlc_version():
+    return load().nlc_version().decode()
+
+
+# -- convenience wrapper -----------------------------------------------------
+
+class Simulation:
+    """One lattice on the current CUDA device.
+
+    shape is (nz, ny, nx); params a dict with A0, K, gamma, Gamma, xi, tau
+    (and optionally rho0).  stream: a cudaStream_t as an int (for example
+    torch.cuda.current_stream().cuda_stream), or None.
+    """
+
+    def __init__(self, lattice, shape, params, precision=NLC_FP64,
+                 stream=None, schedule=NLC_SCHED_FUSED):
+        nz, ny, nx = shape
+        self.shape = (nz, ny, nx)
+        self.lattice = lattice
+        self.q = 9 if lattice == NLC_D2Q9 else 19
+        g = nlc_grid(nx, ny, nz, lattice, precision)
+        p = nlc_params(params["A0"], params["K"], params["gamma"],
+                       params["Gamma"], params["xi"], params["tau"],
+                       params.get("rho0", 1.0))
+        self.ctx = nlc_create(g, p, stream)
+        if schedule != NLC_SCHED_FUSED:
+            nlc_set_schedule(self.ctx, schedule)
+
+    @property
+    def n_cells(self):
+        nz, ny, nx = self.shape
+        return nx * ny * nz
+
+    def set_fields(self, Q5, rho=None, u=None):
+        sh = self.shape
+        nlc_set_fields(self.ctx, 0, _f64(Q5, (5,) + sh), _f64(rho, sh),
+                       _f64(u, (3,) + sh))
+
+    def get_fields(self):
+        sh = self.shape
+        Q5 = np.empty((5,) + sh)
+        rho = np.empty(sh)
+        u = np.empty((3,) + sh)
+        nlc_get_fields(self.ctx, 0, Q5, rho, u)
+        return Q5, rho, u
+
+    def get_populations(self):
+        f = np.empty((self.q,) + self.shape)
+        nlc_get_populations(self.ctx, 0, f)
+        return f
+
+    def step(self, n=1):
+        nlc_step(self.ctx, n)
+
+    def observables(self, profile=False):
+        prof = np.empty(self.shape[2]) if profile else None
+        d = nlc_observables(self.ctx, 0, prof).as_dict()
+        if profile:
+            d["s_profile"] = prof
+        return d
+
+    def close(self):
+        if self.ctx:
+            nlc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
