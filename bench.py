@@ -264,7 +264,9 @@ def run_ours(args, w):
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
-                         stream=stream.cuda_stream)
+                         stream=stream.cuda_stream,
+                         schedule=(nlc.NLC_SCHED_FUSED if args.schedule == "fused"
+                                   else nlc.NLC_SCHED_UNFUSED))
     Q0 = w.initial_q5()
     sim.set_fields(Q0)
     cells = w.n_cells
@@ -384,11 +386,19 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", default=None,
+                    help="nz,ny,nx of a smaller lattice with the same recipe "
+                         "(profiling captures); the reported workload is "
+                         "the default 256^3")
+    ap.add_argument("--schedule", default="fused", choices=["fused", "unfused"])
     args = ap.parse_args()
     # at least three untimed warm-up steps (reported as the count used)
     args.warmup = max(args.warmup, 3)
     from paper_1907_13415_gb300 import workloads as wl
     w = wl.sphere_256()
+    if args.shape:
+        nz, ny, nx = (int(v) for v in args.shape.split(","))
+        w = wl.scaled(w, (nz, ny, nx), size=48 * min(nx, ny, nz) / 256)
     if args.impl == "reference":
         return run_reference(args, w)
     return run_ours(args, w)

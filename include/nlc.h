@@ -154,6 +154,23 @@ NLC_API nlc_status nlc_step(nlc_ctx* ctx, int64_t n);
 NLC_API nlc_status nlc_observables(nlc_ctx* ctx, int32_t inst, nlc_obs* out,
                            double* s_profile);
 
+/* Checkpoint of a single-lattice context: a header (magic "NLCSTATE",
+ * format version, grid, parameters, step count), the populations and the Q
+ * components exactly as stored on the device (bitwise, in the context's
+ * precision), and a checksum (64-bit FNV-1a over 8-byte little-endian words
+ * of the payload).  buf == NULL: *len receives the size needed.  Otherwise
+ * *len must be at least that size and receives the bytes written.  The
+ * caller owns buf.  Synchronises the stream.  Errors: NLC_EINVAL (small
+ * buffer, null len), NLC_ECUDA. */
+NLC_API nlc_status nlc_save(nlc_ctx* ctx, void* buf, size_t* len);
+
+/* Restores a checkpoint written by nlc_save into a context of the same grid
+ * (extents, lattice, precision) and parameters; continuing from it gives the
+ * same results, bit for bit, as never having stopped.  Errors: NLC_EINVAL
+ * (not a checkpoint, other grid or parameters, short buffer), NLC_ECORRUPT
+ * (checksum mismatch; the state is left unchanged), NLC_ECUDA. */
+NLC_API nlc_status nlc_load(nlc_ctx* ctx, const void* buf, size_t len);
+
 /* Per-kernel device timing (CUDA events recorded on the context's stream
  * around each kernel launch of nlc_step).  enable = 1 clears the log and
  * starts recording; enable = 0 stops.  Meant for profiling: while enabled,

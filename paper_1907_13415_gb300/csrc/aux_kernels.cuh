@@ -13,18 +13,20 @@ namespace nlc {
 template <class Lat, class T>
 __global__ void __launch_bounds__(256) k_set_fields(
     const double* __restrict__ q_in, const double* __restrict__ rho_in,
-    const double* __restrict__ u_in, T* __restrict__ Q, T* __restrict__ g,
+    const double* __restrict__ u_in, Field<T> Q, T* __restrict__ g,
     Dims d, double rho0, unsigned long long* __restrict__ bad) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (!decode(d, idx, x, y, z)) return;
   int nbad = 0;
+  T qv[5];
 #pragma unroll
   for (int k = 0; k < 5; k++) {
     const double v = q_in[k * d.n + idx];
     nbad += !isfinite(v);
-    Q[k * d.n + idx] = (T)v;
+    qv[k] = (T)v;
   }
+  store_with_images<T, 5, Lat::DIM>(Q, d, x, y, z, qv);
   if (rho_in) nbad += !isfinite(rho_in[idx]) || !(rho_in[idx] > 0.0);
   if (u_in)
     for (int a = 0; a < 3; a++) nbad += !isfinite(u_in[a * d.n + idx]);
@@ -81,12 +83,37 @@ __global__ void __launch_bounds__(256) k_populations_out(
     f[(int64_t)i * d.n + idx] = Lat::w(i) * rho0 + (double)g[i];
 }
 
+// interior of a padded NC-component field into a dense float64 array
 template <class T>
-__global__ void __launch_bounds__(256) k_to_double(const T* __restrict__ in,
-                                                   double* __restrict__ out,
-                                                   int64_t count) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) out[i] = (double)in[i];
+__global__ void __launch_bounds__(256) k_field_out(Field<T> F, int nc, Dims d,
+                                                   double* __restrict__ out) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!decode(d, idx, x, y, z)) return;
+  for (int k = 0; k < nc; k++) out[k * d.n + idx] = (double)F.at(k, x, y, z);
+}
+
+// interior of a padded 5-component field to a dense array of the same type
+// (checkpoints: bit-exact)
+template <class T>
+__global__ void __launch_bounds__(256) k_field_raw_out(Field<T> F, int nc, Dims d,
+                                                       T* __restrict__ out) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!decode(d, idx, x, y, z)) return;
+  for (int k = 0; k < nc; k++) out[k * d.n + idx] = F.at(k, x, y, z);
+}
+
+// dense 5-component array into a padded field, with periodic images
+template <class T, int DIM>
+__global__ void __launch_bounds__(256) k_field_raw_in(const T* __restrict__ in, Dims d,
+                                                      Field<T> F) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!decode(d, idx, x, y, z)) return;
+  T v[5];
+  for (int k = 0; k < 5; k++) v[k] = in[k * d.n + idx];
+  store_with_images<T, 5, DIM>(F, d, x, y, z, v);
 }
 
 // Observables, pass 1: per-block FP64 partial sums over cells.
@@ -96,7 +123,7 @@ constexpr int OBS_SLOTS = 8;
 
 template <class Lat, class T>
 __global__ void __launch_bounds__(256) k_obs_partial(
-    const T* __restrict__ Q, const T* __restrict__ gpost,
+    Field<T> Q, const T* __restrict__ gpost,
     const double* __restrict__ rho, const double* __restrict__ u, Dims d,
     Par<T> p, double s_ref, double* __restrict__ partial) {
   __shared__ double sh[32];
@@ -121,7 +148,7 @@ __global__ void __launch_bounds__(256) k_obs_partial(
     int nbad = 0;
 #pragma unroll
     for (int k = 0; k < 5; k++) {
-      q[k] = (double)Q[k * d.n + idx];
+      q[k] = (double)Q.at(k, x, y, z);
       nbad += !isfinite(q[k]);
     }
 #pragma unroll
@@ -138,12 +165,13 @@ __global__ void __launch_bounds__(256) k_obs_partial(
     double e = A0 / 2.0 * (1.0 - gam / 3.0) * tr2 - A0 * gam / 3.0 * tr3 +
                A0 * gam / 4.0 * tr2 * tr2;
     // forward-difference gradient energy K/2 sum_g |Q(x+e_g) - Q(x)|^2
-    const int64_t nbs[3] = {cell_of(d, wrap_inc(x, d.nx), y, z),
-                            cell_of(d, x, wrap_inc(y, d.ny), z),
-                            cell_of(d, x, y, wrap_inc(z, d.nz))};
+    const int nb[3][3] = {{wrap_inc(x, d.nx), y, z},
+                          {x, wrap_inc(y, d.ny), z},
+                          {x, y, wrap_inc(z, d.nz)}};
     for (int gdir = 0; gdir < 3; gdir++) {
       double dv[5];
-      for (int k = 0; k < 5; k++) dv[k] = (double)Q[k * d.n + nbs[gdir]] - q[k];
+      for (int k = 0; k < 5; k++)
+        dv[k] = (double)Q.at(k, nb[gdir][0], nb[gdir][1], nb[gdir][2]) - q[k];
       const double dzz = -dv[0] - dv[3];
       e += K / 2.0 * (dv[0] * dv[0] + dv[3] * dv[3] + dzz * dzz +
                       2.0 * (dv[1] * dv[1] + dv[2] * dv[2] + dv[4] * dv[4]));
@@ -182,7 +210,7 @@ __global__ void __launch_bounds__(256) k_obs_final(const double* __restrict__ pa
 // y,z-mean of S per x: partial sums over row chunks, then a fixed-order sum
 template <class T>
 __global__ void __launch_bounds__(128) k_profile_partial(
-    const T* __restrict__ Q, Dims d, int rows_per_chunk,
+    Field<T> Q, Dims d, int rows_per_chunk,
     double* __restrict__ partial) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int chunk = blockIdx.y;
@@ -192,9 +220,9 @@ __global__ void __launch_bounds__(128) k_profile_partial(
   const int64_t r1 = r0 + rows_per_chunk < rows ? r0 + rows_per_chunk : rows;
   double s = 0.0;
   for (int64_t r = r0; r < r1; r++) {
-    const int64_t c = r * d.nx + x;
+    const int yy = (int)(r % d.ny), zz = (int)(r / d.ny);
     double q[5];
-    for (int k = 0; k < 5; k++) q[k] = (double)Q[k * d.n + c];
+    for (int k = 0; k < 5; k++) q[k] = (double)Q.at(k, x, yy, zz);
     const double qzz = -q[0] - q[3];
     const double tr2 = q[0] * q[0] + q[3] * q[3] + qzz * qzz +
                        2.0 * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);

@@ -1,4 +1,4 @@
-// common.cuh -- lattice extent, indexing and small device helpers.
+// common.cuh -- lattice extent, field layout, indexing and small helpers.
 #pragma once
 #include <cstdint>
 
@@ -7,6 +7,46 @@ namespace nlc {
 struct Dims {
   int nx, ny, nz;
   int64_t n;  // nx * ny * nz
+};
+
+// Ghost layers of the stencil fields (Q and u).  These fields are stored
+// padded, with periodic images of the interior in a 2-cell ring around it in
+// each lattice direction, so that every halo tile the kernels need is one
+// plain rectangular box (loaded by TMA) and no wrap-around arithmetic is
+// needed when reading them.  The interior x = 0 sits at padded column XOFF;
+// XOFF = 4 keeps every tile's box start (x0 - 4) 16-byte aligned.
+constexpr int GHOST = 2;
+constexpr int XOFF = 4;
+
+struct Layout {
+  int nxp, nyp, nzp;  // padded extents
+  int zoff;           // GHOST on 3D lattices, 0 on a single plane (D2Q9)
+  int64_t plane;      // nxp * nyp
+  int64_t comp;       // nxp * nyp * nzp
+};
+
+inline Layout make_layout(const Dims& d, bool three_d) {
+  Layout L;
+  L.nxp = ((d.nx + XOFF + GHOST) + 3) / 4 * 4;
+  L.nyp = d.ny + 2 * GHOST;
+  L.nzp = three_d ? d.nz + 2 * GHOST : 1;
+  L.zoff = three_d ? GHOST : 0;
+  L.plane = (int64_t)L.nxp * L.nyp;
+  L.comp = L.plane * L.nzp;
+  return L;
+}
+
+// A padded multi-component field; at(k, x, y, z) with x, y, z in interior
+// coordinates, valid for -GHOST <= x < nx + GHOST (and likewise y, z).
+template <class T>
+struct Field {
+  T* base;  // start of the allocation
+  Layout L;
+  __host__ __device__ int64_t off(int k, int x, int y, int z) const {
+    return (int64_t)k * L.comp + (int64_t)(z + L.zoff) * L.plane +
+           (int64_t)(y + GHOST) * L.nxp + (x + XOFF);
+  }
+  __device__ T& at(int k, int x, int y, int z) const { return base[off(k, x, y, z)]; }
 };
 
 __device__ __forceinline__ int wrap_inc(int v, int n) { return v + 1 == n ? 0 : v + 1; }
@@ -20,6 +60,37 @@ __device__ __forceinline__ int wrap_add(int v, int d, int n) {
 
 __device__ __forceinline__ int64_t cell_of(const Dims& d, int x, int y, int z) {
   return (int64_t)x + (int64_t)d.nx * ((int64_t)y + (int64_t)d.ny * z);
+}
+
+// Stores NC component values of cell (x, y, z) of a padded field, and every
+// periodic image of the cell that falls in the ghost ring.  Only cells within
+// GHOST of a face have images; lattices thinner than the ring get several.
+template <class T, int NC, int DIM>
+__device__ __forceinline__ void store_with_images(const Field<T>& F, const Dims& d,
+                                                  int x, int y, int z,
+                                                  const T v[NC]) {
+#pragma unroll
+  for (int k = 0; k < NC; k++) F.at(k, x, y, z) = v[k];
+  const bool inner = x >= GHOST && x < d.nx - GHOST && y >= GHOST &&
+                     y < d.ny - GHOST &&
+                     (DIM == 2 || (z >= GHOST && z < d.nz - GHOST));
+  if (inner) return;
+  const int kz0 = DIM == 3 ? -GHOST : 0, kz1 = DIM == 3 ? GHOST : 0;
+  for (int kz = kz0; kz <= kz1; kz++) {
+    const int zi = z + kz * d.nz;
+    if (zi < -GHOST || zi >= d.nz + GHOST) continue;
+    for (int ky = -GHOST; ky <= GHOST; ky++) {
+      const int yi = y + ky * d.ny;
+      if (yi < -GHOST || yi >= d.ny + GHOST) continue;
+      for (int kx = -GHOST; kx <= GHOST; kx++) {
+        const int xi = x + kx * d.nx;
+        if (xi < -GHOST || xi >= d.nx + GHOST) continue;
+        if (kx == 0 && ky == 0 && kz == 0) continue;
+#pragma unroll
+        for (int k = 0; k < NC; k++) F.at(k, xi, yi, zi) = v[k];
+      }
+    }
+  }
 }
 
 // fixed-order FP64 block sum (blockDim.x a multiple of 32, <= 1024);

@@ -41,6 +41,7 @@ class Engine final : public EngineBase {
     d_.ny = a.grid.ny;
     d_.nz = a.grid.nz;
     d_.n = (int64_t)a.grid.nx * a.grid.ny * a.grid.nz;
+    L_ = make_layout(d_, DIM == 3);
     const nlc_params& q = a.params;
     p_.A0 = (T)q.A0;
     p_.K = (T)q.K;
@@ -60,27 +61,43 @@ class Engine final : public EngineBase {
   nlc_status init() {
     const int64_t n = d_.n;
     nlc_status s;
+    T *q0, *q1, *u;
     if ((s = alloc(&g_[0], (size_t)Q * n)) || (s = alloc(&g_[1], (size_t)Q * n)) ||
-        (s = alloc(&q_[0], (size_t)5 * n)) || (s = alloc(&q_[1], (size_t)5 * n)) ||
-        (s = alloc(&u_, (size_t)DIM * n)) || (s = alloc(&bad_, 1)))
+        (s = alloc(&q0, (size_t)5 * L_.comp)) || (s = alloc(&q1, (size_t)5 * L_.comp)) ||
+        (s = alloc(&u, (size_t)DIM * L_.comp)) || (s = alloc(&bad_, 1)) ||
+        (s = alloc(&derr_, 1)))
       return s;
-    NLC_CK(cudaMemsetAsync(g_[0], 0, sizeof(T) * Q * n, args_.stream));
-    NLC_CK(cudaMemsetAsync(q_[0], 0, sizeof(T) * 5 * n, args_.stream));
-    NLC_CK(cudaMemsetAsync(u_, 0, sizeof(T) * DIM * n, args_.stream));
+    q_[0] = Field<T>{q0, L_};
+    q_[1] = Field<T>{q1, L_};
+    u_ = Field<T>{u, L_};
+    cudaStream_t st = args_.stream;
+    NLC_CK(cudaMemsetAsync(g_[0], 0, sizeof(T) * Q * n, st));
+    NLC_CK(cudaMemsetAsync(q0, 0, sizeof(T) * 5 * L_.comp, st));
+    NLC_CK(cudaMemsetAsync(q1, 0, sizeof(T) * 5 * L_.comp, st));
+    NLC_CK(cudaMemsetAsync(u, 0, sizeof(T) * DIM * L_.comp, st));
+    NLC_CK(cudaMemsetAsync(derr_, 0, sizeof(unsigned), st));
+    // TMA descriptors of the three padded fields (pointers never change)
+    maps_ok_ = encode_field_map<T>(&qmap_[0], q0, L_.nxp, L_.nyp, L_.nzp, 5, BXW, BYH) &&
+               encode_field_map<T>(&qmap_[1], q1, L_.nxp, L_.nyp, L_.nzp, 5, BXW, BYH) &&
+               encode_field_map<T>(&umap_, u, L_.nxp, L_.nyp, L_.nzp, DIM, BXW, BYH);
     return NLC_OK;
   }
 
   // ---------------------------------------------------------------- step
   nlc_status step(int64_t n, int schedule) override {
     if (n <= 0) return NLC_OK;
+    nlc_status s;
     if (schedule == NLC_SCHED_UNFUSED) {
-      nlc_status s;
       if ((s = ensure_unfused())) return s;
       for (int64_t k = 0; k < n; k++)
         if ((s = step_unfused())) return s;
       return NLC_OK;
     }
-    nlc_status s;
+    if (!maps_ok_) {
+      err = "TMA tensor maps unavailable (driver entry point missing); use the "
+            "unfused schedule";
+      return NLC_EUNSUPPORTED;
+    }
     for (int64_t k = 0; k < n; k++)
       if ((s = step_fused())) return s;
     return NLC_OK;
@@ -121,8 +138,8 @@ class Engine final : public EngineBase {
     const int64_t n = d_.n;
     cudaStream_t st = args_.stream;
     if (Q5) {
-      k_to_double<T><<<grid1(5 * n), 256, 0, st>>>(q_[cur_], stage_, 5 * n);
-      NLC_CK_LAUNCH("k_to_double");
+      k_field_out<T><<<grid1(n), 256, 0, st>>>(q_[cur_], 5, d_, stage_);
+      NLC_CK_LAUNCH("k_field_out");
       NLC_CK(cudaMemcpyAsync(Q5, stage_, sizeof(double) * 5 * n, cudaMemcpyDeviceToHost, st));
     }
     if (rho || u) {
@@ -133,7 +150,7 @@ class Engine final : public EngineBase {
         NLC_CK(cudaMemcpyAsync(u, stage_ + 6 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
     }
     NLC_CK(cudaStreamSynchronize(st));
-    return NLC_OK;
+    return device_error();
   }
 
   nlc_status get_populations(double* f) override {
@@ -145,6 +162,37 @@ class Engine final : public EngineBase {
     NLC_CK_LAUNCH("k_populations_out");
     NLC_CK(cudaMemcpyAsync(f, fstage_, sizeof(double) * Q * n, cudaMemcpyDeviceToHost, st));
     NLC_CK(cudaStreamSynchronize(st));
+    return device_error();
+  }
+
+  size_t state_bytes() const override { return sizeof(T) * (size_t)(Q + 5) * (size_t)d_.n; }
+
+  nlc_status save_state(void* dst) override {
+    nlc_status s;
+    if ((s = ensure_raw())) return s;
+    const int64_t n = d_.n;
+    cudaStream_t st = args_.stream;
+    k_field_raw_out<T><<<grid1(n), 256, 0, st>>>(q_[cur_], 5, d_, raw_);
+    NLC_CK_LAUNCH("k_field_raw_out");
+    NLC_CK(cudaMemcpyAsync(dst, g_[cur_], sizeof(T) * Q * n, cudaMemcpyDeviceToHost, st));
+    NLC_CK(cudaMemcpyAsync((char*)dst + sizeof(T) * Q * n, raw_, sizeof(T) * 5 * n,
+                           cudaMemcpyDeviceToHost, st));
+    NLC_CK(cudaStreamSynchronize(st));
+    return device_error();
+  }
+
+  nlc_status load_state(const void* src) override {
+    nlc_status s;
+    if ((s = ensure_raw())) return s;
+    const int64_t n = d_.n;
+    cudaStream_t st = args_.stream;
+    NLC_CK(cudaMemcpyAsync(g_[0], src, sizeof(T) * Q * n, cudaMemcpyHostToDevice, st));
+    NLC_CK(cudaMemcpyAsync(raw_, (const char*)src + sizeof(T) * Q * n, sizeof(T) * 5 * n,
+                           cudaMemcpyHostToDevice, st));
+    k_field_raw_in<T, DIM><<<grid1(n), 256, 0, st>>>(raw_, d_, q_[0]);
+    NLC_CK_LAUNCH("k_field_raw_in");
+    NLC_CK(cudaStreamSynchronize(st));
+    cur_ = 0;
     return NLC_OK;
   }
 
@@ -173,6 +221,7 @@ class Engine final : public EngineBase {
     NLC_CK(cudaMemcpyAsync(tot, partial_ + obs_blocks_ * OBS_SLOTS, sizeof(tot), cudaMemcpyDeviceToHost, st));
     NLC_CK(cudaMemcpyAsync(prof.data(), prof_, sizeof(double) * d_.nx, cudaMemcpyDeviceToHost, st));
     NLC_CK(cudaStreamSynchronize(st));
+    if ((s = device_error())) return s;
     out->mass = tot[0];
     out->mom[0] = tot[1];
     out->mom[1] = tot[2];
@@ -215,13 +264,27 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
+  // device-side error word (bounded waits that ran out); read after a sync
+  nlc_status device_error() {
+    unsigned e = 0;
+    NLC_CK(cudaMemcpy(&e, derr_, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e != DEV_ERR_NONE) {
+      err = "a bounded wait on a tile copy ran out inside a step kernel (code " +
+            std::to_string(e) + ")";
+      return NLC_ETIMEOUT;
+    }
+    return NLC_OK;
+  }
+
   nlc_status ensure_unfused() {
     if (pi_) return NLC_OK;
     nlc_status s;
     const int64_t n = d_.n;
-    if ((s = alloc(&pi_, (size_t)DIM * DIM * n)) || (s = alloc(&qp_, (size_t)5 * n)) ||
+    T* qp;
+    if ((s = alloc(&pi_, (size_t)DIM * DIM * n)) || (s = alloc(&qp, (size_t)5 * L_.comp)) ||
         (s = alloc(&r1_, (size_t)5 * n)))
       return s;
+    qp_ = Field<T>{qp, L_};
     return NLC_OK;
   }
 
@@ -243,6 +306,11 @@ class Engine final : public EngineBase {
     if ((s = alloc(&prof_partial_, (size_t)(nchunks * d_.nx)))) return s;
     if ((s = alloc(&prof_, (size_t)d_.nx))) return s;
     return NLC_OK;
+  }
+
+  nlc_status ensure_raw() {
+    if (raw_) return NLC_OK;
+    return alloc(&raw_, (size_t)5 * d_.n);
   }
 
   nlc_status ensure_fstage() {
@@ -295,13 +363,13 @@ class Engine final : public EngineBase {
     cudaStream_t st = args_.stream;
     const int a = cur_, b = cur_ ^ 1;
     const int e0 = mark();
-    cudaError_t e = launch_fused_lb<Lat, T>(g_[a], g_[b], q_[a], u_, d_, p_, st);
+    cudaError_t e = launch_fused_lb<Lat, T>(qmap_[a], g_[a], g_[b], u_, d_, p_, derr_, st);
     if (e != cudaSuccess) {
       err = std::string("fused lb kernel: ") + cudaGetErrorString(e);
       return NLC_ECUDA;
     }
     const int e1 = mark();
-    e = launch_fused_be<Lat, T>(q_[a], u_, q_[b], d_, p_, st);
+    e = launch_fused_be<Lat, T>(qmap_[a], umap_, q_[b], d_, p_, derr_, st);
     if (e != cudaSuccess) {
       err = std::string("fused Beris-Edwards kernel: ") + cudaGetErrorString(e);
       return NLC_ECUDA;
@@ -317,20 +385,26 @@ class Engine final : public EngineBase {
 
   EngineArgs args_;
   Dims d_;
+  Layout L_;
   Par<T> p_;
   std::vector<void*> allocs_;
   T* g_[2] = {nullptr, nullptr};
-  T* q_[2] = {nullptr, nullptr};
-  T* u_ = nullptr;
+  Field<T> q_[2];
+  Field<T> u_;
+  Field<T> qp_;
+  CUtensorMap qmap_[2];
+  CUtensorMap umap_;
+  bool maps_ok_ = false;
   T* pi_ = nullptr;
-  T* qp_ = nullptr;
   T* r1_ = nullptr;
+  T* raw_ = nullptr;
   double* stage_ = nullptr;
   double* fstage_ = nullptr;
   double* partial_ = nullptr;
   double* prof_partial_ = nullptr;
   double* prof_ = nullptr;
   unsigned long long* bad_ = nullptr;
+  unsigned* derr_ = nullptr;
   int obs_blocks_ = 1;
   int cur_ = 0;
 };

@@ -77,6 +77,10 @@ struct EngineBase {
   virtual nlc_status get_fields(double* Q5, double* rho, double* u) = 0;
   virtual nlc_status get_populations(double* f) = 0;
   virtual nlc_status observables(nlc_obs* out, double* s_profile) = 0;
+  // raw device state: populations (current buffer) then Q interior
+  virtual size_t state_bytes() const = 0;
+  virtual nlc_status save_state(void* dst) = 0;
+  virtual nlc_status load_state(const void* src) = 0;
   std::string err;
 };
 

@@ -186,6 +186,94 @@ nlc_status nlc_observables(nlc_ctx* ctx, int32_t inst, nlc_obs* out,
   return NLC_OK;
 }
 
+namespace {
+
+struct SaveHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t header_bytes;
+  nlc_grid grid;
+  int32_t pad0;
+  nlc_params params;
+  int64_t step;
+  uint64_t payload_bytes;
+  uint64_t checksum;
+};
+
+const char kMagic[8] = {'N', 'L', 'C', 'S', 'T', 'A', 'T', 'E'};
+
+// 64-bit FNV-1a over 8-byte little-endian words, then the tail bytes
+uint64_t checksum64(const unsigned char* p, size_t n) {
+  uint64_t h = 14695981039346656037ull;
+  const uint64_t prime = 1099511628211ull;
+  size_t i = 0;
+  for (; i + 8 <= n; i += 8) {
+    uint64_t w = 0;
+    for (int b = 7; b >= 0; b--) w = (w << 8) | p[i + b];
+    h ^= w;
+    h *= prime;
+  }
+  for (; i < n; i++) {
+    h ^= p[i];
+    h *= prime;
+  }
+  return h;
+}
+
+}  // namespace
+
+nlc_status nlc_save(nlc_ctx* ctx, void* buf, size_t* len) {
+  if (!ctx) return NLC_EINVAL;
+  if (!len) return fail(ctx, NLC_EINVAL, "len is NULL");
+  const size_t payload = ctx->eng->state_bytes();
+  const size_t need = sizeof(SaveHeader) + payload;
+  if (!buf) {
+    *len = need;
+    return NLC_OK;
+  }
+  if (*len < need) return fail(ctx, NLC_EINVAL, "buffer too small for the state");
+  unsigned char* out = (unsigned char*)buf;
+  nlc_status st = ctx->eng->save_state(out + sizeof(SaveHeader));
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  SaveHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.header_bytes = sizeof(SaveHeader);
+  h.grid = ctx->grid;
+  h.params = ctx->params;
+  h.step = ctx->steps;
+  h.payload_bytes = payload;
+  h.checksum = checksum64(out + sizeof(SaveHeader), payload);
+  std::memcpy(out, &h, sizeof(h));
+  *len = need;
+  return NLC_OK;
+}
+
+nlc_status nlc_load(nlc_ctx* ctx, const void* buf, size_t len) {
+  if (!ctx) return NLC_EINVAL;
+  if (!buf || len < sizeof(SaveHeader)) return fail(ctx, NLC_EINVAL, "not a checkpoint");
+  SaveHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 ||
+      h.header_bytes != sizeof(SaveHeader))
+    return fail(ctx, NLC_EINVAL, "not a checkpoint of this format");
+  if (std::memcmp(&h.grid, &ctx->grid, sizeof(nlc_grid)) != 0)
+    return fail(ctx, NLC_EINVAL, "checkpoint is for another grid or precision");
+  if (std::memcmp(&h.params, &ctx->params, sizeof(nlc_params)) != 0)
+    return fail(ctx, NLC_EINVAL, "checkpoint has other parameters");
+  const size_t payload = ctx->eng->state_bytes();
+  if (h.payload_bytes != payload || len < sizeof(SaveHeader) + payload)
+    return fail(ctx, NLC_EINVAL, "checkpoint is truncated");
+  const unsigned char* p = (const unsigned char*)buf + sizeof(SaveHeader);
+  if (checksum64(p, payload) != h.checksum)
+    return fail(ctx, NLC_ECORRUPT, "checkpoint checksum mismatch");
+  nlc_status st = ctx->eng->load_state(p);
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  ctx->steps = h.step;
+  return NLC_OK;
+}
+
 nlc_status nlc_set_timing(nlc_ctx* ctx, int32_t enable) {
   if (!ctx) return NLC_EINVAL;
   if (enable) ctx->eng->timer.reset();

@@ -1,213 +1,91 @@
 // step_fused.cuh -- one time step as two tiled kernels.
 //
-//   lb kernel : Q^n halo tile in shared memory -> H (Eq. 3) and the stress Pi
-//               (Eq. 5 without P0) on the tile plus a one-cell ring, also in
-//               shared memory -> F = div Pi -> pull-stream the populations,
-//               rho and u (Eq. 6), BGK collision with the source term
-//               (Sec. 1.2.1); stores the post-collision deviations g* and u^n.
-//   be kernel : Q^n and u^n halo tiles in shared memory -> R(Q^n) and the
-//               predictor Q^P on the tile plus a one-cell ring (shared memory)
-//               -> R(Q^P) and the corrector Q^{n+1} (Sec. 1.2.2, steps 1-5).
+//   lb kernel : Q^n tile (+2-cell halo) in shared memory -> H (Eq. 3) and the
+//               stress Pi (Eq. 5 without P0) on the tile plus a one-cell
+//               ring, in shared memory -> F = div Pi -> pull-stream the
+//               populations, rho and u (Eq. 6), BGK collision with the
+//               source term (Sec. 1.2.1); stores the post-collision
+//               deviations g* and u^n.
+//   be kernel : Q^n and u^n tiles (+2 halo) in shared memory -> R(Q^n) and
+//               the predictor Q^P on the tile plus a one-cell ring (shared
+//               memory) -> R(Q^P) and the corrector Q^{n+1} (Sec. 1.2.2,
+//               steps 1-5).
 //
-// Each thread block owns a TX x TY tile of the (x, y) plane.  On D3Q19 it
-// marches along z through a chunk of planes, keeping rings of the last three
-// (or four) planes of each staged field in shared memory, so the z halo is
-// read once per chunk instead of once per plane.  On D2Q9 there is a single
-// plane.  Periodic wrap-around is applied when the halo tiles are gathered, so
-// tiles at the domain edge, ragged tiles and lattices smaller than a tile all
-// take the same path.
+// Each thread block owns a 32 x 8 tile of the (x, y) plane.  On D3Q19 it
+// marches along z through a chunk of planes; the halo planes of Q and u
+// arrive by TMA (one cp.async.bulk.tensor per plane and field) into rings of
+// shared-memory slots, each completed on its own mbarrier, issued one plane
+// ahead of use so the copy overlaps the computation of the current plane.
+// Q and u are padded fields with periodic ghost rings (common.cuh), so every
+// tile box is a plain rectangle; the kernels that write them also write the
+// images.  Populations are read by pull with precomputed periodic offsets.
+//
+// Block = 11 warps: the 340 cells of the tile plus its one-cell ring get one
+// thread each in the ring phase, the 256 tile cells one thread each in the
+// cell phase.
 #pragma once
 #include "common.cuh"
 #include "lattice.cuh"
 #include "physics.cuh"
 #include "step_unfused.cuh"
+#include "tma.cuh"
 
 namespace nlc {
 
-constexpr int FTX = 32;   // tile width (x), one warp
-constexpr int FTY = 8;    // tile height (y)
-constexpr int FNT = FTX * FTY;
-constexpr int RX2 = FTX + 4, RY2 = FTY + 4;  // tile + 2-cell ring
+constexpr int FTX = 32;                  // tile width (x)
+constexpr int FTY = 8;                   // tile height (y)
 constexpr int RX1 = FTX + 2, RY1 = FTY + 2;  // tile + 1-cell ring
-constexpr int A2 = RX2 * RY2;
-constexpr int A1 = RX1 * RY1;
+constexpr int A1 = RX1 * RY1;            // 340 ring-region cells
+constexpr int FNT = 352;                 // 11 warps >= A1
+constexpr int BXW = FTX + 8;             // TMA box width: x0-4 .. x0+35
+constexpr int BYH = FTY + 4;             // TMA box height: y0-2 .. y0+9
+constexpr int BA = BXW * BYH;            // box plane area (480)
+static_assert(FNT >= A1 && FNT % 32 == 0, "ring phase needs one thread per cell");
 
-__device__ __forceinline__ int wrapm(int v, int n) {
-  int r = v % n;
-  return r < 0 ? r + n : r;
-}
+// box index of lattice offset (dx, dy) from the tile origin (x0, y0)
+__host__ __device__ constexpr int box_at(int dx, int dy) { return (dy + 2) * BXW + dx + 4; }
 
-// gather `ncomp` planes of field F (plane stride n) at z into a shared tile
-// of the 2-cell ring region, periodic
 template <class T>
-__device__ __forceinline__ void stage_plane(const T* __restrict__ F, int ncomp,
-                                            const Dims& d, int x0, int y0,
-                                            int z, T* __restrict__ s) {
-  const int zz = wrapm(z, d.nz);
-  for (int c = threadIdx.x; c < A2; c += FNT) {
-    const int rx = c % RX2, ry = c / RX2;
-    const int gx = wrapm(x0 - 2 + rx, d.nx), gy = wrapm(y0 - 2 + ry, d.ny);
-    const int64_t cell = cell_of(d, gx, gy, zz);
-    for (int k = 0; k < ncomp; k++) s[k * A2 + c] = F[k * d.n + cell];
-  }
+constexpr size_t align128(size_t bytes) {
+  return (bytes + 127) / 128 * 128;
 }
 
 // ---------------------------------------------------------------------------
 // lb kernel
 // ---------------------------------------------------------------------------
 template <class Lat, class T>
-struct LbSmem {
-  static constexpr int NP = Lat::DIM == 3 ? 3 : 1;
-  static constexpr int NPI = Lat::DIM * Lat::DIM;
-  static constexpr size_t bytes = sizeof(T) * (size_t)NP * (5 * A2 + NPI * A1);
+struct LbCfg {
+  static constexpr int DIM = Lat::DIM;
+  static constexpr int NPI = DIM * DIM;
+  static constexpr int NSQ = DIM == 3 ? 4 : 1;  // Q plane slots
+  static constexpr int NSP = DIM == 3 ? 3 : 1;  // Pi plane slots
+  static constexpr size_t q_slot = align128<T>(sizeof(T) * 5 * BA);
+  static constexpr size_t p_slot = align128<T>(sizeof(T) * NPI * A1);
+  static constexpr size_t off_p = NSQ * q_slot;
+  static constexpr size_t off_bar = off_p + NSP * p_slot;
+  static constexpr size_t bytes = off_bar + 8 * NSQ;
+  static constexpr uint32_t tx_bytes = sizeof(T) * 5 * BA;
 };
 
-// stress on the 1-ring region of plane slot `s` (z neighbours in slots sm, sp)
-template <class Lat, class T>
-__device__ __forceinline__ void stress_plane(const T* __restrict__ sQ, int s,
-                                             int sm, int sp,
-                                             T* __restrict__ sPi,
-                                             const Par<T>& p) {
-  constexpr int DIM = Lat::DIM;
-  constexpr int NPI = DIM * DIM;
-  const T* Qc = sQ + s * 5 * A2;
-  const T* Qm = sQ + sm * 5 * A2;
-  const T* Qp = sQ + sp * 5 * A2;
-  for (int c = threadIdx.x; c < A1; c += FNT) {
-    const int hx = c % RX1 + 1, hy = c / RX1 + 1;
-    const int o = hy * RX2 + hx;
-    T q[5], dq[3][5], lap[5], h[5], P[3][3];
-#pragma unroll
-    for (int k = 0; k < 5; k++) {
-      const T* F = Qc + k * A2;
-      const T v = F[o], xp = F[o + 1], xm = F[o - 1], yp = F[o + RX2], ym = F[o - RX2];
-      q[k] = v;
-      dq[0][k] = (xp - xm) / T(2);
-      dq[1][k] = (yp - ym) / T(2);
-      T l = (xp + xm - T(2) * v) + (yp + ym - T(2) * v);
-      if (DIM == 3) {
-        const T zp = Qp[k * A2 + o], zm = Qm[k * A2 + o];
-        dq[2][k] = (zp - zm) / T(2);
-        l += zp + zm - T(2) * v;
-      } else {
-        dq[2][k] = T(0);
-      }
-      lap[k] = l;
-    }
-    molecular_field(q, lap, p, h);
-    stress<T, DIM>(q, h, dq, p, P);
-#pragma unroll
-    for (int a = 0; a < DIM; a++)
-#pragma unroll
-      for (int b = 0; b < DIM; b++) sPi[(a * DIM + b) * A1 + c] = P[a][b];
-  }
-  (void)NPI;
-}
-
-template <class Lat, class T>
-__global__ void __launch_bounds__(FNT) k_fused_lb(const T* __restrict__ gin,
-                                                  T* __restrict__ gout,
-                                                  const T* __restrict__ Q,
-                                                  T* __restrict__ U, Dims d,
-                                                  Par<T> p, int tz) {
-  constexpr int DIM = Lat::DIM;
-  constexpr int NPI = DIM * DIM;
-  constexpr int NP = LbSmem<Lat, T>::NP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sQ = reinterpret_cast<T*>(smem_raw);   // [NP][5][A2]
-  T* sPi = sQ + NP * 5 * A2;                // [NP][NPI][A1]
-
-  const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
-  const int tx = threadIdx.x % FTX, ty = threadIdx.x / FTX;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool inside = x < d.nx && y < d.ny;
-  const int ic = (ty + 1) * RX1 + (tx + 1);  // own cell in the 1-ring region
-
-  auto lb_cell = [&](int z, const T* Pc, const T* Pm, const T* Pp) {
-    if (!inside || z >= d.nz) return;
-    T F[3] = {T(0), T(0), T(0)};
-#pragma unroll
-    for (int a = 0; a < DIM; a++) {
-      T s = (Pc[(a * DIM + 0) * A1 + ic + 1] - Pc[(a * DIM + 0) * A1 + ic - 1]) / T(2);
-      s += (Pc[(a * DIM + 1) * A1 + ic + RX1] - Pc[(a * DIM + 1) * A1 + ic - RX1]) / T(2);
-      if (DIM == 3) s += (Pp[(a * DIM + 2) * A1 + ic] - Pm[(a * DIM + 2) * A1 + ic]) / T(2);
-      F[a] = s;
-    }
-    T g[Lat::Q], rho, u[3];
-    pull<Lat, T>(gin, d, x, y, z, g);
-    moments<Lat, T>(g, F, p, rho, u);
-    collide_bgk<Lat, T>(g, rho, u, F, p);
-    const int64_t cell = cell_of(d, x, y, z);
-#pragma unroll
-    for (int i = 0; i < Lat::Q; i++) gout[(int64_t)i * d.n + cell] = g[i];
-#pragma unroll
-    for (int a = 0; a < DIM; a++) U[a * d.n + cell] = u[a];
-  };
-
-  if constexpr (DIM == 2) {
-    stage_plane<T>(Q, 5, d, x0, y0, 0, sQ);
-    __syncthreads();
-    stress_plane<Lat, T>(sQ, 0, 0, 0, sPi, p);
-    __syncthreads();
-    lb_cell(0, sPi, sPi, sPi);
-  } else {
-    const int z0 = blockIdx.z * tz;
-    const int z1 = min(z0 + tz, d.nz);
-    // plane z lives in slot (z - z0 + 3) % 3 of both rings
-    auto slot = [&](int z) { return (z - z0 + 6) % 3; };
-    auto Qs = [&](int z) { return sQ + slot(z) * 5 * A2; };
-    auto Ps = [&](int z) { return sPi + slot(z) * NPI * A1; };
-    stage_plane<T>(Q, 5, d, x0, y0, z0 - 2, Qs(z0 - 2));
-    stage_plane<T>(Q, 5, d, x0, y0, z0 - 1, Qs(z0 - 1));
-    stage_plane<T>(Q, 5, d, x0, y0, z0, Qs(z0));
-    __syncthreads();
-    stress_plane<Lat, T>(sQ, slot(z0 - 1), slot(z0 - 2), slot(z0), Ps(z0 - 1), p);
-    __syncthreads();
-    stage_plane<T>(Q, 5, d, x0, y0, z0 + 1, Qs(z0 + 1));
-    __syncthreads();
-    stress_plane<Lat, T>(sQ, slot(z0), slot(z0 - 1), slot(z0 + 1), Ps(z0), p);
-    for (int z = z0; z < z1; z++) {
-      __syncthreads();
-      stage_plane<T>(Q, 5, d, x0, y0, z + 2, Qs(z + 2));
-      __syncthreads();
-      stress_plane<Lat, T>(sQ, slot(z + 1), slot(z), slot(z + 2), Ps(z + 1), p);
-      __syncthreads();
-      lb_cell(z, Ps(z), Ps(z - 1), Ps(z + 1));
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Beris-Edwards kernel
-// ---------------------------------------------------------------------------
-template <class Lat, class T>
-struct BeSmem {
-  static constexpr int NQ = Lat::DIM == 3 ? 3 : 1;   // Q^n ring
-  static constexpr int NU = Lat::DIM == 3 ? 4 : 1;   // u ring
-  static constexpr int NQP = Lat::DIM == 3 ? 3 : 1;  // Q^P ring
-  static constexpr int NR = Lat::DIM == 3 ? 2 : 1;   // R(Q^n) ring
-  static constexpr size_t bytes =
-      sizeof(T) * ((size_t)NQ * 5 * A2 + (size_t)NU * Lat::DIM * A2 +
-                   (size_t)NQP * 5 * A1 + (size_t)NR * 5 * A1);
-};
-
-// central differences + Laplacian of a 5-component tile field at offset o of
-// a tile with row length RX (z neighbours from the planes above and below)
-template <class T, int DIM, int RX, int AREA>
-__device__ __forceinline__ void tile_stencil5(const T* __restrict__ c,
-                                              const T* __restrict__ m,
-                                              const T* __restrict__ pp, int o,
-                                              T q[5], T dq[3][5], T lap[5]) {
+// stress on the ring-region cell c of a plane whose Q box is in sq (z
+// neighbours in sqm, sqp), into the Pi slot sp
+template <class T, int DIM>
+__device__ __forceinline__ void stress_ring_cell(int c, const T* __restrict__ sq,
+                                                 const T* __restrict__ sqm,
+                                                 const T* __restrict__ sqp,
+                                                 T* __restrict__ sp, const Par<T>& p) {
+  const int o = box_at(c % RX1 - 1, c / RX1 - 1);
+  T q[5], dq[3][5], lap[5], h[5], P[3][3];
 #pragma unroll
   for (int k = 0; k < 5; k++) {
-    const T* F = c + k * AREA;
-    const T v = F[o], xp = F[o + 1], xm = F[o - 1], yp = F[o + RX], ym = F[o - RX];
+    const T* F = sq + k * BA;
+    const T v = F[o], xp = F[o + 1], xm = F[o - 1], yp = F[o + BXW], ym = F[o - BXW];
     q[k] = v;
     dq[0][k] = (xp - xm) / T(2);
     dq[1][k] = (yp - ym) / T(2);
     T l = (xp + xm - T(2) * v) + (yp + ym - T(2) * v);
     if (DIM == 3) {
-      const T zp = pp[k * AREA + o], zm = m[k * AREA + o];
+      const T zp = sqp[k * BA + o], zm = sqm[k * BA + o];
       dq[2][k] = (zp - zm) / T(2);
       l += zp + zm - T(2) * v;
     } else {
@@ -215,22 +93,186 @@ __device__ __forceinline__ void tile_stencil5(const T* __restrict__ c,
     }
     lap[k] = l;
   }
+  molecular_field(q, lap, p, h);
+  stress<T, DIM>(q, h, dq, p, P);
+#pragma unroll
+  for (int a = 0; a < DIM; a++)
+#pragma unroll
+    for (int b = 0; b < DIM; b++) sp[(a * DIM + b) * A1 + c] = P[a][b];
 }
 
-// u and G[a][b] = d_b u_a at offset o of the 2-ring u tile
+template <class Lat, class T>
+__global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
+    k_fused_lb(const __grid_constant__ CUtensorMap qmap, const T* __restrict__ gin,
+               T* __restrict__ gout, Field<T> U, Dims d, Par<T> p, int tz,
+               int zoff, unsigned* __restrict__ err) {
+  using C = LbCfg<Lat, T>;
+  constexpr int DIM = Lat::DIM;
+  constexpr int NPI = C::NPI;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::off_bar);
+  auto sQ = [&](int slot) { return reinterpret_cast<T*>(smem + slot * C::q_slot); };
+  auto sP = [&](int slot) { return reinterpret_cast<T*>(smem + C::off_p + slot * C::p_slot); };
+
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+  const int z0 = DIM == 3 ? blockIdx.z * tz : 0;
+  const int z1 = DIM == 3 ? min(z0 + tz, d.nz) : 1;
+  const int zq0 = DIM == 3 ? z0 - 2 : 0;  // first Q plane loaded
+  const int zp0 = DIM == 3 ? z0 - 1 : 0;  // first Pi plane computed
+  auto qslot = [&](int z) { return (z - zq0) % C::NSQ; };
+  auto qpar = [&](int z) { return (uint32_t)(((z - zq0) / C::NSQ) & 1); };
+  auto pslot = [&](int z) { return (z - zp0) % C::NSP; };
+
+  if (tid == 0) {
+    for (int s = 0; s < C::NSQ; s++) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int z) {  // thread 0 only
+    const int s = qslot(z);
+    mbar_expect_tx(&bars[s], C::tx_bytes);
+    tma_load_4d(sQ(s), &qmap, x0, y0, z + zoff, 0, &bars[s]);
+  };
+  bool late = false;
+  auto wait = [&](int z) { late |= !mbar_wait(&bars[qslot(z)], qpar(z)); };
+  auto abort_block = [&]() {
+    // a wait ran out: report, and let thread 0 drain the copies still in
+    // flight (bounded) before the block exits
+    if (tid == 0) {
+      atomicExch(err, DEV_ERR_TMA_TIMEOUT);
+      for (int s = 0; s < C::NSQ; s++) (void)mbar_wait(&bars[s], 0), (void)mbar_wait(&bars[s], 1);
+    }
+  };
+
+  // per-thread pull offsets (x, y fixed for the whole chunk)
+  const int tx = tid % FTX, ty = tid / FTX;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool cell = tid < FTX * FTY && x < d.nx && y < d.ny;
+  int colx[3] = {0, 0, 0};
+  int64_t rowy[3] = {0, 0, 0};
+  if (cell) {
+    colx[0] = wrap_inc(x, d.nx);  // source x for c_x = -1 ... index c_x + 1
+    colx[1] = x;
+    colx[2] = wrap_dec(x, d.nx);
+    rowy[0] = (int64_t)wrap_inc(y, d.ny) * d.nx;
+    rowy[1] = (int64_t)y * d.nx;
+    rowy[2] = (int64_t)wrap_dec(y, d.ny) * d.nx;
+  }
+  const int64_t nxy = (int64_t)d.nx * d.ny;
+  const int ic = (ty + 1) * RX1 + (tx + 1);
+
+  auto lb_cell = [&](int z) {
+    if (!cell) return;
+    const T* Pc = sP(pslot(z));
+    T F[3] = {T(0), T(0), T(0)};
+    const T* Pm = DIM == 3 ? sP(pslot(z - 1)) : Pc;
+    const T* Pp = DIM == 3 ? sP(pslot(z + 1)) : Pc;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      T s = (Pc[(a * DIM + 0) * A1 + ic + 1] - Pc[(a * DIM + 0) * A1 + ic - 1]) / T(2);
+      s += (Pc[(a * DIM + 1) * A1 + ic + RX1] - Pc[(a * DIM + 1) * A1 + ic - RX1]) / T(2);
+      if (DIM == 3) s += (Pp[(a * DIM + 2) * A1 + ic] - Pm[(a * DIM + 2) * A1 + ic]) / T(2);
+      F[a] = s;
+    }
+    int64_t plane[3];
+    plane[1] = (int64_t)z * nxy;
+    plane[0] = DIM == 3 ? (int64_t)wrap_inc(z, d.nz) * nxy : plane[1];
+    plane[2] = DIM == 3 ? (int64_t)wrap_dec(z, d.nz) * nxy : plane[1];
+    T g[Lat::Q], rho, u[3];
+#pragma unroll
+    for (int i = 0; i < Lat::Q; i++)
+      g[i] = gin[(int64_t)i * d.n + plane[Lat::c(i, 2) + 1] + rowy[Lat::c(i, 1) + 1] +
+                 colx[Lat::c(i, 0) + 1]];
+    moments<Lat, T>(g, F, p, rho, u);
+    collide_bgk<Lat, T>(g, rho, u, F, p);
+    const int64_t o = plane[1] + rowy[1] + x;
+#pragma unroll
+    for (int i = 0; i < Lat::Q; i++) gout[(int64_t)i * d.n + o] = g[i];
+    store_with_images<T, DIM, DIM>(U, d, x, y, z, u);
+  };
+
+  if constexpr (DIM == 2) {
+    if (tid == 0) issue(0);
+    wait(0);
+    if (tid < A1) stress_ring_cell<T, DIM>(tid, sQ(0), sQ(0), sQ(0), sP(0), p);
+    if (__syncthreads_or(late)) {
+      abort_block();
+      return;
+    }
+    lb_cell(0);
+  } else {
+    if (tid == 0)
+      for (int z = z0 - 2; z <= z0 + 1; z++) issue(z);
+    wait(z0 - 2);
+    wait(z0 - 1);
+    wait(z0);
+    if (tid < A1)
+      stress_ring_cell<T, DIM>(tid, sQ(qslot(z0 - 1)), sQ(qslot(z0 - 2)), sQ(qslot(z0)),
+                               sP(pslot(z0 - 1)), p);
+    if (__syncthreads_or(late)) {
+      abort_block();
+      return;
+    }
+    if (tid == 0) issue(z0 + 2);
+    wait(z0 + 1);
+    if (tid < A1)
+      stress_ring_cell<T, DIM>(tid, sQ(qslot(z0)), sQ(qslot(z0 - 1)), sQ(qslot(z0 + 1)),
+                               sP(pslot(z0)), p);
+    for (int z = z0; z < z1; z++) {
+      __syncthreads();
+      if (tid == 0 && z + 3 <= z1 + 1) issue(z + 3);
+      wait(z + 2);
+      if (tid < A1)
+        stress_ring_cell<T, DIM>(tid, sQ(qslot(z + 1)), sQ(qslot(z)), sQ(qslot(z + 2)),
+                                 sP(pslot(z + 1)), p);
+      if (__syncthreads_or(late)) {
+        abort_block();
+        return;
+      }
+      lb_cell(z);
+    }
+  }
+  (void)NPI;
+}
+
+// ---------------------------------------------------------------------------
+// Beris-Edwards kernel
+// ---------------------------------------------------------------------------
+template <class Lat, class T>
+struct BeCfg {
+  static constexpr int DIM = Lat::DIM;
+  static constexpr int NSQ = DIM == 3 ? 4 : 1;   // Q^n plane slots
+  static constexpr int NSU = DIM == 3 ? 5 : 1;   // u plane slots
+  static constexpr int NSP = DIM == 3 ? 3 : 1;   // Q^P plane slots
+  static constexpr int NSR = DIM == 3 ? 2 : 1;   // R(Q^n) plane slots
+  static constexpr size_t q_slot = align128<T>(sizeof(T) * 5 * BA);
+  static constexpr size_t u_slot = align128<T>(sizeof(T) * DIM * BA);
+  static constexpr size_t p_slot = align128<T>(sizeof(T) * 5 * A1);
+  static constexpr size_t off_u = NSQ * q_slot;
+  static constexpr size_t off_p = off_u + NSU * u_slot;
+  static constexpr size_t off_r = off_p + NSP * p_slot;
+  static constexpr size_t off_bar = off_r + NSR * p_slot;
+  static constexpr size_t bytes = off_bar + 8 * (NSQ + NSU);
+  static constexpr uint32_t q_tx = sizeof(T) * 5 * BA;
+  static constexpr uint32_t u_tx = sizeof(T) * DIM * BA;
+};
+
+// u and G[a][b] = d_b u_a at box offset o (z neighbours from the planes
+// above and below)
 template <class T, int DIM>
-__device__ __forceinline__ void tile_ugrad(const T* __restrict__ c,
-                                           const T* __restrict__ m,
-                                           const T* __restrict__ pp, int o,
-                                           T u[3], T G[3][3]) {
+__device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
+                                          const T* __restrict__ m,
+                                          const T* __restrict__ pp, int o,
+                                          T u[3], T G[3][3]) {
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     if (a < DIM) {
-      const T* F = c + a * A2;
+      const T* F = c + a * BA;
       u[a] = F[o];
       G[a][0] = (F[o + 1] - F[o - 1]) / T(2);
-      G[a][1] = (F[o + RX2] - F[o - RX2]) / T(2);
-      G[a][2] = DIM == 3 ? (pp[a * A2 + o] - m[a * A2 + o]) / T(2) : T(0);
+      G[a][1] = (F[o + BXW] - F[o - BXW]) / T(2);
+      G[a][2] = DIM == 3 ? (pp[a * BA + o] - m[a * BA + o]) / T(2) : T(0);
     } else {
       u[a] = T(0);
       G[a][0] = G[a][1] = G[a][2] = T(0);
@@ -239,108 +281,188 @@ __device__ __forceinline__ void tile_ugrad(const T* __restrict__ c,
 }
 
 template <class Lat, class T>
-__global__ void __launch_bounds__(FNT) k_fused_be(const T* __restrict__ Q,
-                                                  const T* __restrict__ U,
-                                                  T* __restrict__ Qout, Dims d,
-                                                  Par<T> p, int tz) {
+__global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
+    k_fused_be(const __grid_constant__ CUtensorMap qmap,
+               const __grid_constant__ CUtensorMap umap, Field<T> Qout, Dims d,
+               Par<T> p, int tz, int zoff, unsigned* __restrict__ err) {
+  using C = BeCfg<Lat, T>;
   constexpr int DIM = Lat::DIM;
-  using S = BeSmem<Lat, T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sQ = reinterpret_cast<T*>(smem_raw);  // [NQ][5][A2]
-  T* sU = sQ + S::NQ * 5 * A2;             // [NU][DIM][A2]
-  T* sQP = sU + S::NU * DIM * A2;          // [NQP][5][A1]
-  T* sR = sQP + S::NQP * 5 * A1;           // [NR][5][A1]
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* qbar = reinterpret_cast<uint64_t*>(smem + C::off_bar);
+  uint64_t* ubar = qbar + C::NSQ;
+  auto sQ = [&](int s) { return reinterpret_cast<T*>(smem + s * C::q_slot); };
+  auto sU = [&](int s) { return reinterpret_cast<T*>(smem + C::off_u + s * C::u_slot); };
+  auto sQP = [&](int s) { return reinterpret_cast<T*>(smem + C::off_p + s * C::p_slot); };
+  auto sR = [&](int s) { return reinterpret_cast<T*>(smem + C::off_r + s * C::p_slot); };
 
+  const int tid = threadIdx.x;
   const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
-  const int tx = threadIdx.x % FTX, ty = threadIdx.x / FTX;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool inside = x < d.nx && y < d.ny;
   const int z0 = DIM == 3 ? blockIdx.z * tz : 0;
+  const int z1 = DIM == 3 ? min(z0 + tz, d.nz) : 1;
+  const int zl0 = DIM == 3 ? z0 - 2 : 0;  // first loaded plane
+  const int zr0 = DIM == 3 ? z0 - 1 : 0;  // first predicted plane
+  auto qs = [&](int z) { return (z - zl0) % C::NSQ; };
+  auto qpar = [&](int z) { return (uint32_t)(((z - zl0) / C::NSQ) & 1); };
+  auto us = [&](int z) { return (z - zl0) % C::NSU; };
+  auto upar = [&](int z) { return (uint32_t)(((z - zl0) / C::NSU) & 1); };
+  auto ps = [&](int z) { return (z - zr0) % C::NSP; };
+  auto rs = [&](int z) { return (z - zr0) % C::NSR; };
 
-  auto sq = [&](int z) { return sQ + ((z - z0 + 6) % S::NQ) * 5 * A2; };
-  auto su = [&](int z) { return sU + ((z - z0 + 8) % S::NU) * DIM * A2; };
-  auto sqp = [&](int z) { return sQP + ((z - z0 + 6) % S::NQP) * 5 * A1; };
-  auto sr = [&](int z) { return sR + ((z - z0 + 6) % S::NR) * 5 * A1; };
-
-  // predictor on the 1-ring region of plane z: R(Q^n) and Q^P = Q^n + R
-  auto predict_plane = [&](int z) {
-    const T* qc = sq(z);
-    const T* qm = DIM == 3 ? sq(z - 1) : qc;
-    const T* qpn = DIM == 3 ? sq(z + 1) : qc;
-    const T* uc = su(z);
-    const T* um = DIM == 3 ? su(z - 1) : uc;
-    const T* upn = DIM == 3 ? su(z + 1) : uc;
-    T* qp_out = sqp(z);
-    T* r_out = sr(z);
-    for (int c = threadIdx.x; c < A1; c += FNT) {
-      const int o = (c / RX1 + 1) * RX2 + (c % RX1 + 1);
-      T q[5], dq[3][5], lap[5], u[3], G[3][3], r[5];
-      tile_stencil5<T, DIM, RX2, A2>(qc, qm, qpn, o, q, dq, lap);
-      tile_ugrad<T, DIM>(uc, um, upn, o, u, G);
-      be_rhs<T, DIM>(q, dq, lap, u, G, p, r);
-#pragma unroll
-      for (int k = 0; k < 5; k++) {
-        r_out[k * A1 + c] = r[k];
-        qp_out[k * A1 + c] = q[k] + r[k];
-      }
+  if (tid == 0) {
+    for (int s = 0; s < C::NSQ + C::NSU; s++) mbar_init(&qbar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue_q = [&](int z) {
+    const int s = qs(z);
+    mbar_expect_tx(&qbar[s], C::q_tx);
+    tma_load_4d(sQ(s), &qmap, x0, y0, z + zoff, 0, &qbar[s]);
+  };
+  auto issue_u = [&](int z) {
+    const int s = us(z);
+    mbar_expect_tx(&ubar[s], C::u_tx);
+    tma_load_4d(sU(s), &umap, x0, y0, z + zoff, 0, &ubar[s]);
+  };
+  bool late = false;
+  auto wait_q = [&](int z) { late |= !mbar_wait(&qbar[qs(z)], qpar(z)); };
+  auto wait_u = [&](int z) { late |= !mbar_wait(&ubar[us(z)], upar(z)); };
+  auto abort_block = [&]() {
+    if (tid == 0) {
+      atomicExch(err, DEV_ERR_TMA_TIMEOUT);
+      for (int s = 0; s < C::NSQ + C::NSU; s++)
+        (void)mbar_wait(&qbar[s], 0), (void)mbar_wait(&qbar[s], 1);
     }
   };
 
-  // corrector at the tile cells of plane z
-  auto correct_cell = [&](int z) {
-    if (!inside || z >= d.nz) return;
-    const int ic = (ty + 1) * RX1 + (tx + 1);
-    const int o2 = (ty + 2) * RX2 + (tx + 2);
-    const T* pc = sqp(z);
-    const T* pm = DIM == 3 ? sqp(z - 1) : pc;
-    const T* ppn = DIM == 3 ? sqp(z + 1) : pc;
-    T qp[5], dq[3][5], lap[5], u[3], G[3][3], r2[5];
-    tile_stencil5<T, DIM, RX1, A1>(pc, pm, ppn, ic, qp, dq, lap);
-    tile_ugrad<T, DIM>(su(z), DIM == 3 ? su(z - 1) : su(z),
-                       DIM == 3 ? su(z + 1) : su(z), o2, u, G);
-    be_rhs<T, DIM>(qp, dq, lap, u, G, p, r2);
-    const T* qn = sq(z);
-    const T* r1 = sr(z);
-    const int64_t cell = cell_of(d, x, y, z);
+  // predictor on ring cell c of plane z: R(Q^n) and Q^P = Q^n + R
+  auto predict = [&](int z, int c) {
+    const int o = box_at(c % RX1 - 1, c / RX1 - 1);
+    const T* qc = sQ(qs(z));
+    const T* qm = DIM == 3 ? sQ(qs(z - 1)) : qc;
+    const T* qp = DIM == 3 ? sQ(qs(z + 1)) : qc;
+    const T* uc = sU(us(z));
+    const T* um = DIM == 3 ? sU(us(z - 1)) : uc;
+    const T* up = DIM == 3 ? sU(us(z + 1)) : uc;
+    T q[5], dq[3][5], lap[5], u[3], G[3][3], r[5];
 #pragma unroll
-    for (int k = 0; k < 5; k++)
-      Qout[k * d.n + cell] = qn[k * A2 + o2] + (r1[k * A1 + ic] + r2[k]) / T(2);
+    for (int k = 0; k < 5; k++) {
+      const T* F = qc + k * BA;
+      const T v = F[o], xp = F[o + 1], xm = F[o - 1], yp = F[o + BXW], ym = F[o - BXW];
+      q[k] = v;
+      dq[0][k] = (xp - xm) / T(2);
+      dq[1][k] = (yp - ym) / T(2);
+      T l = (xp + xm - T(2) * v) + (yp + ym - T(2) * v);
+      if (DIM == 3) {
+        const T zp = qp[k * BA + o], zm = qm[k * BA + o];
+        dq[2][k] = (zp - zm) / T(2);
+        l += zp + zm - T(2) * v;
+      } else {
+        dq[2][k] = T(0);
+      }
+      lap[k] = l;
+    }
+    box_ugrad<T, DIM>(uc, um, up, o, u, G);
+    be_rhs<T, DIM>(q, dq, lap, u, G, p, r);
+    T* qpo = sQP(ps(z));
+    T* ro = sR(rs(z));
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+      ro[k * A1 + c] = r[k];
+      qpo[k * A1 + c] = q[k] + r[k];
+    }
+  };
+
+  const int tx = tid % FTX, ty = tid / FTX;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool cell = tid < FTX * FTY && x < d.nx && y < d.ny;
+  const int ic = (ty + 1) * RX1 + (tx + 1);
+  const int o2 = box_at(tx, ty);
+
+  // corrector at the tile cell of this thread on plane z
+  auto correct = [&](int z) {
+    if (!cell) return;
+    const T* pc = sQP(ps(z));
+    const T* pm = DIM == 3 ? sQP(ps(z - 1)) : pc;
+    const T* pp = DIM == 3 ? sQP(ps(z + 1)) : pc;
+    T qp[5], dq[3][5], lap[5], u[3], G[3][3], r2[5], out[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+      const T* F = pc + k * A1;
+      const T v = F[ic], xp = F[ic + 1], xm = F[ic - 1], yp = F[ic + RX1], ym = F[ic - RX1];
+      qp[k] = v;
+      dq[0][k] = (xp - xm) / T(2);
+      dq[1][k] = (yp - ym) / T(2);
+      T l = (xp + xm - T(2) * v) + (yp + ym - T(2) * v);
+      if (DIM == 3) {
+        const T zp = pp[k * A1 + ic], zm = pm[k * A1 + ic];
+        dq[2][k] = (zp - zm) / T(2);
+        l += zp + zm - T(2) * v;
+      } else {
+        dq[2][k] = T(0);
+      }
+      lap[k] = l;
+    }
+    box_ugrad<T, DIM>(sU(us(z)), DIM == 3 ? sU(us(z - 1)) : sU(us(z)),
+                      DIM == 3 ? sU(us(z + 1)) : sU(us(z)), o2, u, G);
+    be_rhs<T, DIM>(qp, dq, lap, u, G, p, r2);
+    const T* qn = sQ(qs(z));
+    const T* r1 = sR(rs(z));
+#pragma unroll
+    for (int k = 0; k < 5; k++) out[k] = qn[k * BA + o2] + (r1[k * A1 + ic] + r2[k]) / T(2);
+    store_with_images<T, 5, DIM>(Qout, d, x, y, z, out);
   };
 
   if constexpr (DIM == 2) {
-    stage_plane<T>(Q, 5, d, x0, y0, 0, sq(0));
-    stage_plane<T>(U, DIM, d, x0, y0, 0, su(0));
-    __syncthreads();
-    predict_plane(0);
-    __syncthreads();
-    correct_cell(0);
-  } else {
-    const int z1 = min(z0 + tz, d.nz);
-    for (int z = z0 - 2; z <= z0; z++) {
-      stage_plane<T>(Q, 5, d, x0, y0, z, sq(z));
-      stage_plane<T>(U, DIM, d, x0, y0, z, su(z));
+    if (tid == 0) {
+      issue_q(0);
+      issue_u(0);
     }
-    __syncthreads();
-    predict_plane(z0 - 1);
-    __syncthreads();
-    stage_plane<T>(Q, 5, d, x0, y0, z0 + 1, sq(z0 + 1));
-    stage_plane<T>(U, DIM, d, x0, y0, z0 + 1, su(z0 + 1));
-    __syncthreads();
-    predict_plane(z0);
+    wait_q(0);
+    wait_u(0);
+    if (tid < A1) predict(0, tid);
+    if (__syncthreads_or(late)) {
+      abort_block();
+      return;
+    }
+    correct(0);
+  } else {
+    if (tid == 0) {
+      for (int z = z0 - 2; z <= z0 + 1; z++) issue_q(z);
+      for (int z = z0 - 2; z <= z0 + 2; z++) issue_u(z);
+    }
+    for (int z = z0 - 2; z <= z0; z++) {
+      wait_q(z);
+      wait_u(z);
+    }
+    if (tid < A1) predict(z0 - 1, tid);
+    if (__syncthreads_or(late)) {
+      abort_block();
+      return;
+    }
+    if (tid == 0) issue_q(z0 + 2);
+    wait_q(z0 + 1);
+    wait_u(z0 + 1);
+    if (tid < A1) predict(z0, tid);
     for (int z = z0; z < z1; z++) {
       __syncthreads();
-      stage_plane<T>(Q, 5, d, x0, y0, z + 2, sq(z + 2));
-      stage_plane<T>(U, DIM, d, x0, y0, z + 2, su(z + 2));
-      __syncthreads();
-      predict_plane(z + 1);
-      __syncthreads();
-      correct_cell(z);
+      if (tid == 0 && z + 3 <= z1 + 1) {
+        issue_q(z + 3);
+        issue_u(z + 3);
+      }
+      wait_q(z + 2);
+      wait_u(z + 2);
+      if (tid < A1) predict(z + 1, tid);
+      if (__syncthreads_or(late)) {
+        abort_block();
+        return;
+      }
+      correct(z);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// launchers
+// launch helpers
 // ---------------------------------------------------------------------------
 template <class Lat>
 __host__ inline dim3 fused_grid(const Dims& d, int tz) {
@@ -348,52 +470,52 @@ __host__ inline dim3 fused_grid(const Dims& d, int tz) {
               Lat::DIM == 3 ? (unsigned)((d.nz + tz - 1) / tz) : 1u);
 }
 
+// z planes per block on D3Q19: enough blocks for several waves over the SMs
+// while amortising the two-plane prologue of each chunk
 template <class Lat>
 __host__ inline int fused_tz(const Dims& d) {
   if (Lat::DIM == 2) return 1;
-  // enough blocks for several waves over the SMs while amortising the
-  // z ring prologue
   const int64_t tiles = (int64_t)((d.nx + FTX - 1) / FTX) * ((d.ny + FTY - 1) / FTY);
-  int tz = 16;
+  int tz = 32;
   while (tz > 4 && tiles * ((d.nz + tz - 1) / tz) < 1200) tz /= 2;
   return tz < d.nz ? tz : d.nz;
 }
 
-template <class Lat, class T>
-cudaError_t launch_fused_lb(const T* gin, T* gout, const T* Q, T* U,
-                            const Dims& d, const Par<T>& p, cudaStream_t st) {
-  static unsigned long long configured = 0;  // one bit per device
-  const size_t smem = LbSmem<Lat, T>::bytes;
+template <class K>
+inline cudaError_t set_smem(K kernel, size_t bytes, unsigned long long* done_mask) {
   int dev = 0;
-  cudaGetDevice(&dev);
-  if (!(configured >> (dev & 63) & 1ull)) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_lb<Lat, T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << (dev & 63);
-  }
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (*done_mask & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) *done_mask |= bit;
+  return e;
+}
+
+template <class Lat, class T>
+cudaError_t launch_fused_lb(const CUtensorMap& qmap, const T* gin, T* gout,
+                            const Field<T>& U, const Dims& d, const Par<T>& p,
+                            unsigned* err, cudaStream_t st) {
+  static unsigned long long configured = 0;
+  cudaError_t e = set_smem(k_fused_lb<Lat, T>, LbCfg<Lat, T>::bytes, &configured);
+  if (e != cudaSuccess) return e;
   const int tz = fused_tz<Lat>(d);
-  k_fused_lb<Lat, T><<<fused_grid<Lat>(d, tz), FNT, smem, st>>>(gin, gout, Q, U, d, p, tz);
+  k_fused_lb<Lat, T><<<fused_grid<Lat>(d, tz), FNT, LbCfg<Lat, T>::bytes, st>>>(
+      qmap, gin, gout, U, d, p, tz, U.L.zoff, err);
   return cudaGetLastError();
 }
 
 template <class Lat, class T>
-cudaError_t launch_fused_be(const T* Q, const T* U, T* Qout, const Dims& d,
-                            const Par<T>& p, cudaStream_t st) {
-  static unsigned long long configured = 0;  // one bit per device
-  const size_t smem = BeSmem<Lat, T>::bytes;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (!(configured >> (dev & 63) & 1ull)) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_be<Lat, T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << (dev & 63);
-  }
+cudaError_t launch_fused_be(const CUtensorMap& qmap, const CUtensorMap& umap,
+                            const Field<T>& Qout, const Dims& d, const Par<T>& p,
+                            unsigned* err, cudaStream_t st) {
+  static unsigned long long configured = 0;
+  cudaError_t e = set_smem(k_fused_be<Lat, T>, BeCfg<Lat, T>::bytes, &configured);
+  if (e != cudaSuccess) return e;
   const int tz = fused_tz<Lat>(d);
-  k_fused_be<Lat, T><<<fused_grid<Lat>(d, tz), FNT, smem, st>>>(Q, U, Qout, d, p, tz);
+  k_fused_be<Lat, T><<<fused_grid<Lat>(d, tz), FNT, BeCfg<Lat, T>::bytes, st>>>(
+      qmap, umap, Qout, d, p, tz, Qout.L.zoff, err);
   return cudaGetLastError();
 }
 

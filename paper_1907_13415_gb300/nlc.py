@@ -86,6 +86,8 @@ def load(build_if_missing=True):
         "nlc_destroy": ([P], None),
         "nlc_lattice_velocities": ([I32, P, P], I32),
         "nlc_set_timing": ([P, I32], I32),
+        "nlc_save": ([P, P, ctypes.POINTER(ctypes.c_size_t)], I32),
+        "nlc_load": ([P, P, ctypes.c_size_t], I32),
         "nlc_get_timing": ([P, I32, P, P, P], I32),
         "nlc_timing_name": ([I32], ctypes.c_char_p),
         "nlc_version": ([], ctypes.c_char_p),
@@ -103,7 +105,7 @@ def exported_symbols():
             "nlc_get_fields", "nlc_get_populations", "nlc_step",
             "nlc_observables", "nlc_last_error", "nlc_destroy",
             "nlc_lattice_velocities", "nlc_version", "nlc_set_timing",
-            "nlc_get_timing", "nlc_timing_name"]
+            "nlc_get_timing", "nlc_timing_name", "nlc_save", "nlc_load"]
 
 
 def _check(ctx, status):
@@ -197,6 +199,21 @@ def nlc_get_timing(ctx):
             for k in range(n.value)}
 
 
+def nlc_save(ctx):
+    """The context's checkpoint as bytes."""
+    lib = load()
+    n = ctypes.c_size_t(0)
+    _check(ctx, lib.nlc_save(ctx, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(ctx, lib.nlc_save(ctx, buf, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def nlc_load(ctx, data):
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(ctx, load().nlc_load(ctx, buf, len(data)))
+
+
 def nlc_version():
     return load().nlc_version().decode()
 
@@ -257,6 +274,12 @@ class Simulation:
         if profile:
             d["s_profile"] = prof
         return d
+
+    def save(self):
+        return nlc_save(self.ctx)
+
+    def load_state(self, data):
+        nlc_load(self.ctx, data)
 
     def close(self):
         if self.ctx:

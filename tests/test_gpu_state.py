@@ -1,0 +1,73 @@
+"""Checkpoints (nlc_save / nlc_load) and the device-side error paths."""
+import numpy as np
+import pytest
+
+from paper_1907_13415_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def make(w, precision):
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    return nlc.Simulation(w.lattice, w.shape, w.params, precision=precision,
+                          stream=torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("lattice,shape", [(wl.D2Q9, (1, 20, 45)),
+                                           (wl.D3Q19, (10, 12, 34))])
+def test_resume_is_bitwise_identical(lattice, shape, precision):
+    base = wl.flat_128x8() if lattice == wl.D2Q9 else wl.sphere_256()
+    w = base.with_(lattice=lattice, shape=shape, geometry="ball",
+                   size=0.3 * min(shape[1:]), noise=1e-3)
+    a = make(w, precision)
+    a.set_fields(w.initial_q5())
+    a.step(7)
+    blob = a.save()
+    a.step(9)
+    fa = a.get_populations()
+    Qa, _, _ = a.get_fields()
+    b = make(w, precision)
+    b.load_state(blob)
+    b.step(9)
+    fb = b.get_populations()
+    Qb, _, _ = b.get_fields()
+    assert np.array_equal(fa, fb) and np.array_equal(Qa, Qb)
+    assert b.observables()["step"] == 16
+    a.close()
+    b.close()
+
+
+def test_corrupt_or_mismatched_checkpoint_is_rejected():
+    from paper_1907_13415_gb300 import nlc
+    w = wl.flat_128x8().with_(shape=(1, 8, 40), size=20)
+    a = make(w, 0)
+    a.set_fields(w.initial_q5())
+    a.step(3)
+    blob = bytearray(a.save())
+    Q0, _, _ = a.get_fields()
+    bad = bytearray(blob)
+    bad[-5] ^= 0x40
+    with pytest.raises(nlc.NlcError) as ei:
+        a.load_state(bytes(bad))
+    assert ei.value.status == -6
+    Q1, _, _ = a.get_fields()
+    assert np.array_equal(Q0, Q1)  # state untouched
+    other = make(w.with_(shape=(1, 8, 41)), 0)
+    with pytest.raises(nlc.NlcError) as ei:
+        other.load_state(bytes(blob))
+    assert ei.value.status == -1
+    with pytest.raises(nlc.NlcError) as ei:
+        a.load_state(bytes(blob[:100]))
+    assert ei.value.status == -1
+    a.close()
+    other.close()
