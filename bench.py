@@ -377,6 +377,72 @@ def run_ours(args, w):
     return 0
 
 
+def run_sweep(args):
+    """Batched temperature sweep: 64 flat-interface D2Q9 lattices of uneven
+    extents (gamma over [2.60, 2.80]) advanced by the same launches and
+    replayed as CUDA graphs, against the same lattices stepped one context
+    after another."""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    from paper_1907_13415_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ws = wl.sweep_64()
+    cells = sum(w.n_cells for w in ws)
+    b = nlc.Batch(wl.D2Q9, [w.shape for w in ws], [w.params for w in ws],
+                  precision=nlc.NLC_FP32, stream=stream.cuda_stream,
+                  graph_steps=args.graph_steps)
+    for i, w in enumerate(ws):
+        b.set_fields(i, w.initial_q5())
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    b.step(max(args.warmup, args.graph_steps))
+    t_batch = timed(b.step, args.steps)
+    b.close()
+    sims = []
+    for w in ws:
+        s = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                           stream=stream.cuda_stream)
+        s.set_fields(w.initial_q5())
+        sims.append(s)
+
+    def seq(steps):
+        for _ in range(steps):
+            for s in sims:
+                s.step(1)
+
+    seq(args.warmup)
+    t_seq = timed(seq, args.steps)
+    for s in sims:
+        s.close()
+    v_b = cells * args.steps / (t_batch * 1e-3) / 1e6
+    v_s = cells * args.steps / (t_seq * 1e-3) / 1e6
+    out = {"metric": "MLUPS, batched temperature sweep vs sequential contexts",
+           "value": v_b, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_batch / args.steps,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "sweep_64 flat interfaces, D2Q9, "
+                                  "Lx in {256..2048}, Ly in {8,16,64}, "
+                                  "gamma in [2.60, 2.80]",
+                      "instances": len(ws), "cells": cells,
+                      "graph_steps": args.graph_steps},
+           "sequential": {"value": v_s, "unit": UNIT,
+                          "ms_per_step": t_seq / args.steps,
+                          "launches_per_step": 2 * len(ws)},
+           "batched_over_sequential": t_seq / t_batch}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,10 +457,16 @@ def main():
                          "(profiling captures); the reported workload is "
                          "the default 256^3")
     ap.add_argument("--schedule", default="fused", choices=["fused", "unfused"])
+    ap.add_argument("--workload", default="sphere256",
+                    choices=["sphere256", "sweep64"],
+                    help="sweep64: batched vs sequential temperature sweep")
+    ap.add_argument("--graph-steps", type=int, default=50)
     args = ap.parse_args()
     # at least three untimed warm-up steps (reported as the count used)
     args.warmup = max(args.warmup, 3)
     from paper_1907_13415_gb300 import workloads as wl
+    if args.workload == "sweep64":
+        return run_sweep(args)
     w = wl.sphere_256()
     if args.shape:
         nz, ny, nx = (int(v) for v in args.shape.split(","))

@@ -121,13 +121,34 @@ typedef struct nlc_ctx nlc_ctx;
 NLC_API nlc_status nlc_create(const nlc_grid* grid, const nlc_params* params,
                       void* stream, nlc_ctx** out);
 
+/* Creates one context holding n independent lattices that nlc_step advances
+ * together (for example a sweep over gamma, Sec. 2.1's interface velocity
+ * against temperature): every kernel launch of a step covers the tiles of
+ * all n lattices.  The lattices share the lattice type and precision; their
+ * extents and parameters may differ.  grids and params are arrays of n
+ * entries (copied).  Instance i (0 <= i < n) is addressed by the inst
+ * argument of the calls below.  Errors as nlc_create, and NLC_EINVAL for
+ * n < 1 or mixed lattice types or precisions. */
+NLC_API nlc_status nlc_create_batch(int32_t n, const nlc_grid* grids,
+                                    const nlc_params* params, void* stream,
+                                    nlc_ctx** out);
+
+/* Number of lattices in the context (-1 for NULL). */
+NLC_API int32_t nlc_count(const nlc_ctx* ctx);
+
+/* steps > 0: nlc_step replays whole chunks of `steps` fused time steps as
+ * one captured CUDA graph (captured on first use, on a private stream, and
+ * launched on the context's stream); 0 (default) launches kernels directly.
+ * Not used while timing is enabled. */
+NLC_API nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps);
+
 /* Selects the kernel schedule (NLC_SCHED_*) for later nlc_step calls. */
 NLC_API nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule);
 
-/* Replaces the state with Q5, rho and u (host float64, layouts above).  The
- * populations are set to the equilibrium f_i^eq(rho, u) of Sec. 1.2.1.
- * rho may be NULL (rho0 everywhere) and u may be NULL (at rest).  The step
- * counter restarts at 0.  inst must be 0 for a single-lattice context.
+/* Replaces the state of lattice inst with Q5, rho and u (host float64,
+ * layouts above).  The populations are set to the equilibrium
+ * f_i^eq(rho, u) of Sec. 1.2.1.  rho may be NULL (rho0 everywhere) and u may
+ * be NULL (at rest).  The lattice's step counter restarts at 0.
  * Synchronises the stream.  Errors: NLC_EINVAL (null Q5, inst out of range),
  * NLC_EUNSTABLE (a non-finite input value; the state is then undefined),
  * NLC_ECUDA. */
@@ -154,18 +175,19 @@ NLC_API nlc_status nlc_step(nlc_ctx* ctx, int64_t n);
 NLC_API nlc_status nlc_observables(nlc_ctx* ctx, int32_t inst, nlc_obs* out,
                            double* s_profile);
 
-/* Checkpoint of a single-lattice context: a header (magic "NLCSTATE",
- * format version, grid, parameters, step count), the populations and the Q
- * components exactly as stored on the device (bitwise, in the context's
- * precision), and a checksum (64-bit FNV-1a over 8-byte little-endian words
- * of the payload).  buf == NULL: *len receives the size needed.  Otherwise
+/* Checkpoint of a context: a header (magic "NLCSTATE", format version,
+ * lattice count, a hash of the grids and parameters), then the payload: the
+ * per-lattice step counters and, lattice by lattice, the populations and the
+ * Q components exactly as stored on the device (bitwise, in the context's
+ * precision); the header carries a checksum of the payload (64-bit FNV-1a
+ * over 8-byte little-endian words, then the tail bytes).  buf == NULL: *len receives the size needed.  Otherwise
  * *len must be at least that size and receives the bytes written.  The
  * caller owns buf.  Synchronises the stream.  Errors: NLC_EINVAL (small
  * buffer, null len), NLC_ECUDA. */
 NLC_API nlc_status nlc_save(nlc_ctx* ctx, void* buf, size_t* len);
 
-/* Restores a checkpoint written by nlc_save into a context of the same grid
- * (extents, lattice, precision) and parameters; continuing from it gives the
+/* Restores a checkpoint written by nlc_save into a context of the same
+ * lattices (extents, lattice type, precision) and parameters; continuing from it gives the
  * same results, bit for bit, as never having stopped.  Errors: NLC_EINVAL
  * (not a checkpoint, other grid or parameters, short buffer), NLC_ECORRUPT
  * (checksum mismatch; the state is left unchanged), NLC_ECUDA. */

@@ -1,5 +1,6 @@
-// engine.cuh -- the templated engine: device buffers of one lattice and the
-// launch sequences of the step, set-up, read-back and observables.
+// engine.cuh -- the templated engine: device buffers of one or more lattices
+// (a batch: same lattice type and precision, any extents and parameters) and
+// the launch sequences of the step, set-up, read-back and observables.
 #pragma once
 #include <cmath>
 #include <cstdio>
@@ -30,65 +31,121 @@ namespace nlc {
     }                                                                      \
   } while (0)
 
+// host-side record of one lattice
+template <class T>
+struct InstHost {
+  Dims d;
+  Layout L;
+  Par<T> p;
+  T* g[2] = {nullptr, nullptr};
+  Field<T> q[2];
+  Field<T> u;
+  int tz = 1;
+  // lazily allocated: unfused schedule, read-back staging, checkpoints
+  T* pi = nullptr;
+  Field<T> qp;
+  T* r1 = nullptr;
+  T* raw = nullptr;
+  double* stage = nullptr;
+  double* fstage = nullptr;
+  double* partial = nullptr;
+  double* prof_partial = nullptr;
+  double* prof = nullptr;
+  int obs_blocks = 1;
+};
+
 template <class Lat, class T>
 class Engine final : public EngineBase {
  public:
   static constexpr int Q = Lat::Q;
   static constexpr int DIM = Lat::DIM;
 
-  explicit Engine(const EngineArgs& a) : args_(a) {
-    d_.nx = a.grid.nx;
-    d_.ny = a.grid.ny;
-    d_.nz = a.grid.nz;
-    d_.n = (int64_t)a.grid.nx * a.grid.ny * a.grid.nz;
-    L_ = make_layout(d_, DIM == 3);
-    const nlc_params& q = a.params;
-    p_.A0 = (T)q.A0;
-    p_.K = (T)q.K;
-    p_.gamma = (T)q.gamma;
-    p_.Gamma = (T)q.Gamma;
-    p_.xi = (T)q.xi;
-    p_.tau = (T)q.tau;
-    p_.rho0 = (T)q.rho0;
-    p_.inv_tau = (T)(1.0 / q.tau);
-    p_.guo = (T)(1.0 - 1.0 / (2.0 * q.tau));
-  }
+  explicit Engine(const EngineArgs& a) : args_(a) {}
 
   ~Engine() override {
+    for (int c = 0; c < 2; c++)
+      if (graph_[c]) cudaGraphExecDestroy(graph_[c]);
+    if (cap_stream_) cudaStreamDestroy(cap_stream_);
     for (void* ptr : allocs_) cudaFree(ptr);
   }
 
   nlc_status init() {
-    const int64_t n = d_.n;
-    nlc_status s;
-    T *q0, *q1, *u;
-    if ((s = alloc(&g_[0], (size_t)Q * n)) || (s = alloc(&g_[1], (size_t)Q * n)) ||
-        (s = alloc(&q0, (size_t)5 * L_.comp)) || (s = alloc(&q1, (size_t)5 * L_.comp)) ||
-        (s = alloc(&u, (size_t)DIM * L_.comp)) || (s = alloc(&bad_, 1)) ||
-        (s = alloc(&derr_, 1)))
-      return s;
-    q_[0] = Field<T>{q0, L_};
-    q_[1] = Field<T>{q1, L_};
-    u_ = Field<T>{u, L_};
+    const int n = args_.n;
+    inst_.resize(n);
+    std::vector<InstDev<T>> dev(n);
+    std::vector<CUtensorMap> qmaps(2 * n), umaps(n);
+    std::vector<TileRef> tiles;
+    int64_t tiles_so_far = 0;
+    maps_ok_ = true;
     cudaStream_t st = args_.stream;
-    NLC_CK(cudaMemsetAsync(g_[0], 0, sizeof(T) * Q * n, st));
-    NLC_CK(cudaMemsetAsync(q0, 0, sizeof(T) * 5 * L_.comp, st));
-    NLC_CK(cudaMemsetAsync(q1, 0, sizeof(T) * 5 * L_.comp, st));
-    NLC_CK(cudaMemsetAsync(u, 0, sizeof(T) * DIM * L_.comp, st));
+    nlc_status s;
+    for (int i = 0; i < n; i++) {
+      InstHost<T>& I = inst_[i];
+      const nlc_grid& g = args_.grids[i];
+      const nlc_params& q = args_.params[i];
+      I.d = Dims{g.nx, g.ny, g.nz, (int64_t)g.nx * g.ny * g.nz};
+      I.L = make_layout(I.d, DIM == 3);
+      I.p.A0 = (T)q.A0;
+      I.p.K = (T)q.K;
+      I.p.gamma = (T)q.gamma;
+      I.p.Gamma = (T)q.Gamma;
+      I.p.xi = (T)q.xi;
+      I.p.tau = (T)q.tau;
+      I.p.rho0 = (T)q.rho0;
+      I.p.inv_tau = (T)(1.0 / q.tau);
+      I.p.guo = (T)(1.0 - 1.0 / (2.0 * q.tau));
+      T *q0, *q1, *u;
+      if ((s = alloc(&I.g[0], (size_t)Q * I.d.n)) || (s = alloc(&I.g[1], (size_t)Q * I.d.n)) ||
+          (s = alloc(&q0, (size_t)5 * I.L.comp)) || (s = alloc(&q1, (size_t)5 * I.L.comp)) ||
+          (s = alloc(&u, (size_t)DIM * I.L.comp)))
+        return s;
+      I.q[0] = Field<T>{q0, I.L};
+      I.q[1] = Field<T>{q1, I.L};
+      I.u = Field<T>{u, I.L};
+      NLC_CK(cudaMemsetAsync(I.g[0], 0, sizeof(T) * Q * I.d.n, st));
+      NLC_CK(cudaMemsetAsync(I.g[1], 0, sizeof(T) * Q * I.d.n, st));
+      NLC_CK(cudaMemsetAsync(q0, 0, sizeof(T) * 5 * I.L.comp, st));
+      NLC_CK(cudaMemsetAsync(q1, 0, sizeof(T) * 5 * I.L.comp, st));
+      NLC_CK(cudaMemsetAsync(u, 0, sizeof(T) * DIM * I.L.comp, st));
+      maps_ok_ = maps_ok_ &&
+                 encode_field_map<T>(&qmaps[2 * i], q0, I.L.nxp, I.L.nyp, I.L.nzp, 5, BXW, BYH) &&
+                 encode_field_map<T>(&qmaps[2 * i + 1], q1, I.L.nxp, I.L.nyp, I.L.nzp, 5, BXW, BYH) &&
+                 encode_field_map<T>(&umaps[i], u, I.L.nxp, I.L.nyp, I.L.nzp, DIM, BXW, BYH);
+      I.tz = fused_tz<Lat>(I.d, tiles_so_far);
+      append_tiles<Lat>(i, I.d, I.tz, &tiles);
+      tiles_so_far = (int64_t)tiles.size();
+      dev[i].d = I.d;
+      dev[i].p = I.p;
+      dev[i].g[0] = I.g[0];
+      dev[i].g[1] = I.g[1];
+      dev[i].q[0] = I.q[0];
+      dev[i].q[1] = I.q[1];
+      dev[i].u = I.u;
+      dev[i].tz = I.tz;
+    }
+    if ((s = alloc(&bad_, 1)) || (s = alloc(&derr_, 1)) || (s = alloc(&insts_dev_, (size_t)n)) ||
+        (s = alloc(&qmaps_dev_, (size_t)2 * n)) || (s = alloc(&umaps_dev_, (size_t)n)) ||
+        (s = alloc(&tiles_dev_, tiles.size())))
+      return s;
+    ntiles_ = (int)tiles.size();
     NLC_CK(cudaMemsetAsync(derr_, 0, sizeof(unsigned), st));
-    // TMA descriptors of the three padded fields (pointers never change)
-    maps_ok_ = encode_field_map<T>(&qmap_[0], q0, L_.nxp, L_.nyp, L_.nzp, 5, BXW, BYH) &&
-               encode_field_map<T>(&qmap_[1], q1, L_.nxp, L_.nyp, L_.nzp, 5, BXW, BYH) &&
-               encode_field_map<T>(&umap_, u, L_.nxp, L_.nyp, L_.nzp, DIM, BXW, BYH);
+    NLC_CK(cudaMemcpyAsync(insts_dev_, dev.data(), sizeof(InstDev<T>) * n, cudaMemcpyHostToDevice, st));
+    NLC_CK(cudaMemcpyAsync(qmaps_dev_, qmaps.data(), sizeof(CUtensorMap) * 2 * n, cudaMemcpyHostToDevice, st));
+    NLC_CK(cudaMemcpyAsync(umaps_dev_, umaps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, st));
+    NLC_CK(cudaMemcpyAsync(tiles_dev_, tiles.data(), sizeof(TileRef) * tiles.size(), cudaMemcpyHostToDevice, st));
+    NLC_CK(cudaStreamSynchronize(st));
     return NLC_OK;
   }
+
+  int count() const override { return (int)inst_.size(); }
 
   // ---------------------------------------------------------------- step
   nlc_status step(int64_t n, int schedule) override {
     if (n <= 0) return NLC_OK;
     nlc_status s;
     if (schedule == NLC_SCHED_UNFUSED) {
-      if ((s = ensure_unfused())) return s;
+      for (auto& I : inst_)
+        if ((s = ensure_unfused(I))) return s;
       for (int64_t k = 0; k < n; k++)
         if ((s = step_unfused())) return s;
       return NLC_OK;
@@ -98,28 +155,37 @@ class Engine final : public EngineBase {
             "unfused schedule";
       return NLC_EUNSUPPORTED;
     }
+    // whole chunks of steps replay a captured CUDA graph (not while timing)
+    if (graph_steps > 0 && !timer.on) {
+      while (n >= graph_steps) {
+        if ((s = ensure_graph(cur_))) return s;
+        NLC_CK(cudaGraphLaunch(graph_[cur_], args_.stream));
+        if (graph_steps % 2) cur_ ^= 1;
+        n -= graph_steps;
+      }
+    }
     for (int64_t k = 0; k < n; k++)
-      if ((s = step_fused())) return s;
+      if ((s = step_fused(args_.stream))) return s;
     return NLC_OK;
   }
 
   // ---------------------------------------------------------------- I/O
-  nlc_status set_fields(const double* Q5, const double* rho,
+  nlc_status set_fields(int i, const double* Q5, const double* rho,
                         const double* u) override {
+    InstHost<T>& I = inst_[i];
     nlc_status s;
-    if ((s = ensure_staging())) return s;
-    const int64_t n = d_.n;
+    if ((s = ensure_staging(I))) return s;
+    const int64_t n = I.d.n;
     cudaStream_t st = args_.stream;
-    NLC_CK(cudaMemcpyAsync(stage_, Q5, sizeof(double) * 5 * n, cudaMemcpyHostToDevice, st));
+    NLC_CK(cudaMemcpyAsync(I.stage, Q5, sizeof(double) * 5 * n, cudaMemcpyHostToDevice, st));
     if (rho)
-      NLC_CK(cudaMemcpyAsync(stage_ + 5 * n, rho, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+      NLC_CK(cudaMemcpyAsync(I.stage + 5 * n, rho, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     if (u)
-      NLC_CK(cudaMemcpyAsync(stage_ + 6 * n, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+      NLC_CK(cudaMemcpyAsync(I.stage + 6 * n, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
     NLC_CK(cudaMemsetAsync(bad_, 0, sizeof(unsigned long long), st));
-    cur_ = 0;
     k_set_fields<Lat, T><<<grid1(n), 256, 0, st>>>(
-        stage_, rho ? stage_ + 5 * n : nullptr, u ? stage_ + 6 * n : nullptr,
-        q_[0], g_[0], d_, args_.params.rho0, bad_);
+        I.stage, rho ? I.stage + 5 * n : nullptr, u ? I.stage + 6 * n : nullptr,
+        I.q[cur_], I.g[cur_], I.d, args_.params[i].rho0, bad_);
     NLC_CK_LAUNCH("k_set_fields");
     unsigned long long nbad = 0;
     NLC_CK(cudaMemcpyAsync(&nbad, bad_, sizeof(nbad), cudaMemcpyDeviceToHost, st));
@@ -132,94 +198,114 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
-  nlc_status get_fields(double* Q5, double* rho, double* u) override {
+  nlc_status get_fields(int i, double* Q5, double* rho, double* u) override {
+    InstHost<T>& I = inst_[i];
     nlc_status s;
-    if ((s = ensure_staging())) return s;
-    const int64_t n = d_.n;
+    if ((s = ensure_staging(I))) return s;
+    const int64_t n = I.d.n;
     cudaStream_t st = args_.stream;
     if (Q5) {
-      k_field_out<T><<<grid1(n), 256, 0, st>>>(q_[cur_], 5, d_, stage_);
+      k_field_out<T><<<grid1(n), 256, 0, st>>>(I.q[cur_], 5, I.d, I.stage);
       NLC_CK_LAUNCH("k_field_out");
-      NLC_CK(cudaMemcpyAsync(Q5, stage_, sizeof(double) * 5 * n, cudaMemcpyDeviceToHost, st));
+      NLC_CK(cudaMemcpyAsync(Q5, I.stage, sizeof(double) * 5 * n, cudaMemcpyDeviceToHost, st));
     }
     if (rho || u) {
-      if ((s = moments_to_stage())) return s;
+      if ((s = moments_to_stage(I))) return s;
       if (rho)
-        NLC_CK(cudaMemcpyAsync(rho, stage_ + 5 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        NLC_CK(cudaMemcpyAsync(rho, I.stage + 5 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
       if (u)
-        NLC_CK(cudaMemcpyAsync(u, stage_ + 6 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+        NLC_CK(cudaMemcpyAsync(u, I.stage + 6 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
     }
     NLC_CK(cudaStreamSynchronize(st));
     return device_error();
   }
 
-  nlc_status get_populations(double* f) override {
-    nlc_status s;
-    if ((s = ensure_fstage())) return s;
-    const int64_t n = d_.n;
+  nlc_status get_populations(int i, double* f) override {
+    InstHost<T>& I = inst_[i];
+    if (!I.fstage) {
+      nlc_status s = alloc(&I.fstage, (size_t)Q * I.d.n);
+      if (s) return s;
+    }
+    const int64_t n = I.d.n;
     cudaStream_t st = args_.stream;
-    k_populations_out<Lat, T><<<grid1(n), 256, 0, st>>>(g_[cur_], d_, args_.params.rho0, fstage_);
+    k_populations_out<Lat, T><<<grid1(n), 256, 0, st>>>(I.g[cur_], I.d, args_.params[i].rho0,
+                                                         I.fstage);
     NLC_CK_LAUNCH("k_populations_out");
-    NLC_CK(cudaMemcpyAsync(f, fstage_, sizeof(double) * Q * n, cudaMemcpyDeviceToHost, st));
+    NLC_CK(cudaMemcpyAsync(f, I.fstage, sizeof(double) * Q * n, cudaMemcpyDeviceToHost, st));
     NLC_CK(cudaStreamSynchronize(st));
     return device_error();
   }
 
-  size_t state_bytes() const override { return sizeof(T) * (size_t)(Q + 5) * (size_t)d_.n; }
+  size_t state_bytes() const override {
+    size_t b = 0;
+    for (const auto& I : inst_) b += sizeof(T) * (size_t)(Q + 5) * (size_t)I.d.n;
+    return b;
+  }
 
   nlc_status save_state(void* dst) override {
-    nlc_status s;
-    if ((s = ensure_raw())) return s;
-    const int64_t n = d_.n;
     cudaStream_t st = args_.stream;
-    k_field_raw_out<T><<<grid1(n), 256, 0, st>>>(q_[cur_], 5, d_, raw_);
-    NLC_CK_LAUNCH("k_field_raw_out");
-    NLC_CK(cudaMemcpyAsync(dst, g_[cur_], sizeof(T) * Q * n, cudaMemcpyDeviceToHost, st));
-    NLC_CK(cudaMemcpyAsync((char*)dst + sizeof(T) * Q * n, raw_, sizeof(T) * 5 * n,
-                           cudaMemcpyDeviceToHost, st));
+    char* out = (char*)dst;
+    for (auto& I : inst_) {
+      nlc_status s;
+      if (!I.raw && (s = alloc(&I.raw, (size_t)5 * I.d.n))) return s;
+      const int64_t n = I.d.n;
+      k_field_raw_out<T><<<grid1(n), 256, 0, st>>>(I.q[cur_], 5, I.d, I.raw);
+      NLC_CK_LAUNCH("k_field_raw_out");
+      NLC_CK(cudaMemcpyAsync(out, I.g[cur_], sizeof(T) * Q * n, cudaMemcpyDeviceToHost, st));
+      out += sizeof(T) * Q * n;
+      NLC_CK(cudaMemcpyAsync(out, I.raw, sizeof(T) * 5 * n, cudaMemcpyDeviceToHost, st));
+      out += sizeof(T) * 5 * n;
+    }
     NLC_CK(cudaStreamSynchronize(st));
     return device_error();
   }
 
   nlc_status load_state(const void* src) override {
-    nlc_status s;
-    if ((s = ensure_raw())) return s;
-    const int64_t n = d_.n;
     cudaStream_t st = args_.stream;
-    NLC_CK(cudaMemcpyAsync(g_[0], src, sizeof(T) * Q * n, cudaMemcpyHostToDevice, st));
-    NLC_CK(cudaMemcpyAsync(raw_, (const char*)src + sizeof(T) * Q * n, sizeof(T) * 5 * n,
-                           cudaMemcpyHostToDevice, st));
-    k_field_raw_in<T, DIM><<<grid1(n), 256, 0, st>>>(raw_, d_, q_[0]);
-    NLC_CK_LAUNCH("k_field_raw_in");
+    const char* in = (const char*)src;
+    for (auto& I : inst_) {
+      nlc_status s;
+      if (!I.raw && (s = alloc(&I.raw, (size_t)5 * I.d.n))) return s;
+      const int64_t n = I.d.n;
+      NLC_CK(cudaMemcpyAsync(I.g[0], in, sizeof(T) * Q * n, cudaMemcpyHostToDevice, st));
+      in += sizeof(T) * Q * n;
+      NLC_CK(cudaMemcpyAsync(I.raw, in, sizeof(T) * 5 * n, cudaMemcpyHostToDevice, st));
+      in += sizeof(T) * 5 * n;
+      k_field_raw_in<T, DIM><<<grid1(n), 256, 0, st>>>(I.raw, I.d, I.q[0]);
+      NLC_CK_LAUNCH("k_field_raw_in");
+    }
     NLC_CK(cudaStreamSynchronize(st));
     cur_ = 0;
     return NLC_OK;
   }
 
-  nlc_status observables(nlc_obs* out, double* s_profile) override {
+  nlc_status observables(int i, nlc_obs* out, double* s_profile) override {
+    InstHost<T>& I = inst_[i];
     nlc_status s;
-    if ((s = ensure_staging())) return s;
-    const int64_t n = d_.n;
+    if ((s = ensure_staging(I))) return s;
+    const int64_t n = I.d.n;
+    const Dims& d = I.d;
     cudaStream_t st = args_.stream;
-    if ((s = moments_to_stage())) return s;
+    if ((s = moments_to_stage(I))) return s;
     const double s_ref = 1.0 / 3.0;
-    k_obs_partial<Lat, T><<<obs_blocks_, 256, 0, st>>>(
-        q_[cur_], g_[cur_], stage_ + 5 * n, stage_ + 6 * n, d_, p_, s_ref, partial_);
+    k_obs_partial<Lat, T><<<I.obs_blocks, 256, 0, st>>>(
+        I.q[cur_], I.g[cur_], I.stage + 5 * n, I.stage + 6 * n, d, I.p, s_ref, I.partial);
     NLC_CK_LAUNCH("k_obs_partial");
-    k_obs_final<<<1, 256, 0, st>>>(partial_, obs_blocks_, partial_ + obs_blocks_ * OBS_SLOTS);
+    k_obs_final<<<1, 256, 0, st>>>(I.partial, I.obs_blocks, I.partial + I.obs_blocks * OBS_SLOTS);
     NLC_CK_LAUNCH("k_obs_final");
-    const int64_t rows = (int64_t)d_.ny * d_.nz;
+    const int64_t rows = (int64_t)d.ny * d.nz;
     const int rows_per_chunk = 64;
     const int nchunks = (int)((rows + rows_per_chunk - 1) / rows_per_chunk);
-    dim3 pg((d_.nx + 127) / 128, nchunks);
-    k_profile_partial<T><<<pg, 128, 0, st>>>(q_[cur_], d_, rows_per_chunk, prof_partial_);
+    dim3 pg((d.nx + 127) / 128, nchunks);
+    k_profile_partial<T><<<pg, 128, 0, st>>>(I.q[cur_], d, rows_per_chunk, I.prof_partial);
     NLC_CK_LAUNCH("k_profile_partial");
-    k_profile_final<<<(d_.nx + 127) / 128, 128, 0, st>>>(prof_partial_, nchunks, d_, prof_);
+    k_profile_final<<<(d.nx + 127) / 128, 128, 0, st>>>(I.prof_partial, nchunks, d, I.prof);
     NLC_CK_LAUNCH("k_profile_final");
     double tot[OBS_SLOTS];
-    std::vector<double> prof(d_.nx);
-    NLC_CK(cudaMemcpyAsync(tot, partial_ + obs_blocks_ * OBS_SLOTS, sizeof(tot), cudaMemcpyDeviceToHost, st));
-    NLC_CK(cudaMemcpyAsync(prof.data(), prof_, sizeof(double) * d_.nx, cudaMemcpyDeviceToHost, st));
+    std::vector<double> prof(d.nx);
+    NLC_CK(cudaMemcpyAsync(tot, I.partial + I.obs_blocks * OBS_SLOTS, sizeof(tot),
+                           cudaMemcpyDeviceToHost, st));
+    NLC_CK(cudaMemcpyAsync(prof.data(), I.prof, sizeof(double) * d.nx, cudaMemcpyDeviceToHost, st));
     NLC_CK(cudaStreamSynchronize(st));
     if ((s = device_error())) return s;
     out->mass = tot[0];
@@ -230,19 +316,19 @@ class Engine final : public EngineBase {
     out->free_energy = tot[5];
     out->nonfinite = (int64_t)tot[6];
     out->max_u = tot[7];
-    out->radius = (DIM == 2 || d_.nz == 1) ? std::sqrt(tot[4] / M_PI)
-                                           : std::cbrt(3.0 * tot[4] / (4.0 * M_PI));
+    out->radius = (DIM == 2 || d.nz == 1) ? std::sqrt(tot[4] / M_PI)
+                                          : std::cbrt(3.0 * tot[4] / (4.0 * M_PI));
     const double half = s_ref / 2.0;
     out->x_iface = -1.0;
-    for (int x = 0; x < d_.nx; x++) {
-      const double a = prof[x], b = prof[(x + 1) % d_.nx];
+    for (int x = 0; x < d.nx; x++) {
+      const double a = prof[x], b = prof[(x + 1) % d.nx];
       if (a >= half && b < half) {
         out->x_iface = x + (a - half) / (a - b);
         break;
       }
     }
     if (s_profile)
-      for (int x = 0; x < d_.nx; x++) s_profile[x] = prof[x];
+      for (int x = 0; x < d.nx; x++) s_profile[x] = prof[x];
     return NLC_OK;
   }
 
@@ -276,56 +362,46 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
-  nlc_status ensure_unfused() {
-    if (pi_) return NLC_OK;
+  nlc_status ensure_unfused(InstHost<T>& I) {
+    if (I.pi) return NLC_OK;
     nlc_status s;
-    const int64_t n = d_.n;
+    const int64_t n = I.d.n;
     T* qp;
-    if ((s = alloc(&pi_, (size_t)DIM * DIM * n)) || (s = alloc(&qp, (size_t)5 * L_.comp)) ||
-        (s = alloc(&r1_, (size_t)5 * n)))
+    if ((s = alloc(&I.pi, (size_t)DIM * DIM * n)) || (s = alloc(&qp, (size_t)5 * I.L.comp)) ||
+        (s = alloc(&I.r1, (size_t)5 * n)))
       return s;
-    qp_ = Field<T>{qp, L_};
+    I.qp = Field<T>{qp, I.L};
     return NLC_OK;
   }
 
-  nlc_status ensure_staging() {
-    if (stage_) return NLC_OK;
+  nlc_status ensure_staging(InstHost<T>& I) {
+    if (I.stage) return NLC_OK;
     nlc_status s;
-    const int64_t n = d_.n;
-    if ((s = alloc(&stage_, (size_t)9 * n))) return s;
-    if ((s = ensure_unfused())) return s;
+    const int64_t n = I.d.n;
+    if ((s = alloc(&I.stage, (size_t)9 * n))) return s;
+    if ((s = ensure_unfused(I))) return s;
     int dev = 0, sms = 0;
     NLC_CK(cudaGetDevice(&dev));
     NLC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int64_t want = (n + 255) / 256;
-    obs_blocks_ = (int)(want < 4 * sms ? want : 4 * sms);
-    if (obs_blocks_ < 1) obs_blocks_ = 1;
-    if ((s = alloc(&partial_, (size_t)(obs_blocks_ + 1) * OBS_SLOTS))) return s;
-    const int64_t rows = (int64_t)d_.ny * d_.nz;
+    const int64_t want = (n + 255) / 256;
+    I.obs_blocks = (int)(want < 4 * sms ? want : 4 * sms);
+    if (I.obs_blocks < 1) I.obs_blocks = 1;
+    if ((s = alloc(&I.partial, (size_t)(I.obs_blocks + 1) * OBS_SLOTS))) return s;
+    const int64_t rows = (int64_t)I.d.ny * I.d.nz;
     const int64_t nchunks = (rows + 63) / 64;
-    if ((s = alloc(&prof_partial_, (size_t)(nchunks * d_.nx)))) return s;
-    if ((s = alloc(&prof_, (size_t)d_.nx))) return s;
+    if ((s = alloc(&I.prof_partial, (size_t)(nchunks * I.d.nx)))) return s;
+    if ((s = alloc(&I.prof, (size_t)I.d.nx))) return s;
     return NLC_OK;
   }
 
-  nlc_status ensure_raw() {
-    if (raw_) return NLC_OK;
-    return alloc(&raw_, (size_t)5 * d_.n);
-  }
-
-  nlc_status ensure_fstage() {
-    if (fstage_) return NLC_OK;
-    return alloc(&fstage_, (size_t)Q * d_.n);
-  }
-
-  // rho, u of Eq. 6 at the current state into stage_[5n..9n)
-  nlc_status moments_to_stage() {
-    const int64_t n = d_.n;
+  // rho, u of Eq. 6 at the current state into stage[5n..9n)
+  nlc_status moments_to_stage(InstHost<T>& I) {
+    const int64_t n = I.d.n;
     cudaStream_t st = args_.stream;
-    k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(q_[cur_], pi_, d_, p_);
+    k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[cur_], I.pi, I.d, I.p);
     NLC_CK_LAUNCH("k_stress");
-    k_moments_out<Lat, T><<<grid1(n), 256, 0, st>>>(g_[cur_], pi_, d_, p_,
-                                                     stage_ + 5 * n, stage_ + 6 * n);
+    k_moments_out<Lat, T><<<grid1(n), 256, 0, st>>>(I.g[cur_], I.pi, I.d, I.p, I.stage + 5 * n,
+                                                     I.stage + 6 * n);
     NLC_CK_LAUNCH("k_moments_out");
     return NLC_OK;
   }
@@ -333,43 +409,47 @@ class Engine final : public EngineBase {
   int mark() { return timer.on ? timer.mark(args_.stream) : -1; }
 
   nlc_status step_unfused() {
-    const int64_t n = d_.n;
     cudaStream_t st = args_.stream;
     const int a = cur_, b = cur_ ^ 1;
-    const int e0 = mark();
-    k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(q_[a], pi_, d_, p_);
-    NLC_CK_LAUNCH("k_stress");
-    const int e1 = mark();
-    k_lb<Lat, T><<<grid1(n), 256, 0, st>>>(g_[a], g_[b], pi_, u_, d_, p_);
-    NLC_CK_LAUNCH("k_lb");
-    const int e2 = mark();
-    k_predict<Lat, T><<<grid1(n), 256, 0, st>>>(q_[a], u_, qp_, r1_, d_, p_);
-    NLC_CK_LAUNCH("k_predict");
-    const int e3 = mark();
-    k_correct<Lat, T><<<grid1(n), 256, 0, st>>>(q_[a], qp_, r1_, u_, q_[b], d_, p_);
-    NLC_CK_LAUNCH("k_correct");
-    const int e4 = mark();
-    if (timer.on) {
-      timer.span(KID_STRESS, e0, e1);
-      timer.span(KID_LB, e1, e2);
-      timer.span(KID_PREDICT, e2, e3);
-      timer.span(KID_CORRECT, e3, e4);
+    for (auto& I : inst_) {
+      const int64_t n = I.d.n;
+      const int e0 = mark();
+      k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.pi, I.d, I.p);
+      NLC_CK_LAUNCH("k_stress");
+      const int e1 = mark();
+      k_lb<Lat, T><<<grid1(n), 256, 0, st>>>(I.g[a], I.g[b], I.pi, I.u, I.d, I.p);
+      NLC_CK_LAUNCH("k_lb");
+      const int e2 = mark();
+      k_predict<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.u, I.qp, I.r1, I.d, I.p);
+      NLC_CK_LAUNCH("k_predict");
+      const int e3 = mark();
+      k_correct<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.qp, I.r1, I.u, I.q[b], I.d, I.p);
+      NLC_CK_LAUNCH("k_correct");
+      const int e4 = mark();
+      if (timer.on) {
+        timer.span(KID_STRESS, e0, e1);
+        timer.span(KID_LB, e1, e2);
+        timer.span(KID_PREDICT, e2, e3);
+        timer.span(KID_CORRECT, e3, e4);
+      }
     }
     cur_ = b;
     return NLC_OK;
   }
 
-  nlc_status step_fused() {
-    cudaStream_t st = args_.stream;
-    const int a = cur_, b = cur_ ^ 1;
+  // one step of every lattice: two launches over the joint tile list
+  nlc_status step_fused(cudaStream_t st) {
+    const int a = cur_;
     const int e0 = mark();
-    cudaError_t e = launch_fused_lb<Lat, T>(qmap_[a], g_[a], g_[b], u_, d_, p_, derr_, st);
+    cudaError_t e = launch_fused_lb<Lat, T>(insts_dev_, qmaps_dev_, tiles_dev_, ntiles_, a,
+                                            derr_, st);
     if (e != cudaSuccess) {
       err = std::string("fused lb kernel: ") + cudaGetErrorString(e);
       return NLC_ECUDA;
     }
     const int e1 = mark();
-    e = launch_fused_be<Lat, T>(qmap_[a], umap_, q_[b], d_, p_, derr_, st);
+    e = launch_fused_be<Lat, T>(insts_dev_, qmaps_dev_, umaps_dev_, tiles_dev_, ntiles_, a,
+                                derr_, st);
     if (e != cudaSuccess) {
       err = std::string("fused Beris-Edwards kernel: ") + cudaGetErrorString(e);
       return NLC_ECUDA;
@@ -379,34 +459,59 @@ class Engine final : public EngineBase {
       timer.span(KID_FUSED_LB, e0, e1);
       timer.span(KID_FUSED_BE, e1, e2);
     }
-    cur_ = b;
+    cur_ ^= 1;
+    return NLC_OK;
+  }
+
+  // captures graph_steps fused steps starting from buffer parity c
+  nlc_status ensure_graph(int c) {
+    if (graph_[c] && graph_len_[c] == graph_steps) return NLC_OK;
+    if (graph_[c]) {
+      cudaGraphExecDestroy(graph_[c]);
+      graph_[c] = nullptr;
+    }
+    if (!cap_stream_) NLC_CK(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
+    const int saved = cur_;
+    cur_ = c;
+    NLC_CK(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
+    nlc_status s = NLC_OK;
+    for (int k = 0; k < graph_steps && s == NLC_OK; k++) s = step_fused(cap_stream_);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap_stream_, &g);
+    cur_ = saved;
+    if (s != NLC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) {
+      err = std::string("stream capture: ") + cudaGetErrorString(e);
+      return NLC_ECUDA;
+    }
+    e = cudaGraphInstantiate(&graph_[c], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+      return NLC_ECUDA;
+    }
+    graph_len_[c] = graph_steps;
     return NLC_OK;
   }
 
   EngineArgs args_;
-  Dims d_;
-  Layout L_;
-  Par<T> p_;
+  std::vector<InstHost<T>> inst_;
   std::vector<void*> allocs_;
-  T* g_[2] = {nullptr, nullptr};
-  Field<T> q_[2];
-  Field<T> u_;
-  Field<T> qp_;
-  CUtensorMap qmap_[2];
-  CUtensorMap umap_;
+  InstDev<T>* insts_dev_ = nullptr;
+  CUtensorMap* qmaps_dev_ = nullptr;
+  CUtensorMap* umaps_dev_ = nullptr;
+  TileRef* tiles_dev_ = nullptr;
+  int ntiles_ = 0;
   bool maps_ok_ = false;
-  T* pi_ = nullptr;
-  T* r1_ = nullptr;
-  T* raw_ = nullptr;
-  double* stage_ = nullptr;
-  double* fstage_ = nullptr;
-  double* partial_ = nullptr;
-  double* prof_partial_ = nullptr;
-  double* prof_ = nullptr;
   unsigned long long* bad_ = nullptr;
   unsigned* derr_ = nullptr;
-  int obs_blocks_ = 1;
   int cur_ = 0;
+  cudaStream_t cap_stream_ = nullptr;
+  cudaGraphExec_t graph_[2] = {nullptr, nullptr};
+  int graph_len_[2] = {0, 0};
 };
 
 template <class Lat, class T>

@@ -71,12 +71,14 @@ class KernelTimer {
 struct EngineBase {
   virtual ~EngineBase() = default;
   KernelTimer timer;
+  int graph_steps = 0;  // >0: whole chunks of this many steps replay a CUDA graph
+  virtual int count() const = 0;
   virtual nlc_status step(int64_t n, int schedule) = 0;
-  virtual nlc_status set_fields(const double* Q5, const double* rho,
+  virtual nlc_status set_fields(int inst, const double* Q5, const double* rho,
                                 const double* u) = 0;
-  virtual nlc_status get_fields(double* Q5, double* rho, double* u) = 0;
-  virtual nlc_status get_populations(double* f) = 0;
-  virtual nlc_status observables(nlc_obs* out, double* s_profile) = 0;
+  virtual nlc_status get_fields(int inst, double* Q5, double* rho, double* u) = 0;
+  virtual nlc_status get_populations(int inst, double* f) = 0;
+  virtual nlc_status observables(int inst, nlc_obs* out, double* s_profile) = 0;
   // raw device state: populations (current buffer) then Q interior
   virtual size_t state_bytes() const = 0;
   virtual nlc_status save_state(void* dst) = 0;
@@ -85,8 +87,9 @@ struct EngineBase {
 };
 
 struct EngineArgs {
-  nlc_grid grid;
-  nlc_params params;
+  int n;                           // lattices in the context
+  std::vector<nlc_grid> grids;     // n entries, same lattice and precision
+  std::vector<nlc_params> params;  // n entries
   cudaStream_t stream;
 };
 

@@ -9,6 +9,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/nlc.h"
 #include "engine.h"
@@ -17,12 +18,12 @@
 static_assert(nlc::KID_COUNT == NLC_N_KERNELS, "kernel id table out of sync");
 
 struct nlc_ctx {
-  nlc_grid grid;
-  nlc_params params;
+  std::vector<nlc_grid> grids;
+  std::vector<nlc_params> params;
   cudaStream_t stream = nullptr;
   int device = 0;
   int schedule = NLC_SCHED_FUSED;
-  int64_t steps = 0;
+  std::vector<int64_t> steps;  // per lattice, since its last nlc_set_fields
   std::unique_ptr<nlc::EngineBase> eng;
   std::string err;
 };
@@ -95,28 +96,35 @@ nlc_status check_params(const nlc_params* p, std::string* msg) {
 
 extern "C" {
 
-nlc_status nlc_create(const nlc_grid* grid, const nlc_params* params,
-                      void* stream, nlc_ctx** out) {
+nlc_status nlc_create_batch(int32_t n, const nlc_grid* grids,
+                            const nlc_params* params, void* stream,
+                            nlc_ctx** out) {
   if (!out) return NLC_EINVAL;
   *out = nullptr;
+  if (n < 1 || !grids || !params) return NLC_EINVAL;
   std::string msg;
-  nlc_status st = check_grid(grid, &msg);
-  if (st == NLC_OK) st = check_params(params, &msg);
-  if (st != NLC_OK) return st;
+  for (int i = 0; i < n; i++) {
+    nlc_status st = check_grid(&grids[i], &msg);
+    if (st == NLC_OK) st = check_params(&params[i], &msg);
+    if (st != NLC_OK) return st;
+    if (grids[i].lattice != grids[0].lattice || grids[i].precision != grids[0].precision)
+      return NLC_EINVAL;  // one lattice type and precision per context
+  }
   nlc_ctx* ctx = new (std::nothrow) nlc_ctx();
   if (!ctx) return NLC_ENOMEM;
-  ctx->grid = *grid;
-  ctx->params = *params;
+  ctx->grids.assign(grids, grids + n);
+  ctx->params.assign(params, params + n);
+  ctx->steps.assign(n, 0);
   ctx->stream = (cudaStream_t)stream;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
     cudaGetLastError();
     delete ctx;
     return NLC_ECUDA;
   }
-  nlc::EngineArgs a{*grid, *params, ctx->stream};
-  const bool d3 = grid->lattice == NLC_D3Q19;
-  const bool f64 = grid->precision == NLC_FP64;
-  st = NLC_OK;
+  nlc::EngineArgs a{n, ctx->grids, ctx->params, ctx->stream};
+  const bool d3 = grids[0].lattice == NLC_D3Q19;
+  const bool f64 = grids[0].precision == NLC_FP64;
+  nlc_status st = NLC_OK;
   if (d3)
     ctx->eng = f64 ? nlc::make_engine_d3q19_f64(a, &st, &msg)
                    : nlc::make_engine_d3q19_f32(a, &st, &msg);
@@ -131,6 +139,20 @@ nlc_status nlc_create(const nlc_grid* grid, const nlc_params* params,
   return NLC_OK;
 }
 
+nlc_status nlc_create(const nlc_grid* grid, const nlc_params* params,
+                      void* stream, nlc_ctx** out) {
+  return nlc_create_batch(1, grid, params, stream, out);
+}
+
+nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps) {
+  if (!ctx) return NLC_EINVAL;
+  if (steps < 0) return fail(ctx, NLC_EINVAL, "negative graph length");
+  ctx->eng->graph_steps = steps;
+  return NLC_OK;
+}
+
+int32_t nlc_count(const nlc_ctx* ctx) { return ctx ? (int32_t)ctx->grids.size() : -1; }
+
 nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule) {
   if (!ctx) return NLC_EINVAL;
   if (schedule != NLC_SCHED_FUSED && schedule != NLC_SCHED_UNFUSED)
@@ -139,30 +161,34 @@ nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule) {
   return NLC_OK;
 }
 
+static bool bad_inst(const nlc_ctx* ctx, int32_t inst) {
+  return inst < 0 || inst >= (int32_t)ctx->grids.size();
+}
+
 nlc_status nlc_set_fields(nlc_ctx* ctx, int32_t inst, const double* Q5,
                           const double* rho, const double* u) {
   if (!ctx) return NLC_EINVAL;
-  if (inst != 0) return fail(ctx, NLC_EINVAL, "instance out of range");
+  if (bad_inst(ctx, inst)) return fail(ctx, NLC_EINVAL, "instance out of range");
   if (!Q5) return fail(ctx, NLC_EINVAL, "Q5 is NULL");
-  nlc_status st = ctx->eng->set_fields(Q5, rho, u);
+  nlc_status st = ctx->eng->set_fields(inst, Q5, rho, u);
   if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
-  ctx->steps = 0;
+  ctx->steps[inst] = 0;
   return NLC_OK;
 }
 
 nlc_status nlc_get_fields(nlc_ctx* ctx, int32_t inst, double* Q5, double* rho,
                           double* u) {
   if (!ctx) return NLC_EINVAL;
-  if (inst != 0) return fail(ctx, NLC_EINVAL, "instance out of range");
-  nlc_status st = ctx->eng->get_fields(Q5, rho, u);
+  if (bad_inst(ctx, inst)) return fail(ctx, NLC_EINVAL, "instance out of range");
+  nlc_status st = ctx->eng->get_fields(inst, Q5, rho, u);
   return st == NLC_OK ? st : fail(ctx, st, ctx->eng->err);
 }
 
 nlc_status nlc_get_populations(nlc_ctx* ctx, int32_t inst, double* f) {
   if (!ctx) return NLC_EINVAL;
-  if (inst != 0) return fail(ctx, NLC_EINVAL, "instance out of range");
+  if (bad_inst(ctx, inst)) return fail(ctx, NLC_EINVAL, "instance out of range");
   if (!f) return fail(ctx, NLC_EINVAL, "f is NULL");
-  nlc_status st = ctx->eng->get_populations(f);
+  nlc_status st = ctx->eng->get_populations(inst, f);
   return st == NLC_OK ? st : fail(ctx, st, ctx->eng->err);
 }
 
@@ -171,18 +197,18 @@ nlc_status nlc_step(nlc_ctx* ctx, int64_t n) {
   if (n < 0) return fail(ctx, NLC_EINVAL, "negative step count");
   nlc_status st = ctx->eng->step(n, ctx->schedule);
   if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
-  ctx->steps += n;
+  for (auto& s : ctx->steps) s += n;
   return NLC_OK;
 }
 
 nlc_status nlc_observables(nlc_ctx* ctx, int32_t inst, nlc_obs* out,
                            double* s_profile) {
   if (!ctx) return NLC_EINVAL;
-  if (inst != 0) return fail(ctx, NLC_EINVAL, "instance out of range");
+  if (bad_inst(ctx, inst)) return fail(ctx, NLC_EINVAL, "instance out of range");
   if (!out) return fail(ctx, NLC_EINVAL, "out is NULL");
-  nlc_status st = ctx->eng->observables(out, s_profile);
+  nlc_status st = ctx->eng->observables(inst, out, s_profile);
   if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
-  out->step = ctx->steps;
+  out->step = ctx->steps[inst];
   return NLC_OK;
 }
 
@@ -192,12 +218,11 @@ struct SaveHeader {
   char magic[8];
   uint32_t version;
   uint32_t header_bytes;
-  nlc_grid grid;
+  int32_t count;         // lattices
   int32_t pad0;
-  nlc_params params;
-  int64_t step;
+  uint64_t desc_hash;    // checksum of the lattices' grids and parameters
   uint64_t payload_bytes;
-  uint64_t checksum;
+  uint64_t checksum;     // of the payload (step counters, then the state)
 };
 
 const char kMagic[8] = {'N', 'L', 'C', 'S', 'T', 'A', 'T', 'E'};
@@ -220,12 +245,24 @@ uint64_t checksum64(const unsigned char* p, size_t n) {
   return h;
 }
 
+uint64_t desc_hash(const nlc_ctx* ctx) {
+  std::vector<unsigned char> b;
+  for (size_t i = 0; i < ctx->grids.size(); i++) {
+    const unsigned char* g = (const unsigned char*)&ctx->grids[i];
+    const unsigned char* q = (const unsigned char*)&ctx->params[i];
+    b.insert(b.end(), g, g + sizeof(nlc_grid));
+    b.insert(b.end(), q, q + sizeof(nlc_params));
+  }
+  return checksum64(b.data(), b.size());
+}
+
 }  // namespace
 
 nlc_status nlc_save(nlc_ctx* ctx, void* buf, size_t* len) {
   if (!ctx) return NLC_EINVAL;
   if (!len) return fail(ctx, NLC_EINVAL, "len is NULL");
-  const size_t payload = ctx->eng->state_bytes();
+  const size_t nst = sizeof(int64_t) * ctx->steps.size();
+  const size_t payload = nst + ctx->eng->state_bytes();
   const size_t need = sizeof(SaveHeader) + payload;
   if (!buf) {
     *len = need;
@@ -233,16 +270,16 @@ nlc_status nlc_save(nlc_ctx* ctx, void* buf, size_t* len) {
   }
   if (*len < need) return fail(ctx, NLC_EINVAL, "buffer too small for the state");
   unsigned char* out = (unsigned char*)buf;
-  nlc_status st = ctx->eng->save_state(out + sizeof(SaveHeader));
+  std::memcpy(out + sizeof(SaveHeader), ctx->steps.data(), nst);
+  nlc_status st = ctx->eng->save_state(out + sizeof(SaveHeader) + nst);
   if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
   SaveHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, kMagic, 8);
   h.version = 1;
   h.header_bytes = sizeof(SaveHeader);
-  h.grid = ctx->grid;
-  h.params = ctx->params;
-  h.step = ctx->steps;
+  h.count = (int32_t)ctx->grids.size();
+  h.desc_hash = desc_hash(ctx);
   h.payload_bytes = payload;
   h.checksum = checksum64(out + sizeof(SaveHeader), payload);
   std::memcpy(out, &h, sizeof(h));
@@ -258,19 +295,18 @@ nlc_status nlc_load(nlc_ctx* ctx, const void* buf, size_t len) {
   if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 ||
       h.header_bytes != sizeof(SaveHeader))
     return fail(ctx, NLC_EINVAL, "not a checkpoint of this format");
-  if (std::memcmp(&h.grid, &ctx->grid, sizeof(nlc_grid)) != 0)
-    return fail(ctx, NLC_EINVAL, "checkpoint is for another grid or precision");
-  if (std::memcmp(&h.params, &ctx->params, sizeof(nlc_params)) != 0)
-    return fail(ctx, NLC_EINVAL, "checkpoint has other parameters");
-  const size_t payload = ctx->eng->state_bytes();
+  if (h.count != (int32_t)ctx->grids.size() || h.desc_hash != desc_hash(ctx))
+    return fail(ctx, NLC_EINVAL, "checkpoint is for other lattices or parameters");
+  const size_t nst = sizeof(int64_t) * ctx->steps.size();
+  const size_t payload = nst + ctx->eng->state_bytes();
   if (h.payload_bytes != payload || len < sizeof(SaveHeader) + payload)
     return fail(ctx, NLC_EINVAL, "checkpoint is truncated");
   const unsigned char* p = (const unsigned char*)buf + sizeof(SaveHeader);
   if (checksum64(p, payload) != h.checksum)
     return fail(ctx, NLC_ECORRUPT, "checkpoint checksum mismatch");
-  nlc_status st = ctx->eng->load_state(p);
+  nlc_status st = ctx->eng->load_state(p + nst);
   if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
-  ctx->steps = h.step;
+  std::memcpy(ctx->steps.data(), p, nst);
   return NLC_OK;
 }
 

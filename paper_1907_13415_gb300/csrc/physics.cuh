@@ -18,7 +18,7 @@ struct Par {
 
 // five stored components -> full symmetric traceless 3x3
 template <class T>
-__device__ __forceinline__ void q_full(const T q[5], T Q[3][3]) {
+__host__ __device__ __forceinline__ void q_full(const T q[5], T Q[3][3]) {
   Q[0][0] = q[0];
   Q[0][1] = q[1];
   Q[0][2] = q[2];
@@ -30,108 +30,99 @@ __device__ __forceinline__ void q_full(const T q[5], T Q[3][3]) {
   Q[2][2] = -q[0] - q[3];
 }
 
+// Products of symmetric traceless tensors are written out in the five stored
+// components (a, b, c, d, e) = (xx, xy, xz, yy, yz), f = zz = -a - d.
+
 // Eq. 3: H = -A0(1-g/3) Q - A0 g (Tr(Q^2) I/3 - Q Q) - A0 g Q Tr(Q^2) + K lapQ
 // (returned as the five independent components; H is symmetric traceless)
 template <class T>
-__device__ __forceinline__ void molecular_field(const T q[5], const T lap[5],
+__host__ __device__ __forceinline__ void molecular_field(const T q[5], const T lap[5],
                                                 const Par<T>& p, T h[5]) {
-  T Q[3][3];
-  q_full(q, Q);
-  T QQ[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; a++)
-#pragma unroll
-    for (int b = 0; b < 3; b++)
-      QQ[a][b] = Q[a][0] * Q[0][b] + Q[a][1] * Q[1][b] + Q[a][2] * Q[2][b];
-  const T tr2 = QQ[0][0] + QQ[1][1] + QQ[2][2];
-  const T c1 = -p.A0 * (T(1) - p.gamma / T(3)) - p.A0 * p.gamma * tr2;
-  const T c2 = p.A0 * p.gamma;
-  const T c3 = -p.A0 * p.gamma * tr2 / T(3);
-  h[0] = c1 * Q[0][0] + c2 * QQ[0][0] + c3 + p.K * lap[0];
-  h[1] = c1 * Q[0][1] + c2 * QQ[0][1] + p.K * lap[1];
-  h[2] = c1 * Q[0][2] + c2 * QQ[0][2] + p.K * lap[2];
-  h[3] = c1 * Q[1][1] + c2 * QQ[1][1] + c3 + p.K * lap[3];
-  h[4] = c1 * Q[1][2] + c2 * QQ[1][2] + p.K * lap[4];
+  const T a = q[0], b = q[1], c = q[2], d = q[3], e = q[4], f = -q[0] - q[3];
+  // (Q Q)_xx, _xy, _xz, _yy, _yz
+  const T qq0 = a * a + b * b + c * c;
+  const T qq1 = a * b + b * d + c * e;
+  const T qq2 = a * c + b * e + c * f;
+  const T qq3 = b * b + d * d + e * e;
+  const T qq4 = b * c + d * e + e * f;
+  const T tr2 = a * a + d * d + f * f + T(2) * (b * b + c * c + e * e);
+  const T Ag = p.A0 * p.gamma;
+  const T c1 = -p.A0 * (T(1) - p.gamma / T(3)) - Ag * tr2;
+  const T c3 = -Ag * tr2 / T(3);
+  h[0] = c1 * a + Ag * qq0 + c3 + p.K * lap[0];
+  h[1] = c1 * b + Ag * qq1 + p.K * lap[1];
+  h[2] = c1 * c + Ag * qq2 + p.K * lap[2];
+  h[3] = c1 * d + Ag * qq3 + c3 + p.K * lap[3];
+  h[4] = c1 * e + Ag * qq4 + p.K * lap[4];
 }
 
 // Eq. 5 without P0, with dF/d(d_b Q) = K d_b Q:
 //   Pi_ab = 2 xi Qt_ab (Q:H) - xi (H Qt)_ab - xi (Qt H)_ab
 //           - K d_a Q : d_b Q + (Q H)_ab - (H Q)_ab,      Qt = Q + I/3.
+// With X = Q H (so H Q = X^T, H Qt = X^T + H/3, Qt H = X + H/3):
+//   Pi_ab = 2 xi Qt_ab (Q:H) - (xi - 1) X_ab - (xi + 1) X_ba
+//           - (2 xi/3) H_ab - K d_a Q : d_b Q.
 // dq[g][k]: d_g of stored component k.  Only a, b < DIM are produced.
 template <class T, int DIM>
-__device__ __forceinline__ void stress(const T q[5], const T h[5],
+__host__ __device__ __forceinline__ void stress(const T q[5], const T h[5],
                                        const T dq[3][5], const Par<T>& p,
                                        T Pi[3][3]) {
-  T Q[3][3], H[3][3];
-  q_full(q, Q);
-  q_full(h, H);
-  T QH[3][3];  // (Q H); since Q, H are symmetric, H Q = (Q H)^T
-#pragma unroll
-  for (int a = 0; a < 3; a++)
-#pragma unroll
-    for (int b = 0; b < 3; b++)
-      QH[a][b] = Q[a][0] * H[0][b] + Q[a][1] * H[1][b] + Q[a][2] * H[2][b];
-  const T qh = QH[0][0] + QH[1][1] + QH[2][2];  // Q:H
-  // d_a Q : d_b Q over all nine entries (off-diagonals twice, Qzz included)
-  T el[3][3];
+  const T Q[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], -q[0] - q[3]}};
+  const T H[3][3] = {{h[0], h[1], h[2]}, {h[1], h[3], h[4]}, {h[2], h[4], -h[0] - h[3]}};
+  // Q:H over all nine entries
+  const T qh = Q[0][0] * H[0][0] + Q[1][1] * H[1][1] + Q[2][2] * H[2][2] +
+               T(2) * (q[1] * h[1] + q[2] * h[2] + q[4] * h[4]);
+  const T xm1 = p.xi - T(1), xp1 = p.xi + T(1), x23 = T(2) * p.xi / T(3);
+  T X[3][3];  // X = Q H
 #pragma unroll
   for (int a = 0; a < DIM; a++)
 #pragma unroll
-    for (int b = 0; b < DIM; b++) {
-      if (b < a) {
-        el[a][b] = el[b][a];
-        continue;
-      }
-      const T zza = -dq[a][0] - dq[a][3], zzb = -dq[b][0] - dq[b][3];
-      el[a][b] = dq[a][0] * dq[b][0] + dq[a][3] * dq[b][3] + zza * zzb +
-                 T(2) * (dq[a][1] * dq[b][1] + dq[a][2] * dq[b][2] +
-                         dq[a][4] * dq[b][4]);
-    }
+    for (int b = 0; b < DIM; b++)
+      X[a][b] = Q[a][0] * H[0][b] + Q[a][1] * H[1][b] + Q[a][2] * H[2][b];
 #pragma unroll
   for (int a = 0; a < DIM; a++)
 #pragma unroll
-    for (int b = 0; b < DIM; b++) {
+    for (int b = a; b < DIM; b++) {
+      // d_a Q : d_b Q over all nine entries (off-diagonals twice, zz included)
+      const T el = T(2) * (dq[a][0] * dq[b][0] + dq[a][3] * dq[b][3]) +
+                   dq[a][0] * dq[b][3] + dq[a][3] * dq[b][0] +
+                   T(2) * (dq[a][1] * dq[b][1] + dq[a][2] * dq[b][2] + dq[a][4] * dq[b][4]);
       const T qt = Q[a][b] + (a == b ? T(1) / T(3) : T(0));
-      // H Qt = H Q + H/3 = (QH)^T + H/3 ; Qt H = QH + H/3
-      const T HQt = QH[b][a] + H[a][b] * (T(1) / T(3));
-      const T QtH = QH[a][b] + H[a][b] * (T(1) / T(3));
-      Pi[a][b] = T(2) * p.xi * qt * qh - p.xi * HQt - p.xi * QtH -
-                 p.K * el[a][b] + QH[a][b] - QH[b][a];
+      const T sym = T(2) * p.xi * qt * qh - x23 * H[a][b] - p.K * el;
+      Pi[a][b] = sym - xm1 * X[a][b] - xp1 * X[b][a];
+      if (b != a) Pi[b][a] = sym - xm1 * X[b][a] - xp1 * X[a][b];
     }
 }
 
 // Co-rotational term of Eq. 1:
 //   S = (xi D + W) Qt + Qt (xi D - W) - 2 xi Qt (Q_ge d_g u_e)
 //   W_ab = (d_b u_a - d_a u_b)/2, D_ab = (d_b u_a + d_a u_b)/2.
-// G[a][b] = d_b u_a.  Writes the five stored components of S.
+// G[a][b] = d_b u_a.  With M = xi D + W = ((xi+1) G + (xi-1) G^T)/2 one has
+// xi D - W = M^T, so S = P + P^T - 2 xi Qt (Q:G^T) with P = M Qt.
+// Writes the five stored components of S.
 template <class T>
-__device__ __forceinline__ void corotation(const T G[3][3], const T q[5],
+__host__ __device__ __forceinline__ void corotation(const T G[3][3], const T q[5],
                                            T xi, T s[5]) {
-  T Q[3][3];
-  q_full(q, Q);
-  T L[3][3], R[3][3], Qt[3][3];
-  T qgu = T(0);
+  const T Qt[3][3] = {{q[0] + T(1) / T(3), q[1], q[2]},
+                      {q[1], q[3] + T(1) / T(3), q[4]},
+                      {q[2], q[4], -q[0] - q[3] + T(1) / T(3)}};
+  const T hp = (xi + T(1)) * T(0.5), hm = (xi - T(1)) * T(0.5);
+  T M[3][3];
 #pragma unroll
   for (int a = 0; a < 3; a++)
 #pragma unroll
-    for (int b = 0; b < 3; b++) {
-      const T W = (G[a][b] - G[b][a]) * T(0.5);
-      const T D = (G[a][b] + G[b][a]) * T(0.5);
-      L[a][b] = xi * D + W;
-      R[a][b] = xi * D - W;
-      Qt[a][b] = Q[a][b] + (a == b ? T(1) / T(3) : T(0));
-      qgu += Q[a][b] * G[b][a];
-    }
-  constexpr int ia[5] = {0, 0, 0, 1, 1};
-  constexpr int ib[5] = {0, 1, 2, 1, 2};
-#pragma unroll
-  for (int k = 0; k < 5; k++) {
-    const int a = ia[k], b = ib[k];
-    T v = T(0);
-#pragma unroll
-    for (int g = 0; g < 3; g++) v += L[a][g] * Qt[g][b] + Qt[a][g] * R[g][b];
-    s[k] = v - T(2) * xi * Qt[a][b] * qgu;
-  }
+    for (int b = 0; b < 3; b++) M[a][b] = hp * G[a][b] + hm * G[b][a];
+  // Q_ge d_g u_e = sum Q_ge G_eg
+  const T qg = q[0] * G[0][0] + q[3] * G[1][1] + (-q[0] - q[3]) * G[2][2] +
+               q[1] * (G[0][1] + G[1][0]) + q[2] * (G[0][2] + G[2][0]) +
+               q[4] * (G[1][2] + G[2][1]);
+  auto P = [&](int a, int b) { return M[a][0] * Qt[0][b] + M[a][1] * Qt[1][b] + M[a][2] * Qt[2][b]; };
+  const T t = T(2) * xi * qg;
+  s[0] = T(2) * P(0, 0) - t * Qt[0][0];
+  s[1] = P(0, 1) + P(1, 0) - t * Qt[0][1];
+  s[2] = P(0, 2) + P(2, 0) - t * Qt[0][2];
+  s[3] = T(2) * P(1, 1) - t * Qt[1][1];
+  s[4] = P(1, 2) + P(2, 1) - t * Qt[1][2];
 }
 
 // Right-hand side of Eq. 1 at one cell,
@@ -142,7 +133,7 @@ __device__ __forceinline__ void corotation(const T G[3][3], const T q[5],
 // Inputs: q (5), its central first derivatives dq[g][k], its Laplacian
 // lap[k], u (3), G.
 template <class T, int DIM>
-__device__ __forceinline__ void be_rhs(const T q[5], const T dq[3][5],
+__host__ __device__ __forceinline__ void be_rhs(const T q[5], const T dq[3][5],
                                        const T lap[5], const T u[3],
                                        const T G[3][3], const Par<T>& p,
                                        T r[5]) {
@@ -171,7 +162,7 @@ __device__ __forceinline__ void be_rhs(const T q[5], const T dq[3][5],
 // and the BGK source term
 // S_i = w_i (1 - 1/2tau) [c_i/cs2 (1 + c_i.u/cs2) - u/cs2] . F.
 template <class Lat, class T>
-__device__ __forceinline__ void collide_bgk(T g[Lat::Q], T rho, const T u[3],
+__host__ __device__ __forceinline__ void collide_bgk(T g[Lat::Q], T rho, const T u[3],
                                             const T F[3], const Par<T>& p) {
   const T uu = u[0] * u[0] + u[1] * u[1] + (Lat::DIM == 3 ? u[2] * u[2] : T(0));
   const T uF = u[0] * F[0] + u[1] * F[1] + (Lat::DIM == 3 ? u[2] * F[2] : T(0));

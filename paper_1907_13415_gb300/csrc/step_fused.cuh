@@ -11,7 +11,9 @@
 //               memory) -> R(Q^P) and the corrector Q^{n+1} (Sec. 1.2.2,
 //               steps 1-5).
 //
-// Each thread block owns a 32 x 8 tile of the (x, y) plane.  On D3Q19 it
+// Each thread block owns a 32 x 8 tile of the (x, y) plane of one lattice
+// (a batched context lists the tiles of all its lattices, so one launch
+// advances all of them).  On D3Q19 it
 // marches along z through a chunk of planes; the halo planes of Q and u
 // arrive by TMA (one cp.async.bulk.tensor per plane and field) into rings of
 // shared-memory slots, each completed on its own mbarrier, issued one plane
@@ -29,6 +31,8 @@
 #include "physics.cuh"
 #include "step_unfused.cuh"
 #include "tma.cuh"
+
+#include <vector>
 
 namespace nlc {
 
@@ -49,6 +53,23 @@ template <class T>
 constexpr size_t align128(size_t bytes) {
   return (bytes + 127) / 128 * 128;
 }
+
+// One lattice of a (possibly batched) context, as the step kernels see it.
+template <class T>
+struct InstDev {
+  Dims d;
+  Par<T> p;
+  T* g[2];         // populations, ping-pong
+  Field<T> q[2];   // Q, ping-pong
+  Field<T> u;      // u^n handed from the lb to the Beris-Edwards kernel
+  int tz;          // z planes per tile (1 on a single plane)
+};
+
+// One thread block's work: a 32 x 8 (x, y) tile of instance `inst`, planes
+// z0 .. z0 + tz - 1.
+struct TileRef {
+  int inst, x0, y0, z0;
+};
 
 // ---------------------------------------------------------------------------
 // lb kernel
@@ -103,9 +124,10 @@ __device__ __forceinline__ void stress_ring_cell(int c, const T* __restrict__ sq
 
 template <class Lat, class T>
 __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
-    k_fused_lb(const __grid_constant__ CUtensorMap qmap, const T* __restrict__ gin,
-               T* __restrict__ gout, Field<T> U, Dims d, Par<T> p, int tz,
-               int zoff, unsigned* __restrict__ err) {
+    k_fused_lb(const InstDev<T>* __restrict__ insts,
+               const CUtensorMap* __restrict__ qmaps,
+               const TileRef* __restrict__ tiles, int cur,
+               unsigned* __restrict__ err) {
   using C = LbCfg<Lat, T>;
   constexpr int DIM = Lat::DIM;
   constexpr int NPI = C::NPI;
@@ -114,10 +136,20 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   auto sQ = [&](int slot) { return reinterpret_cast<T*>(smem + slot * C::q_slot); };
   auto sP = [&](int slot) { return reinterpret_cast<T*>(smem + C::off_p + slot * C::p_slot); };
 
+  const TileRef tile = tiles[blockIdx.x];
+  const InstDev<T>& I = insts[tile.inst];
+  const Dims d = I.d;
+  const Par<T> p = I.p;
+  const T* __restrict__ gin = I.g[cur];
+  T* __restrict__ gout = I.g[cur ^ 1];
+  const Field<T> U = I.u;
+  const int zoff = U.L.zoff;
+  const CUtensorMap* qmap = &qmaps[2 * tile.inst + cur];
+
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
-  const int z0 = DIM == 3 ? blockIdx.z * tz : 0;
-  const int z1 = DIM == 3 ? min(z0 + tz, d.nz) : 1;
+  const int x0 = tile.x0, y0 = tile.y0;
+  const int z0 = tile.z0;
+  const int z1 = DIM == 3 ? min(z0 + I.tz, d.nz) : 1;
   const int zq0 = DIM == 3 ? z0 - 2 : 0;  // first Q plane loaded
   const int zp0 = DIM == 3 ? z0 - 1 : 0;  // first Pi plane computed
   auto qslot = [&](int z) { return (z - zq0) % C::NSQ; };
@@ -132,7 +164,7 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   auto issue = [&](int z) {  // thread 0 only
     const int s = qslot(z);
     mbar_expect_tx(&bars[s], C::tx_bytes);
-    tma_load_4d(sQ(s), &qmap, x0, y0, z + zoff, 0, &bars[s]);
+    tma_load_4d(sQ(s), qmap, x0, y0, z + zoff, 0, &bars[s]);
   };
   bool late = false;
   auto wait = [&](int z) { late |= !mbar_wait(&bars[qslot(z)], qpar(z)); };
@@ -149,17 +181,19 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   const int tx = tid % FTX, ty = tid / FTX;
   const int x = x0 + tx, y = y0 + ty;
   const bool cell = tid < FTX * FTY && x < d.nx && y < d.ny;
+  // source offsets within a plane for c_x, c_y in {-1, 0, 1} (index c + 1);
+  // a lattice holds fewer than 2^31 cells, so 32-bit offsets suffice
   int colx[3] = {0, 0, 0};
-  int64_t rowy[3] = {0, 0, 0};
+  int rowy[3] = {0, 0, 0};
   if (cell) {
-    colx[0] = wrap_inc(x, d.nx);  // source x for c_x = -1 ... index c_x + 1
+    colx[0] = wrap_inc(x, d.nx);
     colx[1] = x;
     colx[2] = wrap_dec(x, d.nx);
-    rowy[0] = (int64_t)wrap_inc(y, d.ny) * d.nx;
-    rowy[1] = (int64_t)y * d.nx;
-    rowy[2] = (int64_t)wrap_dec(y, d.ny) * d.nx;
+    rowy[0] = wrap_inc(y, d.ny) * d.nx;
+    rowy[1] = y * d.nx;
+    rowy[2] = wrap_dec(y, d.ny) * d.nx;
   }
-  const int64_t nxy = (int64_t)d.nx * d.ny;
+  const int nxy = d.nx * d.ny;
   const int ic = (ty + 1) * RX1 + (tx + 1);
 
   auto lb_cell = [&](int z) {
@@ -175,20 +209,21 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
       if (DIM == 3) s += (Pp[(a * DIM + 2) * A1 + ic] - Pm[(a * DIM + 2) * A1 + ic]) / T(2);
       F[a] = s;
     }
-    int64_t plane[3];
-    plane[1] = (int64_t)z * nxy;
-    plane[0] = DIM == 3 ? (int64_t)wrap_inc(z, d.nz) * nxy : plane[1];
-    plane[2] = DIM == 3 ? (int64_t)wrap_dec(z, d.nz) * nxy : plane[1];
+    int plane[3];
+    plane[1] = z * nxy;
+    plane[0] = DIM == 3 ? wrap_inc(z, d.nz) * nxy : plane[1];
+    plane[2] = DIM == 3 ? wrap_dec(z, d.nz) * nxy : plane[1];
     T g[Lat::Q], rho, u[3];
 #pragma unroll
-    for (int i = 0; i < Lat::Q; i++)
-      g[i] = gin[(int64_t)i * d.n + plane[Lat::c(i, 2) + 1] + rowy[Lat::c(i, 1) + 1] +
-                 colx[Lat::c(i, 0) + 1]];
+    for (int i = 0; i < Lat::Q; i++) {
+      const int64_t off = (int64_t)i * d.n + plane[Lat::c(i, 2) + 1] + rowy[Lat::c(i, 1) + 1] + colx[Lat::c(i, 0) + 1];
+      g[i] = gin[off];
+    }
     moments<Lat, T>(g, F, p, rho, u);
     collide_bgk<Lat, T>(g, rho, u, F, p);
-    const int64_t o = plane[1] + rowy[1] + x;
+    const int o = plane[1] + rowy[1] + x;
 #pragma unroll
-    for (int i = 0; i < Lat::Q; i++) gout[(int64_t)i * d.n + o] = g[i];
+    for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * (size_t)d.n + o] = g[i];
     store_with_images<T, DIM, DIM>(U, d, x, y, z, u);
   };
 
@@ -282,9 +317,11 @@ __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
 
 template <class Lat, class T>
 __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
-    k_fused_be(const __grid_constant__ CUtensorMap qmap,
-               const __grid_constant__ CUtensorMap umap, Field<T> Qout, Dims d,
-               Par<T> p, int tz, int zoff, unsigned* __restrict__ err) {
+    k_fused_be(const InstDev<T>* __restrict__ insts,
+               const CUtensorMap* __restrict__ qmaps,
+               const CUtensorMap* __restrict__ umaps,
+               const TileRef* __restrict__ tiles, int cur,
+               unsigned* __restrict__ err) {
   using C = BeCfg<Lat, T>;
   constexpr int DIM = Lat::DIM;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -295,10 +332,19 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   auto sQP = [&](int s) { return reinterpret_cast<T*>(smem + C::off_p + s * C::p_slot); };
   auto sR = [&](int s) { return reinterpret_cast<T*>(smem + C::off_r + s * C::p_slot); };
 
+  const TileRef tile = tiles[blockIdx.x];
+  const InstDev<T>& I = insts[tile.inst];
+  const Dims d = I.d;
+  const Par<T> p = I.p;
+  const Field<T> Qout = I.q[cur ^ 1];
+  const int zoff = Qout.L.zoff;
+  const CUtensorMap* qmap = &qmaps[2 * tile.inst + cur];
+  const CUtensorMap* umap = &umaps[tile.inst];
+
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
-  const int z0 = DIM == 3 ? blockIdx.z * tz : 0;
-  const int z1 = DIM == 3 ? min(z0 + tz, d.nz) : 1;
+  const int x0 = tile.x0, y0 = tile.y0;
+  const int z0 = tile.z0;
+  const int z1 = DIM == 3 ? min(z0 + I.tz, d.nz) : 1;
   const int zl0 = DIM == 3 ? z0 - 2 : 0;  // first loaded plane
   const int zr0 = DIM == 3 ? z0 - 1 : 0;  // first predicted plane
   auto qs = [&](int z) { return (z - zl0) % C::NSQ; };
@@ -316,12 +362,12 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   auto issue_q = [&](int z) {
     const int s = qs(z);
     mbar_expect_tx(&qbar[s], C::q_tx);
-    tma_load_4d(sQ(s), &qmap, x0, y0, z + zoff, 0, &qbar[s]);
+    tma_load_4d(sQ(s), qmap, x0, y0, z + zoff, 0, &qbar[s]);
   };
   auto issue_u = [&](int z) {
     const int s = us(z);
     mbar_expect_tx(&ubar[s], C::u_tx);
-    tma_load_4d(sU(s), &umap, x0, y0, z + zoff, 0, &ubar[s]);
+    tma_load_4d(sU(s), umap, x0, y0, z + zoff, 0, &ubar[s]);
   };
   bool late = false;
   auto wait_q = [&](int z) { late |= !mbar_wait(&qbar[qs(z)], qpar(z)); };
@@ -464,21 +510,26 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-template <class Lat>
-__host__ inline dim3 fused_grid(const Dims& d, int tz) {
-  return dim3((unsigned)((d.nx + FTX - 1) / FTX), (unsigned)((d.ny + FTY - 1) / FTY),
-              Lat::DIM == 3 ? (unsigned)((d.nz + tz - 1) / tz) : 1u);
-}
 
-// z planes per block on D3Q19: enough blocks for several waves over the SMs
+// z planes per tile on D3Q19: enough tiles for several waves over the SMs
 // while amortising the two-plane prologue of each chunk
 template <class Lat>
-__host__ inline int fused_tz(const Dims& d) {
+__host__ inline int fused_tz(const Dims& d, int64_t other_tiles) {
   if (Lat::DIM == 2) return 1;
   const int64_t tiles = (int64_t)((d.nx + FTX - 1) / FTX) * ((d.ny + FTY - 1) / FTY);
   int tz = 32;
-  while (tz > 4 && tiles * ((d.nz + tz - 1) / tz) < 1200) tz /= 2;
+  while (tz > 4 && other_tiles + tiles * ((d.nz + tz - 1) / tz) < 1200) tz /= 2;
   return tz < d.nz ? tz : d.nz;
+}
+
+// tile list of one instance, x fastest so neighbouring blocks share halos
+template <class Lat>
+__host__ inline void append_tiles(int inst, const Dims& d, int tz,
+                                  std::vector<TileRef>* out) {
+  const int nzc = Lat::DIM == 3 ? (d.nz + tz - 1) / tz : 1;
+  for (int zc = 0; zc < nzc; zc++)
+    for (int y0 = 0; y0 < d.ny; y0 += FTY)
+      for (int x0 = 0; x0 < d.nx; x0 += FTX) out->push_back({inst, x0, y0, zc * tz});
 }
 
 template <class K>
@@ -494,28 +545,25 @@ inline cudaError_t set_smem(K kernel, size_t bytes, unsigned long long* done_mas
 }
 
 template <class Lat, class T>
-cudaError_t launch_fused_lb(const CUtensorMap& qmap, const T* gin, T* gout,
-                            const Field<T>& U, const Dims& d, const Par<T>& p,
-                            unsigned* err, cudaStream_t st) {
+cudaError_t launch_fused_lb(const InstDev<T>* insts, const CUtensorMap* qmaps,
+                            const TileRef* tiles, int ntiles, int cur, unsigned* err,
+                            cudaStream_t st) {
   static unsigned long long configured = 0;
   cudaError_t e = set_smem(k_fused_lb<Lat, T>, LbCfg<Lat, T>::bytes, &configured);
   if (e != cudaSuccess) return e;
-  const int tz = fused_tz<Lat>(d);
-  k_fused_lb<Lat, T><<<fused_grid<Lat>(d, tz), FNT, LbCfg<Lat, T>::bytes, st>>>(
-      qmap, gin, gout, U, d, p, tz, U.L.zoff, err);
+  k_fused_lb<Lat, T><<<ntiles, FNT, LbCfg<Lat, T>::bytes, st>>>(insts, qmaps, tiles, cur, err);
   return cudaGetLastError();
 }
 
 template <class Lat, class T>
-cudaError_t launch_fused_be(const CUtensorMap& qmap, const CUtensorMap& umap,
-                            const Field<T>& Qout, const Dims& d, const Par<T>& p,
-                            unsigned* err, cudaStream_t st) {
+cudaError_t launch_fused_be(const InstDev<T>* insts, const CUtensorMap* qmaps,
+                            const CUtensorMap* umaps, const TileRef* tiles, int ntiles,
+                            int cur, unsigned* err, cudaStream_t st) {
   static unsigned long long configured = 0;
   cudaError_t e = set_smem(k_fused_be<Lat, T>, BeCfg<Lat, T>::bytes, &configured);
   if (e != cudaSuccess) return e;
-  const int tz = fused_tz<Lat>(d);
-  k_fused_be<Lat, T><<<fused_grid<Lat>(d, tz), FNT, BeCfg<Lat, T>::bytes, st>>>(
-      qmap, umap, Qout, d, p, tz, Qout.L.zoff, err);
+  k_fused_be<Lat, T><<<ntiles, FNT, BeCfg<Lat, T>::bytes, st>>>(insts, qmaps, umaps, tiles,
+                                                                 cur, err);
   return cudaGetLastError();
 }
 

@@ -76,6 +76,9 @@ def load(build_if_missing=True):
     sig = {
         "nlc_create": ([ctypes.POINTER(nlc_grid), ctypes.POINTER(nlc_params),
                         P, ctypes.POINTER(P)], I32),
+        "nlc_create_batch": ([I32, P, P, P, ctypes.POINTER(P)], I32),
+        "nlc_count": ([P], I32),
+        "nlc_set_graph": ([P, I32], I32),
         "nlc_set_schedule": ([P, I32], I32),
         "nlc_set_fields": ([P, I32, P, P, P], I32),
         "nlc_get_fields": ([P, I32, P, P, P], I32),
@@ -101,7 +104,8 @@ def load(build_if_missing=True):
 
 
 def exported_symbols():
-    return ["nlc_create", "nlc_set_schedule", "nlc_set_fields",
+    return ["nlc_create", "nlc_create_batch", "nlc_count", "nlc_set_graph",
+            "nlc_set_schedule", "nlc_set_fields",
             "nlc_get_fields", "nlc_get_populations", "nlc_step",
             "nlc_observables", "nlc_last_error", "nlc_destroy",
             "nlc_lattice_velocities", "nlc_version", "nlc_set_timing",
@@ -136,6 +140,27 @@ def nlc_create(grid, params, stream=None):
                         ctypes.c_void_p(stream or 0), ctypes.byref(ctx))
     _check(None, st)
     return ctx
+
+
+def nlc_create_batch(grids, params, stream=None):
+    lib = load()
+    n = len(grids)
+    G = (nlc_grid * n)(*grids)
+    Pm = (nlc_params * n)(*params)
+    ctx = ctypes.c_void_p()
+    st = lib.nlc_create_batch(n, ctypes.cast(G, ctypes.c_void_p),
+                              ctypes.cast(Pm, ctypes.c_void_p),
+                              ctypes.c_void_p(stream or 0), ctypes.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def nlc_count(ctx):
+    return load().nlc_count(ctx)
+
+
+def nlc_set_graph(ctx, steps):
+    _check(ctx, load().nlc_set_graph(ctx, int(steps)))
 
 
 def nlc_set_schedule(ctx, schedule):
@@ -218,7 +243,70 @@ def nlc_version():
     return load().nlc_version().decode()
 
 
-# -- convenience wrapper -----------------------------------------------------
+# -- convenience wrappers ----------------------------------------------------
+
+def _params(d):
+    return nlc_params(d["A0"], d["K"], d["gamma"], d["Gamma"], d["xi"],
+                      d["tau"], d.get("rho0", 1.0))
+
+
+class Batch:
+    """Several lattices (same lattice type and precision) advanced together.
+
+    shapes: list of (nz, ny, nx); params: list of parameter dicts."""
+
+    def __init__(self, lattice, shapes, params, precision=NLC_FP32,
+                 stream=None, graph_steps=0):
+        self.lattice = lattice
+        self.q = 9 if lattice == NLC_D2Q9 else 19
+        self.shapes = [tuple(s) for s in shapes]
+        grids = [nlc_grid(s[2], s[1], s[0], lattice, precision)
+                 for s in self.shapes]
+        self.ctx = nlc_create_batch(grids, [_params(p) for p in params],
+                                    stream)
+        if graph_steps:
+            nlc_set_graph(self.ctx, graph_steps)
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def set_fields(self, i, Q5, rho=None, u=None):
+        sh = self.shapes[i]
+        nlc_set_fields(self.ctx, i, _f64(Q5, (5,) + sh), _f64(rho, sh),
+                       _f64(u, (3,) + sh))
+
+    def get_fields(self, i):
+        sh = self.shapes[i]
+        Q5, rho, u = np.empty((5,) + sh), np.empty(sh), np.empty((3,) + sh)
+        nlc_get_fields(self.ctx, i, Q5, rho, u)
+        return Q5, rho, u
+
+    def get_populations(self, i):
+        f = np.empty((self.q,) + self.shapes[i])
+        nlc_get_populations(self.ctx, i, f)
+        return f
+
+    def step(self, n=1):
+        nlc_step(self.ctx, n)
+
+    def observables(self, i, profile=False):
+        prof = np.empty(self.shapes[i][2]) if profile else None
+        d = nlc_observables(self.ctx, i, prof).as_dict()
+        if profile:
+            d["s_profile"] = prof
+        return d
+
+    def close(self):
+        if self.ctx:
+            nlc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 class Simulation:
     """One lattice on the current CUDA device.
@@ -280,6 +368,9 @@ class Simulation:
 
     def load_state(self, data):
         nlc_load(self.ctx, data)
+
+    def set_graph(self, steps):
+        nlc_set_graph(self.ctx, steps)
 
     def close(self):
         if self.ctx:

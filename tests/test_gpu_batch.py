@@ -1,0 +1,121 @@
+"""Batched contexts (nlc_create_batch): several lattices of different extents
+and parameters advanced by the same kernel launches, and CUDA-graph replay."""
+import numpy as np
+import pytest
+
+from paper_1907_13415_gb300 import workloads as wl
+
+from helpers import perm_to_oracle, rel, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def sweep_members():
+    """Uneven flat-interface lattices across gamma (the temperature-sweep
+    recipe at parity size)."""
+    out = []
+    for i, (lx, ly, g) in enumerate([(64, 8, 2.62), (40, 16, 2.70),
+                                     (97, 3, 2.75), (33, 9, 2.80),
+                                     (1, 1, 2.7)]):
+        p = dict(wl.BASE_PARAMS, gamma=g)
+        out.append(wl.Workload(f"m{i}", wl.D2Q9, (1, ly, lx), p, 0, "slab",
+                               max(1, lx // 2), (0.2, 0.9, 0.1), 1e-3, 20 + i))
+    return out
+
+
+def test_batch_d2q9_fp64_matches_oracle(orc):
+    from paper_1907_13415_gb300 import nlc
+    ws = sweep_members()
+    b = nlc.Batch(wl.D2Q9, [w.shape for w in ws], [w.params for w in ws],
+                  precision=nlc.NLC_FP64, stream=stream())
+    for i, w in enumerate(ws):
+        b.set_fields(i, w.initial_q5())
+    b.step(40)
+    perm = perm_to_oracle(orc, wl.D2Q9)
+    for i, w in enumerate(ws):
+        o = run_oracle(orc, w, 40)
+        Q, rho, u = b.get_fields(i)
+        f = b.get_populations(i)
+        assert rel(Q, o["Q"]) < 1e-12, i
+        assert rel(f, o["f"][perm]) < 1e-12, i
+        assert b.observables(i)["step"] == 40
+    b.close()
+
+
+def test_batch_d3q19_fp64_matches_oracle(orc):
+    from paper_1907_13415_gb300 import nlc
+    base = wl.sphere_256()
+    ws = [base.with_(shape=(9, 10, 33), size=3.5, noise=1e-3, seed=31),
+          base.with_(shape=(5, 17, 20), size=3.0, noise=1e-3, seed=32,
+                     params=dict(base.params, gamma=2.68))]
+    b = nlc.Batch(wl.D3Q19, [w.shape for w in ws], [w.params for w in ws],
+                  precision=nlc.NLC_FP64, stream=stream())
+    for i, w in enumerate(ws):
+        b.set_fields(i, w.initial_q5())
+    b.step(8)
+    perm = perm_to_oracle(orc, wl.D3Q19)
+    for i, w in enumerate(ws):
+        o = run_oracle(orc, w, 8)
+        Q, _, _ = b.get_fields(i)
+        assert rel(Q, o["Q"]) < 1e-12, i
+        assert rel(b.get_populations(i), o["f"][perm]) < 1e-12, i
+    b.close()
+
+
+def test_batch_equals_single_contexts_bitwise():
+    """A lattice advanced inside a batch gives exactly what it gives alone."""
+    from paper_1907_13415_gb300 import nlc
+    ws = sweep_members()[:4]
+    b = nlc.Batch(wl.D2Q9, [w.shape for w in ws], [w.params for w in ws],
+                  precision=nlc.NLC_FP32, stream=stream())
+    for i, w in enumerate(ws):
+        b.set_fields(i, w.initial_q5())
+    b.step(25)
+    for i, w in enumerate(ws):
+        s = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                           stream=stream())
+        s.set_fields(w.initial_q5())
+        s.step(25)
+        assert np.array_equal(s.get_populations(), b.get_populations(i))
+        assert np.array_equal(s.get_fields()[0], b.get_fields(i)[0])
+        s.close()
+    b.close()
+
+
+@pytest.mark.parametrize("chunk", [1, 4, 5])
+def test_graph_replay_is_bitwise_identical(chunk):
+    from paper_1907_13415_gb300 import nlc
+    ws = sweep_members()[:3]
+    out = []
+    for g in (0, chunk):
+        b = nlc.Batch(wl.D2Q9, [w.shape for w in ws], [w.params for w in ws],
+                      precision=nlc.NLC_FP32, stream=stream(), graph_steps=g)
+        for i, w in enumerate(ws):
+            b.set_fields(i, w.initial_q5())
+        b.step(13)
+        b.step(7)
+        out.append([b.get_populations(i) for i in range(len(ws))])
+        b.close()
+    for a, c in zip(out[0], out[1]):
+        assert np.array_equal(a, c)
+
+
+def test_batch_rejects_mixed_lattices():
+    from paper_1907_13415_gb300 import nlc
+    p = nlc._params(wl.BASE_PARAMS)
+    grids = [nlc.nlc_grid(8, 8, 1, nlc.NLC_D2Q9, 1), nlc.nlc_grid(8, 8, 4, nlc.NLC_D3Q19, 1)]
+    with pytest.raises(nlc.NlcError):
+        nlc.nlc_create_batch(grids, [p, p], stream())
