@@ -62,6 +62,22 @@ __device__ __forceinline__ int64_t cell_of(const Dims& d, int x, int y, int z) {
   return (int64_t)x + (int64_t)d.nx * ((int64_t)y + (int64_t)d.ny * z);
 }
 
+// Images of coordinate v (0 <= v < n) in the ghost ring: bit (k + GHOST) of
+// the result is set when v + k n lies in [-GHOST, n + GHOST), k != 0.
+__device__ __forceinline__ unsigned image_mask(int v, int n) {
+  unsigned m = 0;
+  if (n > 2 * GHOST) {  // at most one image on each side
+    if (v < GHOST) m |= 1u << (GHOST + 1);
+    if (v >= n - GHOST) m |= 1u << (GHOST - 1);
+    return m;
+  }
+  for (int k = -GHOST; k <= GHOST; k++) {
+    const int vi = v + k * n;
+    if (k != 0 && vi >= -GHOST && vi < n + GHOST) m |= 1u << (k + GHOST);
+  }
+  return m;
+}
+
 // Stores NC component values of cell (x, y, z) of a padded field, and every
 // periodic image of the cell that falls in the ghost ring.  Only cells within
 // GHOST of a face have images; lattices thinner than the ring get several.
@@ -71,21 +87,20 @@ __device__ __forceinline__ void store_with_images(const Field<T>& F, const Dims&
                                                   const T v[NC]) {
 #pragma unroll
   for (int k = 0; k < NC; k++) F.at(k, x, y, z) = v[k];
-  const bool inner = x >= GHOST && x < d.nx - GHOST && y >= GHOST &&
-                     y < d.ny - GHOST &&
-                     (DIM == 2 || (z >= GHOST && z < d.nz - GHOST));
-  if (inner) return;
-  const int kz0 = DIM == 3 ? -GHOST : 0, kz1 = DIM == 3 ? GHOST : 0;
-  for (int kz = kz0; kz <= kz1; kz++) {
-    const int zi = z + kz * d.nz;
-    if (zi < -GHOST || zi >= d.nz + GHOST) continue;
+  const unsigned mx = image_mask(x, d.nx), my = image_mask(y, d.ny);
+  const unsigned mz = DIM == 3 ? image_mask(z, d.nz) : 0u;
+  if ((mx | my | mz) == 0) return;
+  // offsets per axis: 0 plus every image offset
+  const unsigned ax = mx | (1u << GHOST), ay = my | (1u << GHOST);
+  const unsigned az = mz | (1u << GHOST);
+  for (int kz = -GHOST; kz <= GHOST; kz++) {
+    if (!(az >> (kz + GHOST) & 1u)) continue;
     for (int ky = -GHOST; ky <= GHOST; ky++) {
-      const int yi = y + ky * d.ny;
-      if (yi < -GHOST || yi >= d.ny + GHOST) continue;
+      if (!(ay >> (ky + GHOST) & 1u)) continue;
       for (int kx = -GHOST; kx <= GHOST; kx++) {
-        const int xi = x + kx * d.nx;
-        if (xi < -GHOST || xi >= d.nx + GHOST) continue;
+        if (!(ax >> (kx + GHOST) & 1u)) continue;
         if (kx == 0 && ky == 0 && kz == 0) continue;
+        const int xi = x + kx * d.nx, yi = y + ky * d.ny, zi = z + kz * d.nz;
 #pragma unroll
         for (int k = 0; k < NC; k++) F.at(k, xi, yi, zi) = v[k];
       }

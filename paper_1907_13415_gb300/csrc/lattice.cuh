@@ -19,6 +19,10 @@ struct LatD2Q9 {
   __host__ __device__ static constexpr double w(int i) {
     return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
   }
+  // index of the opposite velocity -c_i
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1);
+  }
 };
 
 struct LatD3Q19 {
@@ -35,6 +39,11 @@ struct LatD3Q19 {
   __host__ __device__ static constexpr double w(int i) {
     return i == 0 ? 1.0 / 3.0
                   : ((i <= 4 || i == 9 || i == 14) ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+  // index of the opposite velocity -c_i
+  __host__ __device__ static constexpr int opp(int i) {
+    constexpr int t[19] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 14, 16, 15, 18, 17, 9, 11, 10, 13, 12};
+    return t[i];
   }
 };
 

@@ -160,15 +160,24 @@ __host__ __device__ __forceinline__ void be_rhs(const T q[5], const T dq[3][5],
 // Equilibrium deviation g^eq_i = f^eq_i - w_i rho0, with
 // f^eq_i = rho w_i [1 + c.u/cs2 + (c.u)^2/(2 cs2^2) - u^2/(2 cs2)] (Sec. 1.2.1)
 // and the BGK source term
-// S_i = w_i (1 - 1/2tau) [c_i/cs2 (1 + c_i.u/cs2) - u/cs2] . F.
+// S_i = w_i (1 - 1/2tau) [c_i/cs2 (1 + c_i.u/cs2) - u/cs2] . F,
+// cs2 = 1/3.  Opposite velocities c_j = -c_i share the even parts
+//   g^eq: w (drho + rho (9/2 (c.u)^2 - 3/2 u.u)),  S: w k (9 (c.F)(c.u) - 3 u.F)
+// and carry the odd parts with opposite signs
+//   g^eq: w rho 3 c.u,                             S: w k 3 c.F.
 template <class Lat, class T>
 __host__ __device__ __forceinline__ void collide_bgk(T g[Lat::Q], T rho, const T u[3],
-                                            const T F[3], const Par<T>& p) {
+                                                     const T F[3], const Par<T>& p) {
   const T uu = u[0] * u[0] + u[1] * u[1] + (Lat::DIM == 3 ? u[2] * u[2] : T(0));
   const T uF = u[0] * F[0] + u[1] * F[1] + (Lat::DIM == 3 ? u[2] * F[2] : T(0));
   const T drho = rho - p.rho0;
+  const T keep = T(1) - p.inv_tau;  // g - (g - geq)/tau = keep g + geq/tau
+  const T ev_eq = drho - T(1.5) * rho * uu;  // even part shared by every i
+  const T ev_src = -T(3) * p.guo * uF;
 #pragma unroll
   for (int i = 0; i < Lat::Q; i++) {
+    const int j = Lat::opp(i);
+    if (j < i) continue;  // handled with its partner
     const T w = T(Lat::w(i));
     T cu = T(Lat::c(i, 0)) * u[0] + T(Lat::c(i, 1)) * u[1];
     T cF = T(Lat::c(i, 0)) * F[0] + T(Lat::c(i, 1)) * F[1];
@@ -176,10 +185,36 @@ __host__ __device__ __forceinline__ void collide_bgk(T g[Lat::Q], T rho, const T
       cu += T(Lat::c(i, 2)) * u[2];
       cF += T(Lat::c(i, 2)) * F[2];
     }
-    const T geq = w * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-    const T src = w * p.guo * (T(3) * cF * (T(1) + T(3) * cu) - T(3) * uF);
-    g[i] = g[i] - (g[i] - geq) * p.inv_tau + src;
+    const T e_eq = w * (ev_eq + T(4.5) * rho * cu * cu);
+    const T o_eq = w * T(3) * rho * cu;
+    const T e_src = w * (ev_src + T(9) * p.guo * cF * cu);
+    const T o_src = w * T(3) * p.guo * cF;
+    const T gi = g[i];
+    g[i] = keep * gi + (e_eq + o_eq) * p.inv_tau + (e_src + o_src);
+    if (j != i) {
+      const T gj = g[j];
+      g[j] = keep * gj + (e_eq - o_eq) * p.inv_tau + (e_src - o_src);
+    }
   }
+}
+
+// rho = rho0 + sum g, u = (sum c g + F/2) / rho  (Eq. 6; sum c w rho0 = 0)
+template <class Lat, class T>
+__host__ __device__ __forceinline__ void moments(const T g[Lat::Q], const T F[3],
+                                        const Par<T>& p, T& rho, T u[3]) {
+  T s = T(0), m[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i < Lat::Q; i++) {
+    s += g[i];
+#pragma unroll
+    for (int a = 0; a < Lat::DIM; a++)
+      if (Lat::c(i, a) != 0) m[a] += T(Lat::c(i, a)) * g[i];
+  }
+  rho = p.rho0 + s;
+  const T inv = T(1) / rho;
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+    u[a] = a < Lat::DIM ? (m[a] + F[a] / T(2)) * inv : T(0);
 }
 
 }  // namespace nlc

@@ -127,25 +127,6 @@ __device__ __forceinline__ void pull(const T* __restrict__ gin, const Dims& d,
   }
 }
 
-// rho = rho0 + sum g, u = (sum c g + F/2) / rho  (Eq. 6; sum c w rho0 = 0)
-template <class Lat, class T>
-__device__ __forceinline__ void moments(const T g[Lat::Q], const T F[3],
-                                        const Par<T>& p, T& rho, T u[3]) {
-  T s = T(0), m[3] = {T(0), T(0), T(0)};
-#pragma unroll
-  for (int i = 0; i < Lat::Q; i++) {
-    s += g[i];
-#pragma unroll
-    for (int a = 0; a < Lat::DIM; a++)
-      if (Lat::c(i, a) != 0) m[a] += T(Lat::c(i, a)) * g[i];
-  }
-  rho = p.rho0 + s;
-  const T inv = T(1) / rho;
-#pragma unroll
-  for (int a = 0; a < 3; a++)
-    u[a] = a < Lat::DIM ? (m[a] + F[a] / T(2)) * inv : T(0);
-}
-
 template <class Lat, class T>
 __global__ void __launch_bounds__(256) k_lb(const T* __restrict__ gin,
                                             T* __restrict__ gout,

@@ -23,8 +23,11 @@ def hp(tmp_path_factory):
                            "-Xcompiler", "-fPIC", "-shared", "-x", "cu",
                            os.path.join(HERE, "host_physics.cu"), "-o", str(out)])
     lib = ctypes.CDLL(str(out))
-    for name in ("hp_molecular_field", "hp_stress3", "hp_corotation", "hp_be_rhs3"):
+    for name in ("hp_molecular_field", "hp_stress3", "hp_corotation", "hp_be_rhs3",
+                 "hp_lattice"):
         getattr(lib, name).restype = None
+    lib.hp_collide.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.hp_corotation.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                   ctypes.c_void_p]
     return lib
@@ -109,3 +112,80 @@ def test_rhs_traceless_projection(hp, orc):
         R = -np.einsum("g,gab->ab", u, dQ) + S + p[3] * H
         R -= np.trace(R) / 3 * np.eye(3)
         assert np.allclose(r, [R[a, b] for a, b in IDX5], rtol=1e-12, atol=1e-16)
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_collision_with_source(hp, orc, lattice):
+    """The pairwise BGK + source update against f - (f - feq)/tau + S_i from
+    the oracle's equilibrium and source term (same velocity matched up)."""
+    q = 9 if lattice == 0 else 19
+    c = np.zeros((q, 3), dtype=np.int32)
+    w = np.zeros(q)
+    hp.hp_lattice(lattice, P(c), P(w))
+    co, wo = orc.lattice(lattice)
+    perm = [int(np.where((co == cv).all(axis=1))[0][0]) for cv in c]
+    rng = np.random.default_rng(4)
+    d = 2 if lattice == 0 else 3
+    for _ in range(30):
+        p = params(rng)
+        rho = 1 + 0.05 * rng.normal()
+        u = np.zeros(3)
+        u[:d] = rng.normal(scale=0.05, size=d)
+        F = np.zeros(3)
+        F[:d] = rng.normal(scale=1e-3, size=d)
+        f = orc.equilibrium_point(lattice, rho, u) + rng.normal(scale=1e-3, size=q)
+        g = f[perm] - w
+        hp.hp_collide(lattice, P(g), rho, P(u), P(F), P(p))
+        feq = orc.equilibrium_point(lattice, rho, u)
+        S = orc.guo_point(lattice, p[5], u, F)
+        ref = f - (f - feq) / p[5] + S
+        assert np.allclose(g + w, ref[perm], rtol=0, atol=1e-15)
+
+
+# piece id: (inputs, outputs)
+PIECES = {0: (10, 5), 1: (25, 9), 2: (14, 5), 3: (37, 5), 4: (11, 12), 5: (22, 22)}
+
+
+def piece_input(k, rng):
+    if k == 0:
+        return np.concatenate([sym5(rng)[1], sym5(rng)[1]])
+    if k == 1:
+        return np.concatenate([sym5(rng)[1], sym5(rng)[1]] + [sym5(rng)[1] for _ in range(3)])
+    if k == 2:
+        return np.concatenate([rng.normal(size=9), sym5(rng)[1]])
+    if k == 3:
+        return np.concatenate([sym5(rng)[1]] + [sym5(rng)[1] for _ in range(3)]
+                              + [sym5(rng)[1], rng.normal(scale=0.05, size=3),
+                                 rng.normal(scale=0.05, size=9)])
+    q = 9 if k == 4 else 19
+    g = rng.normal(scale=0.01, size=q)
+    F = rng.normal(scale=1e-3, size=2 if k == 4 else 3)
+    return np.concatenate([g, F])
+
+
+@pytest.mark.parametrize("k", sorted(PIECES))
+def test_pointwise_adjoints_dot_product(hp, k):
+    """<ob, J v> (complex step) == <J^T ob, v> + <pb, vp> (hand adjoint) for
+    H, the stress, the co-rotation, Eq. 1's right-hand side and the LB cell
+    update (moments + collision), including the gamma, K, Gamma adjoints."""
+    nin, nout = PIECES[k]
+    rng = np.random.default_rng(100 + k)
+    hp.hp_piece_jvp.restype = None
+    hp.hp_piece_vjp.restype = None
+    for _ in range(20):
+        x = piece_input(k, rng)
+        assert x.size == nin
+        p = params(rng)
+        v = rng.normal(size=nin)
+        vp = np.zeros(6)
+        vp[[1, 2, 3]] = rng.normal(size=3)  # K, gamma, Gamma
+        jv = np.zeros(nout)
+        hp.hp_piece_jvp(ctypes.c_int(k), P(x), ctypes.c_int(nin), P(p), P(v), P(vp),
+                        ctypes.c_int(nout), P(jv))
+        ob = rng.normal(size=nout)
+        ib = np.zeros(nin)
+        pb = np.zeros(3)
+        hp.hp_piece_vjp(ctypes.c_int(k), P(x), P(p), P(ob), P(ib), P(pb))
+        lhs = ob @ jv
+        rhs = ib @ v + pb[0] * vp[2] + pb[1] * vp[1] + pb[2] * vp[3]
+        assert lhs == pytest.approx(rhs, rel=1e-11, abs=1e-13)
