@@ -443,6 +443,51 @@ def run_sweep(args):
     return 0
 
 
+def run_adjoint(args):
+    """Adjoint cost: the 128x128 D2Q9 droplet (R = 24, gamma = 2.70),
+    2000 steps with checkpoints every 100, FP32.  Ratio of one nlc_adjoint
+    call (its forward sweep, the recomputation and the reverse sweep) to one
+    plain forward run of the same steps."""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    from paper_1907_13415_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    w = wl.adjoint_disc_128()
+    steps, ckpt = w.steps, w.extra["ckpt_every"]
+    sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                         stream=stream.cuda_stream)
+    Q0 = w.initial_q5()
+
+    def fwd():
+        sim.set_fields(Q0)
+        t0 = time.perf_counter()
+        sim.step(steps)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    def adj():
+        sim.set_fields(Q0)
+        t0 = time.perf_counter()
+        g = sim.adjoint(24.0, 1.0, 1.0, nsteps=steps, ckpt_every=ckpt)
+        return time.perf_counter() - t0, g
+
+    fwd()
+    adj()
+    tf = min(fwd() for _ in range(3))
+    runs = [adj() for _ in range(3)]
+    ta = min(r[0] for r in runs)
+    g = runs[0][1]
+    sim.close()
+    out = {"metric": "adjoint/forward time", "value": ta / tf, "unit": "ratio",
+           "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "steps": steps, "ckpt_every": ckpt},
+           "forward_s": tf, "adjoint_s": ta,
+           "gradient": {k: g[k] for k in ("loss", "radius", "dgamma", "dK", "dGamma")}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -458,7 +503,7 @@ def main():
                          "the default 256^3")
     ap.add_argument("--schedule", default="fused", choices=["fused", "unfused"])
     ap.add_argument("--workload", default="sphere256",
-                    choices=["sphere256", "sweep64"],
+                    choices=["sphere256", "sweep64", "adjoint128"],
                     help="sweep64: batched vs sequential temperature sweep")
     ap.add_argument("--graph-steps", type=int, default=50)
     args = ap.parse_args()
@@ -467,6 +512,8 @@ def main():
     from paper_1907_13415_gb300 import workloads as wl
     if args.workload == "sweep64":
         return run_sweep(args)
+    if args.workload == "adjoint128":
+        return run_adjoint(args)
     w = wl.sphere_256()
     if args.shape:
         nz, ny, nx = (int(v) for v in args.shape.split(","))

@@ -106,9 +106,24 @@ typedef struct {
  *   step        time steps taken since the last nlc_set_fields             */
 typedef struct {
   double mass, mom[3], s_area, radius, x_iface, max_u, free_energy;
+  double u_l2;  /* sqrt(sum over cells of |u|^2) */
   int64_t nonfinite;
   int64_t step;
 } nlc_obs;
+
+/* Loss of the droplet problem: L = w_radius (radius - target_radius)^2
+ * + w_velocity sqrt(sum_x |u(x)|^2), evaluated on the state after the run
+ * (radius and u as in nlc_obs). */
+typedef struct {
+  double target_radius, w_radius, w_velocity;
+} nlc_loss;
+
+/* Result of nlc_adjoint: the loss, its parts, and dL/dgamma, dL/dK,
+ * dL/dGamma (FP64 accumulations). */
+typedef struct {
+  double loss, radius, u_l2;
+  double dgamma, dK, dGamma;
+} nlc_grad;
 
 typedef struct nlc_ctx nlc_ctx;
 
@@ -203,13 +218,30 @@ NLC_API nlc_status nlc_set_timing(nlc_ctx* ctx, int32_t enable);
  * total_ms[k] milliseconds and launches[k] launch counts (arrays of at least
  * max_kernels entries; either may be NULL).  *n_kernels (may be NULL) gets
  * NLC_N_KERNELS.  Synchronises the stream. */
-#define NLC_N_KERNELS 6
+#define NLC_N_KERNELS 7
 NLC_API nlc_status nlc_get_timing(nlc_ctx* ctx, int32_t max_kernels,
                                   double* total_ms, int64_t* launches,
                                   int32_t* n_kernels);
 
 /* Name of kernel id k for nlc_get_timing ("?" when out of range). */
 NLC_API const char* nlc_timing_name(int32_t k);
+
+/* Gradient of the loss after nsteps time steps with respect to gamma, K,
+ * Gamma and the Q field of the current state, by a hand-written adjoint of
+ * the time step (the reverse of Sec. 1.2's update, step by step) with
+ * checkpointed recomputation: the forward run stores the state every
+ * ckpt_every steps, and the backward sweep recomputes each segment from its
+ * checkpoint into a ring of ckpt_every states before stepping back through
+ * it.  The context must hold one lattice whose populations were set by
+ * nlc_set_fields (they do not depend on Q).  On return the context holds
+ * the state after the nsteps steps (as nlc_step would leave it), *out the
+ * loss and parameter gradients, and dQ0 (host float64 [5][nz][ny][nx], may
+ * be NULL) dL/dQ of the starting state.  Device memory: about
+ * (nsteps/ckpt_every + ckpt_every + 12) states.  Synchronises the stream.
+ * Errors: NLC_EINVAL (nsteps < 1, ckpt_every < 1, batch context, null
+ * loss/out), NLC_ENOMEM, NLC_ECUDA, NLC_ETIMEOUT. */
+NLC_API nlc_status nlc_adjoint(nlc_ctx* ctx, const nlc_loss* loss, int64_t nsteps,
+                               int32_t ckpt_every, nlc_grad* out, double* dQ0);
 
 /* Message of the last failed call on ctx (empty if none).  Owned by ctx. */
 NLC_API const char* nlc_last_error(const nlc_ctx* ctx);

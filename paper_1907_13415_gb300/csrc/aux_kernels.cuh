@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256) k_field_raw_in(const T* __restrict__ in, 
 
 // Observables, pass 1: per-block FP64 partial sums over cells.
 // partial[block][OBS_SLOTS]: mass, mom x/y/z, sum S/s_ref, free energy,
-// non-finite count, max |u|.
-constexpr int OBS_SLOTS = 8;
+// non-finite count, sum |u|^2, max |u| (last).
+constexpr int OBS_SLOTS = 9;
 
 template <class Lat, class T>
 __global__ void __launch_bounds__(256) k_obs_partial(
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_obs_partial(
     const double* __restrict__ rho, const double* __restrict__ u, Dims d,
     Par<T> p, double s_ref, double* __restrict__ partial) {
   __shared__ double sh[32];
-  double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0};
+  double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0, 0};
   double umax = 0.0;
   const double A0 = (double)p.A0, K = (double)p.K, gam = (double)p.gamma;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < d.n;
@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(256) k_obs_partial(
       uu += ua * ua;
     }
     umax = fmax(umax, sqrt(uu));
+    acc[7] += uu;
     double q[5];
     int nbad = 0;
 #pragma unroll

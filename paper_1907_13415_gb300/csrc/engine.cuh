@@ -3,9 +3,11 @@
 // the launch sequences of the step, set-up, read-back and observables.
 #pragma once
 #include <cmath>
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "aux_kernels.cuh"
 #include "engine.h"
 #include "step_fused.cuh"
@@ -52,6 +54,16 @@ struct InstHost {
   double* prof_partial = nullptr;
   double* prof = nullptr;
   int obs_blocks = 1;
+  // adjoint work arrays (dense [comp][n])
+  T* lQ[2] = {nullptr, nullptr};
+  T* lG[2] = {nullptr, nullptr};
+  T *lQP = nullptr, *lUa = nullptr, *lGv = nullptr, *lF = nullptr, *lDq = nullptr,
+    *lLap = nullptr;
+  double* acc = nullptr;  // [3 kernels][blocks][3]
+  T* ck = nullptr;        // checkpoints, (Q + 5) n each
+  int64_t ck_count = 0;
+  T* ring = nullptr;      // states of one segment, (Q + 5) n each
+  int64_t ring_count = 0;
 };
 
 template <class Lat, class T>
@@ -279,6 +291,93 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
+
+  // ------------------------------------------------------------- adjoint
+  nlc_status adjoint(const nlc_loss* loss, int64_t nsteps, int ckpt_every, nlc_grad* out,
+                     double* dQ0) override {
+    InstHost<T>& I = inst_[0];
+    const int64_t n = I.d.n;
+    const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
+    const int64_t S = (int64_t)(Q + 5) * n;  // one state
+    cudaStream_t st = args_.stream;
+    nlc_status s;
+    if ((s = ensure_staging(I)) || (s = ensure_adjoint(I, nseg + 1, ckpt_every))) return s;
+    if (!maps_ok_) {
+      err = "TMA tensor maps unavailable; the adjoint needs the fused step";
+      return NLC_EUNSUPPORTED;
+    }
+    // forward sweep, keeping the state at the start of every segment
+    for (int64_t k = 0; k < nseg; k++) {
+      if ((s = state_out(I, I.ck + k * S))) return s;
+      const int64_t len = std::min<int64_t>(ckpt_every, nsteps - k * ckpt_every);
+      for (int64_t j = 0; j < len; j++)
+        if ((s = step_fused(st))) return s;
+    }
+    if ((s = state_out(I, I.ck + nseg * S))) return s;  // final state
+    // loss and its seed on the final state
+    nlc_obs obs;
+    if ((s = observables(0, &obs, nullptr))) return s;
+    const double R = obs.radius, A = obs.s_area;
+    const double dRdA = (DIM == 2 || I.d.nz == 1) ? (R > 0 ? 1.0 / (2.0 * M_PI * R) : 0.0)
+                                                   : (A > 0 ? R / (3.0 * A) : 0.0);
+    const double s_ref = 1.0 / 3.0;
+    const double cR = loss->w_radius * 2.0 * (R - loss->target_radius) * dRdA / s_ref;
+    const double cu = obs.u_l2 > 0 ? loss->w_velocity / obs.u_l2 : 0.0;
+    out->radius = R;
+    out->u_l2 = obs.u_l2;
+    out->loss = loss->w_radius * (R - loss->target_radius) * (R - loss->target_radius) +
+                loss->w_velocity * obs.u_l2;
+    NLC_CK(cudaMemsetAsync(I.acc, 0, sizeof(double) * 3 * 3 * grid1(n), st));
+    int lc = 0;  // lQ[lc], lG[lc] hold the adjoint of the current state
+    {
+      const unsigned gb = grid1(n);
+      k_stress<Lat, T><<<gb, 256, 0, st>>>(I.q[cur_], I.pi, I.d, I.p);
+      k_adj_seed_q<T><<<gb, 256, 0, st>>>(I.q[cur_], (T)cR, I.lQ[lc], I.d);
+      k_adj_lb<Lat, T><<<gb, 256, 0, st>>>(I.g[cur_], I.pi, nullptr, nullptr, nullptr,
+                                           I.lG[lc], I.lF, I.d, I.p, (T)cu);
+      k_adj_stress<Lat, T><<<gb, 256, 0, st>>>(I.q[cur_], I.lF, I.lQ[lc], I.lDq, I.lLap,
+                                               I.d, I.p, I.acc + 2 * 3 * gb);
+      k_adj_stencil<Lat, T><<<gb, 256, 0, st>>>(I.lDq, I.lLap, I.lQ[lc], I.d);
+      NLC_CK_LAUNCH("adjoint seed");
+    }
+    // backward sweep, segment by segment
+    for (int64_t k = nseg - 1; k >= 0; k--) {
+      const int64_t len = std::min<int64_t>(ckpt_every, nsteps - k * ckpt_every);
+      if ((s = state_in(I, I.ck + k * S))) return s;
+      for (int64_t j = 0; j < len; j++) {
+        if ((s = state_out(I, I.ring + j * S))) return s;
+        if (j + 1 < len && (s = step_fused(st))) return s;
+      }
+      for (int64_t j = len - 1; j >= 0; j--) {
+        if ((s = state_in(I, I.ring + j * S))) return s;
+        if ((s = adjoint_step(I, lc))) return s;
+        lc ^= 1;
+      }
+    }
+    // gradients
+    const unsigned gb = grid1(n);
+    std::vector<double> acc((size_t)3 * 3 * gb);
+    NLC_CK(cudaMemcpyAsync(acc.data(), I.acc, sizeof(double) * acc.size(),
+                           cudaMemcpyDeviceToHost, st));
+    if (dQ0) {
+      k_dense_to_double<T><<<grid1(5 * n), 256, 0, st>>>(I.lQ[lc], I.stage, 5 * n);
+      NLC_CK_LAUNCH("k_dense_to_double");
+      NLC_CK(cudaMemcpyAsync(dQ0, I.stage, sizeof(double) * 5 * n, cudaMemcpyDeviceToHost, st));
+    }
+    // leave the context at the final state
+    if ((s = state_in(I, I.ck + nseg * S))) return s;
+    NLC_CK(cudaStreamSynchronize(st));
+    if ((s = device_error())) return s;
+    double g3[3] = {0, 0, 0};
+    for (int kern = 0; kern < 3; kern++)
+      for (unsigned b = 0; b < gb; b++)
+        for (int c = 0; c < 3; c++) g3[c] += acc[((size_t)kern * gb + b) * 3 + c];
+    out->dgamma = g3[0];
+    out->dK = g3[1];
+    out->dGamma = g3[2];
+    return NLC_OK;
+  }
+
   nlc_status observables(int i, nlc_obs* out, double* s_profile) override {
     InstHost<T>& I = inst_[i];
     nlc_status s;
@@ -315,7 +414,8 @@ class Engine final : public EngineBase {
     out->s_area = tot[4];
     out->free_energy = tot[5];
     out->nonfinite = (int64_t)tot[6];
-    out->max_u = tot[7];
+    out->u_l2 = std::sqrt(tot[7]);
+    out->max_u = tot[8];
     out->radius = (DIM == 2 || d.nz == 1) ? std::sqrt(tot[4] / M_PI)
                                           : std::cbrt(3.0 * tot[4] / (4.0 * M_PI));
     const double half = s_ref / 2.0;
@@ -391,6 +491,78 @@ class Engine final : public EngineBase {
     const int64_t nchunks = (rows + 63) / 64;
     if ((s = alloc(&I.prof_partial, (size_t)(nchunks * I.d.nx)))) return s;
     if ((s = alloc(&I.prof, (size_t)I.d.nx))) return s;
+    return NLC_OK;
+  }
+
+  nlc_status ensure_adjoint(InstHost<T>& I, int64_t ck_count, int64_t ring_count) {
+    nlc_status s;
+    const int64_t n = I.d.n;
+    const int64_t S = (int64_t)(Q + 5) * n;
+    if (!I.lQP) {
+      if ((s = alloc(&I.lQ[0], (size_t)5 * n)) || (s = alloc(&I.lQ[1], (size_t)5 * n)) ||
+          (s = alloc(&I.lG[0], (size_t)Q * n)) || (s = alloc(&I.lG[1], (size_t)Q * n)) ||
+          (s = alloc(&I.lQP, (size_t)5 * n)) || (s = alloc(&I.lUa, (size_t)DIM * n)) ||
+          (s = alloc(&I.lGv, (size_t)DIM * DIM * n)) || (s = alloc(&I.lF, (size_t)DIM * n)) ||
+          (s = alloc(&I.lDq, (size_t)DIM * 5 * n)) || (s = alloc(&I.lLap, (size_t)5 * n)) ||
+          (s = alloc(&I.acc, (size_t)3 * 3 * grid1(n))))
+        return s;
+    }
+    if (I.ck_count < ck_count) {
+      if ((s = alloc(&I.ck, (size_t)(ck_count * S)))) return s;
+      I.ck_count = ck_count;
+    }
+    if (I.ring_count < ring_count) {
+      if ((s = alloc(&I.ring, (size_t)(ring_count * S)))) return s;
+      I.ring_count = ring_count;
+    }
+    return NLC_OK;
+  }
+
+  // current state of instance I <-> a dense (g, Q) record
+  nlc_status state_out(InstHost<T>& I, T* dst) {
+    const int64_t n = I.d.n;
+    cudaStream_t st = args_.stream;
+    NLC_CK(cudaMemcpyAsync(dst, I.g[cur_], sizeof(T) * Q * n, cudaMemcpyDeviceToDevice, st));
+    k_field_raw_out<T><<<grid1(n), 256, 0, st>>>(I.q[cur_], 5, I.d, dst + (int64_t)Q * n);
+    NLC_CK_LAUNCH("k_field_raw_out");
+    return NLC_OK;
+  }
+
+  nlc_status state_in(InstHost<T>& I, const T* src) {
+    const int64_t n = I.d.n;
+    cudaStream_t st = args_.stream;
+    NLC_CK(cudaMemcpyAsync(I.g[cur_], src, sizeof(T) * Q * n, cudaMemcpyDeviceToDevice, st));
+    k_field_raw_in<T, DIM><<<grid1(n), 256, 0, st>>>(src + (int64_t)Q * n, I.d, I.q[cur_]);
+    NLC_CK_LAUNCH("k_field_raw_in");
+    return NLC_OK;
+  }
+
+  // one reverse step: the current buffers hold the state of step n; the
+  // adjoint of the state at n+1 is in (lQ[lc], lG[lc]); writes the adjoint
+  // at n into (lQ[lc^1], lG[lc^1])
+  nlc_status adjoint_step(InstHost<T>& I, int lc) {
+    const int64_t n = I.d.n;
+    const unsigned gb = grid1(n);
+    cudaStream_t st = args_.stream;
+    const int a = cur_, b = cur_ ^ 1;
+    const int e0 = mark();
+    // forward intermediates of the step
+    k_stress<Lat, T><<<gb, 256, 0, st>>>(I.q[a], I.pi, I.d, I.p);
+    k_lb<Lat, T><<<gb, 256, 0, st>>>(I.g[a], I.g[b], I.pi, I.u, I.d, I.p);
+    k_predict<Lat, T><<<gb, 256, 0, st>>>(I.q[a], I.u, I.qp, I.r1, I.d, I.p);
+    // reverse
+    k_adj_be2<Lat, T><<<gb, 256, 0, st>>>(I.qp, I.u, I.lQ[lc], I.lQP, I.lUa, I.lGv, I.d, I.p,
+                                          I.acc);
+    k_adj_be1<Lat, T><<<gb, 256, 0, st>>>(I.q[a], I.u, I.lQ[lc], I.lQP, I.lQ[lc ^ 1], I.lUa,
+                                          I.lGv, I.d, I.p, I.acc + 3 * gb);
+    k_adj_lb<Lat, T><<<gb, 256, 0, st>>>(I.g[a], I.pi, I.lG[lc], I.lUa, I.lGv, I.lG[lc ^ 1],
+                                         I.lF, I.d, I.p, T(0));
+    k_adj_stress<Lat, T><<<gb, 256, 0, st>>>(I.q[a], I.lF, I.lQ[lc ^ 1], I.lDq, I.lLap, I.d,
+                                             I.p, I.acc + 2 * 3 * gb);
+    k_adj_stencil<Lat, T><<<gb, 256, 0, st>>>(I.lDq, I.lLap, I.lQ[lc ^ 1], I.d);
+    NLC_CK_LAUNCH("adjoint step");
+    const int e1 = mark();
+    if (timer.on) timer.span(KID_ADJOINT, e0, e1);
     return NLC_OK;
   }
 

@@ -14,7 +14,7 @@ namespace nlc {
 
 // kernel ids of the timing log (names in nlc_timing_name)
 enum KernelId { KID_FUSED_LB = 0, KID_FUSED_BE, KID_STRESS, KID_LB, KID_PREDICT,
-                KID_CORRECT, KID_COUNT };
+                KID_CORRECT, KID_ADJOINT, KID_COUNT };
 
 // CUDA events recorded around kernel launches while timing is on.
 class KernelTimer {
@@ -79,6 +79,8 @@ struct EngineBase {
   virtual nlc_status get_fields(int inst, double* Q5, double* rho, double* u) = 0;
   virtual nlc_status get_populations(int inst, double* f) = 0;
   virtual nlc_status observables(int inst, nlc_obs* out, double* s_profile) = 0;
+  virtual nlc_status adjoint(const nlc_loss* loss, int64_t nsteps, int ckpt_every,
+                             nlc_grad* out, double* dQ0) = 0;
   // raw device state: populations (current buffer) then Q interior
   virtual size_t state_bytes() const = 0;
   virtual nlc_status save_state(void* dst) = 0;

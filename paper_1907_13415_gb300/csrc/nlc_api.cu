@@ -310,6 +310,18 @@ nlc_status nlc_load(nlc_ctx* ctx, const void* buf, size_t len) {
   return NLC_OK;
 }
 
+nlc_status nlc_adjoint(nlc_ctx* ctx, const nlc_loss* loss, int64_t nsteps,
+                       int32_t ckpt_every, nlc_grad* out, double* dQ0) {
+  if (!ctx) return NLC_EINVAL;
+  if (!loss || !out) return fail(ctx, NLC_EINVAL, "loss or out is NULL");
+  if (nsteps < 1 || ckpt_every < 1) return fail(ctx, NLC_EINVAL, "nsteps and ckpt_every must be >= 1");
+  if (ctx->grids.size() != 1) return fail(ctx, NLC_EINVAL, "the adjoint needs a single-lattice context");
+  nlc_status st = ctx->eng->adjoint(loss, nsteps, ckpt_every, out, dQ0);
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  ctx->steps[0] += nsteps;
+  return NLC_OK;
+}
+
 nlc_status nlc_set_timing(nlc_ctx* ctx, int32_t enable) {
   if (!ctx) return NLC_EINVAL;
   if (enable) ctx->eng->timer.reset();
@@ -336,7 +348,7 @@ nlc_status nlc_get_timing(nlc_ctx* ctx, int32_t max_kernels, double* total_ms,
 
 const char* nlc_timing_name(int32_t k) {
   static const char* names[nlc::KID_COUNT] = {
-      "fused_lb", "fused_be", "stress", "lb", "predict", "correct"};
+      "fused_lb", "fused_be", "stress", "lb", "predict", "correct", "adjoint_step"};
   return (k >= 0 && k < nlc::KID_COUNT) ? names[k] : "?";
 }
 

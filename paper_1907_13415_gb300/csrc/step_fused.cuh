@@ -196,6 +196,24 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   const int nxy = d.nx * d.ny;
   const int ic = (ty + 1) * RX1 + (tx + 1);
 
+  // The populations of the next plane are pulled into registers (gn) as
+  // soon as the current plane is done, so their loads are in flight while
+  // the block computes the next plane's stress.
+  T gn[Lat::Q];
+  auto pull_next = [&](int z) {
+    if (!cell) return;
+    int plane[3];
+    plane[1] = z * nxy;
+    plane[0] = DIM == 3 ? wrap_inc(z, d.nz) * nxy : plane[1];
+    plane[2] = DIM == 3 ? wrap_dec(z, d.nz) * nxy : plane[1];
+#pragma unroll
+    for (int i = 0; i < Lat::Q; i++) {
+      const int64_t off = (int64_t)i * d.n + plane[Lat::c(i, 2) + 1] +
+                          rowy[Lat::c(i, 1) + 1] + colx[Lat::c(i, 0) + 1];
+      gn[i] = gin[off];
+    }
+  };
+
   auto lb_cell = [&](int z) {
     if (!cell) return;
     const T* Pc = sP(pslot(z));
@@ -209,26 +227,21 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
       if (DIM == 3) s += (Pp[(a * DIM + 2) * A1 + ic] - Pm[(a * DIM + 2) * A1 + ic]) / T(2);
       F[a] = s;
     }
-    int plane[3];
-    plane[1] = z * nxy;
-    plane[0] = DIM == 3 ? wrap_inc(z, d.nz) * nxy : plane[1];
-    plane[2] = DIM == 3 ? wrap_dec(z, d.nz) * nxy : plane[1];
     T g[Lat::Q], rho, u[3];
 #pragma unroll
-    for (int i = 0; i < Lat::Q; i++) {
-      const int64_t off = (int64_t)i * d.n + plane[Lat::c(i, 2) + 1] + rowy[Lat::c(i, 1) + 1] + colx[Lat::c(i, 0) + 1];
-      g[i] = gin[off];
-    }
+    for (int i = 0; i < Lat::Q; i++) g[i] = gn[i];
     moments<Lat, T>(g, F, p, rho, u);
     collide_bgk<Lat, T>(g, rho, u, F, p);
-    const int o = plane[1] + rowy[1] + x;
+    const int o = z * nxy + rowy[1] + x;
 #pragma unroll
     for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * (size_t)d.n + o] = g[i];
     store_with_images<T, DIM, DIM>(U, d, x, y, z, u);
+    if (z + 1 < z1) pull_next(z + 1);
   };
 
   if constexpr (DIM == 2) {
     if (tid == 0) issue(0);
+    pull_next(0);
     wait(0);
     if (tid < A1) stress_ring_cell<T, DIM>(tid, sQ(0), sQ(0), sQ(0), sP(0), p);
     if (__syncthreads_or(late)) {
@@ -239,6 +252,7 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   } else {
     if (tid == 0)
       for (int z = z0 - 2; z <= z0 + 1; z++) issue(z);
+    pull_next(z0);
     wait(z0 - 2);
     wait(z0 - 1);
     wait(z0);

@@ -42,15 +42,28 @@ class nlc_obs(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double), ("mom", ctypes.c_double * 3),
                 ("s_area", ctypes.c_double), ("radius", ctypes.c_double),
                 ("x_iface", ctypes.c_double), ("max_u", ctypes.c_double),
-                ("free_energy", ctypes.c_double),
+                ("free_energy", ctypes.c_double), ("u_l2", ctypes.c_double),
                 ("nonfinite", ctypes.c_int64), ("step", ctypes.c_int64)]
 
     def as_dict(self):
         return dict(mass=self.mass, mom_x=self.mom[0], mom_y=self.mom[1],
                     mom_z=self.mom[2], s_area=self.s_area, radius=self.radius,
                     x_iface=self.x_iface, max_u=self.max_u,
-                    free_energy=self.free_energy, nonfinite=self.nonfinite,
-                    step=self.step)
+                    free_energy=self.free_energy, u_l2=self.u_l2,
+                    nonfinite=self.nonfinite, step=self.step)
+
+
+class nlc_loss(ctypes.Structure):
+    _fields_ = [("target_radius", ctypes.c_double), ("w_radius", ctypes.c_double),
+                ("w_velocity", ctypes.c_double)]
+
+
+class nlc_grad(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("loss", "radius", "u_l2", "dgamma", "dK", "dGamma")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -90,6 +103,7 @@ def load(build_if_missing=True):
         "nlc_lattice_velocities": ([I32, P, P], I32),
         "nlc_set_timing": ([P, I32], I32),
         "nlc_save": ([P, P, ctypes.POINTER(ctypes.c_size_t)], I32),
+        "nlc_adjoint": ([P, P, I64, I32, P, P], I32),
         "nlc_load": ([P, P, ctypes.c_size_t], I32),
         "nlc_get_timing": ([P, I32, P, P, P], I32),
         "nlc_timing_name": ([I32], ctypes.c_char_p),
@@ -109,7 +123,8 @@ def exported_symbols():
             "nlc_get_fields", "nlc_get_populations", "nlc_step",
             "nlc_observables", "nlc_last_error", "nlc_destroy",
             "nlc_lattice_velocities", "nlc_version", "nlc_set_timing",
-            "nlc_get_timing", "nlc_timing_name", "nlc_save", "nlc_load"]
+            "nlc_get_timing", "nlc_timing_name", "nlc_save", "nlc_load",
+            "nlc_adjoint"]
 
 
 def _check(ctx, status):
@@ -237,6 +252,19 @@ def nlc_save(ctx):
 def nlc_load(ctx, data):
     buf = ctypes.create_string_buffer(bytes(data), len(data))
     _check(ctx, load().nlc_load(ctx, buf, len(data)))
+
+
+def nlc_adjoint(ctx, loss, nsteps, ckpt_every, dQ0=None):
+    """Runs nsteps with checkpoints every ckpt_every steps and returns the
+    loss and its gradients (dict); fills dQ0 (float64 [5][nz][ny][nx]) if
+    given."""
+    out = nlc_grad()
+    L = nlc_loss(*loss) if not isinstance(loss, nlc_loss) else loss
+    _check(ctx, load().nlc_adjoint(ctx, ctypes.cast(ctypes.pointer(L), ctypes.c_void_p),
+                                   int(nsteps), int(ckpt_every),
+                                   ctypes.cast(ctypes.pointer(out), ctypes.c_void_p),
+                                   _ptr(dQ0)))
+    return out.as_dict()
 
 
 def nlc_version():
@@ -371,6 +399,15 @@ class Simulation:
 
     def set_graph(self, steps):
         nlc_set_graph(self.ctx, steps)
+
+    def adjoint(self, target_radius, w_radius, w_velocity, nsteps, ckpt_every,
+                want_dQ0=True):
+        dQ0 = np.empty((5,) + self.shape) if want_dQ0 else None
+        g = nlc_adjoint(self.ctx, (target_radius, w_radius, w_velocity), nsteps,
+                        ckpt_every, dQ0)
+        if want_dQ0:
+            g["dQ0"] = dQ0
+        return g
 
     def close(self):
         if self.ctx:

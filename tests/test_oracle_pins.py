@@ -578,3 +578,39 @@ def test_interface_velocity_near_coexistence(orc, delta):
     v_est = 10 / 9 * 0.3 * 0.1 * lam * delta
     assert np.sign(v) == np.sign(delta)
     assert v == pytest.approx(v_est, rel=0.15)
+
+
+# ---------------------------------------------------------------------------
+# The complex-step twin of the oracle (used as the reference gradient)
+# ---------------------------------------------------------------------------
+
+def test_complex_step_twin_matches_real_oracle_and_differences(orc, orc_cs):
+    """The complex build with zero imaginary parts reproduces the real
+    oracle bit for bit, and its derivatives agree with FP64 central
+    differences of the real oracle (h = 1e-6)."""
+    w = wl.disc_256().with_(shape=(1, 20, 22), size=5, noise=1e-4, seed=3)
+    p = wl.param_vector(w.params)
+    Q0 = w.initial_q5()
+    f0 = orc.init_equilibrium(w.lattice, w.shape)
+    f_r, Q_r = orc.step(w.lattice, p, f0, Q0, 25)
+    f_c, Q_c = orc_cs.step(w.lattice, p.astype(complex), f0.astype(complex),
+                           Q0.astype(complex), 25)
+    assert np.array_equal(Q_r, Q_c.real) and np.array_equal(f_r, f_c.real)
+
+    def L(pv, Q, cs):
+        o = orc_cs if cs else orc
+        f, Qe = o.step(w.lattice, pv, o.init_equilibrium(w.lattice, w.shape), Q, 25)
+        R = o.observables(w.lattice, pv, f, Qe)["radius"]
+        u = o.fields(w.lattice, pv, f, Qe)["u"]
+        return (R - 5.0) ** 2 + 10 * np.sqrt(np.sum(u * u))
+
+    h = 1e-6
+    for k in (1, 2, 3):  # K, gamma, Gamma
+        pc = p.astype(complex)
+        pc[k] += 1e-30j
+        d_cs = L(pc, Q0.astype(complex), True).imag / 1e-30
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        d_fd = (L(pp, Q0, False) - L(pm, Q0, False)) / (2 * h)
+        assert d_cs == pytest.approx(d_fd, rel=1e-5)
