@@ -157,6 +157,12 @@ NLC_API int32_t nlc_count(const nlc_ctx* ctx);
  * Not used while timing is enabled. */
 NLC_API nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps);
 
+/* Replaces the parameters of lattice inst (same checks as nlc_create);
+ * the state is kept.  The step kernels (and captured step graphs) read the
+ * parameters from device memory, so the change applies to the next step.
+ * Synchronises the stream. */
+NLC_API nlc_status nlc_set_params(nlc_ctx* ctx, int32_t inst, const nlc_params* params);
+
 /* Selects the kernel schedule (NLC_SCHED_*) for later nlc_step calls. */
 NLC_API nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule);
 

@@ -151,6 +151,25 @@ class Engine final : public EngineBase {
 
   int count() const override { return (int)inst_.size(); }
 
+  nlc_status set_params(int i, const nlc_params& q) override {
+    InstHost<T>& I = inst_[i];
+    I.p.A0 = (T)q.A0;
+    I.p.K = (T)q.K;
+    I.p.gamma = (T)q.gamma;
+    I.p.Gamma = (T)q.Gamma;
+    I.p.xi = (T)q.xi;
+    I.p.tau = (T)q.tau;
+    I.p.rho0 = (T)q.rho0;
+    I.p.inv_tau = (T)(1.0 / q.tau);
+    I.p.guo = (T)(1.0 - 1.0 / (2.0 * q.tau));
+    args_.params[i] = q;
+    // the device descriptor holds the parameters: update it in place
+    NLC_CK(cudaMemcpyAsync(&insts_dev_[i].p, &I.p, sizeof(Par<T>), cudaMemcpyHostToDevice,
+                           args_.stream));
+    NLC_CK(cudaStreamSynchronize(args_.stream));
+    return NLC_OK;
+  }
+
   // ---------------------------------------------------------------- step
   nlc_status step(int64_t n, int schedule) override {
     if (n <= 0) return NLC_OK;

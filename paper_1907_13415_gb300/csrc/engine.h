@@ -73,6 +73,7 @@ struct EngineBase {
   KernelTimer timer;
   int graph_steps = 0;  // >0: whole chunks of this many steps replay a CUDA graph
   virtual int count() const = 0;
+  virtual nlc_status set_params(int inst, const nlc_params& p) = 0;
   virtual nlc_status step(int64_t n, int schedule) = 0;
   virtual nlc_status set_fields(int inst, const double* Q5, const double* rho,
                                 const double* u) = 0;

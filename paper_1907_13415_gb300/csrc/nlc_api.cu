@@ -144,6 +144,19 @@ nlc_status nlc_create(const nlc_grid* grid, const nlc_params* params,
   return nlc_create_batch(1, grid, params, stream, out);
 }
 
+nlc_status nlc_set_params(nlc_ctx* ctx, int32_t inst, const nlc_params* params) {
+  if (!ctx) return NLC_EINVAL;
+  if (inst < 0 || inst >= (int32_t)ctx->grids.size())
+    return fail(ctx, NLC_EINVAL, "instance out of range");
+  std::string msg;
+  nlc_status st = check_params(params, &msg);
+  if (st != NLC_OK) return fail(ctx, st, msg);
+  st = ctx->eng->set_params(inst, *params);
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  ctx->params[inst] = *params;
+  return NLC_OK;
+}
+
 nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps) {
   if (!ctx) return NLC_EINVAL;
   if (steps < 0) return fail(ctx, NLC_EINVAL, "negative graph length");

@@ -92,6 +92,7 @@ def load(build_if_missing=True):
         "nlc_create_batch": ([I32, P, P, P, ctypes.POINTER(P)], I32),
         "nlc_count": ([P], I32),
         "nlc_set_graph": ([P, I32], I32),
+        "nlc_set_params": ([P, I32, ctypes.POINTER(nlc_params)], I32),
         "nlc_set_schedule": ([P, I32], I32),
         "nlc_set_fields": ([P, I32, P, P, P], I32),
         "nlc_get_fields": ([P, I32, P, P, P], I32),
@@ -119,6 +120,7 @@ def load(build_if_missing=True):
 
 def exported_symbols():
     return ["nlc_create", "nlc_create_batch", "nlc_count", "nlc_set_graph",
+            "nlc_set_params",
             "nlc_set_schedule", "nlc_set_fields",
             "nlc_get_fields", "nlc_get_populations", "nlc_step",
             "nlc_observables", "nlc_last_error", "nlc_destroy",
@@ -172,6 +174,11 @@ def nlc_create_batch(grids, params, stream=None):
 
 def nlc_count(ctx):
     return load().nlc_count(ctx)
+
+
+def nlc_set_params(ctx, inst, params):
+    P = params if isinstance(params, nlc_params) else _params(params)
+    _check(ctx, load().nlc_set_params(ctx, inst, ctypes.byref(P)))
 
 
 def nlc_set_graph(ctx, steps):
@@ -399,6 +406,9 @@ class Simulation:
 
     def set_graph(self, steps):
         nlc_set_graph(self.ctx, steps)
+
+    def set_params(self, params):
+        nlc_set_params(self.ctx, 0, params)
 
     def adjoint(self, target_radius, w_radius, w_velocity, nsteps, ckpt_every,
                 want_dQ0=True):

@@ -135,3 +135,33 @@ def test_adjoint_leaves_final_state_and_rejects_batches():
     with pytest.raises(nlc.NlcError):
         nlc.nlc_adjoint(bt.ctx, LOSS, 5, 5)
     bt.close()
+
+
+def test_torch_autograd_function(orc_cs):
+    """loss.backward() through the autograd bridge gives the adjoint's
+    gradients, which match the oracle's complex-step derivative."""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    from paper_1907_13415_gb300.autograd import droplet_loss
+    w = droplet(wl.D2Q9, (1, 24, 26))
+    sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=0, stream=stream())
+    Q0 = torch.tensor(w.initial_q5(), dtype=torch.float64, requires_grad=True)
+    theta = torch.tensor([w.params["gamma"], w.params["K"], w.params["Gamma"]],
+                         dtype=torch.float64, requires_grad=True)
+    L = droplet_loss(Q0, theta, sim, w.params, 30, 8, *LOSS)
+    L.backward()
+    _, dg = oracle_loss_derivative(orc_cs, w, 30, dparam=2)
+    _, dK = oracle_loss_derivative(orc_cs, w, 30, dparam=1)
+    assert theta.grad[0].item() == pytest.approx(dg, rel=1e-8)
+    assert theta.grad[1].item() == pytest.approx(dK, rel=1e-8)
+    v = np.random.default_rng(9).normal(size=Q0.shape)
+    _, dv = oracle_loss_derivative(orc_cs, w, 30, dQ=v)
+    assert float((Q0.grad.numpy() * v).sum()) == pytest.approx(dv, rel=1e-8)
+    # a second evaluation at shifted gamma through set_params
+    theta2 = torch.tensor([w.params["gamma"] + 0.01, w.params["K"], w.params["Gamma"]],
+                          dtype=torch.float64, requires_grad=True)
+    L2 = droplet_loss(Q0.detach(), theta2, sim, w.params, 30, 8, *LOSS)
+    w2 = w.with_(params=dict(w.params, gamma=w.params["gamma"] + 0.01))
+    L2_ref, _ = oracle_loss_derivative(orc_cs, w2, 30, dparam=2)
+    assert L2.item() == pytest.approx(L2_ref, rel=1e-10)
+    sim.close()
