@@ -85,8 +85,13 @@ template <class T, int NC, int DIM>
 __device__ __forceinline__ void store_with_images(const Field<T>& F, const Dims& d,
                                                   int x, int y, int z,
                                                   const T v[NC]) {
+  const int64_t o = F.off(0, x, y, z);
 #pragma unroll
-  for (int k = 0; k < NC; k++) F.at(k, x, y, z) = v[k];
+  for (int k = 0; k < NC; k++) F.base[o + k * F.L.comp] = v[k];
+  const bool inner = x >= GHOST && x < d.nx - GHOST && y >= GHOST &&
+                     y < d.ny - GHOST &&
+                     (DIM == 2 || (z >= GHOST && z < d.nz - GHOST));
+  if (inner) return;
   const unsigned mx = image_mask(x, d.nx), my = image_mask(y, d.ny);
   const unsigned mz = DIM == 3 ? image_mask(z, d.nz) : 0u;
   if ((mx | my | mz) == 0) return;

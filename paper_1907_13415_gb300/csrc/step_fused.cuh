@@ -206,11 +206,14 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     plane[1] = z * nxy;
     plane[0] = DIM == 3 ? wrap_inc(z, d.nz) * nxy : plane[1];
     plane[2] = DIM == 3 ? wrap_dec(z, d.nz) * nxy : plane[1];
+    // 32-bit element offsets within a population plane; the plane of
+    // population i starts i * n elements after gin
+    const unsigned n32 = (unsigned)d.n;
 #pragma unroll
     for (int i = 0; i < Lat::Q; i++) {
-      const int64_t off = (int64_t)i * d.n + plane[Lat::c(i, 2) + 1] +
-                          rowy[Lat::c(i, 1) + 1] + colx[Lat::c(i, 0) + 1];
-      gn[i] = gin[off];
+      const unsigned off = (unsigned)(plane[Lat::c(i, 2) + 1] + rowy[Lat::c(i, 1) + 1] +
+                                      colx[Lat::c(i, 0) + 1]);
+      gn[i] = __ldg(gin + (size_t)i * n32 + off);
     }
   };
 
@@ -232,9 +235,10 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     for (int i = 0; i < Lat::Q; i++) g[i] = gn[i];
     moments<Lat, T>(g, F, p, rho, u);
     collide_bgk<Lat, T>(g, rho, u, F, p);
-    const int o = z * nxy + rowy[1] + x;
+    const unsigned o = (unsigned)(z * nxy + rowy[1] + x);
+    const unsigned n32 = (unsigned)d.n;
 #pragma unroll
-    for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * (size_t)d.n + o] = g[i];
+    for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = g[i];
     store_with_images<T, DIM, DIM>(U, d, x, y, z, u);
     if (z + 1 < z1) pull_next(z + 1);
   };
@@ -284,6 +288,7 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   }
   (void)NPI;
 }
+
 
 // ---------------------------------------------------------------------------
 // Beris-Edwards kernel
