@@ -1,0 +1,162 @@
+"""The paper's experiments on the GPU library (Sec. 2), with the FP32 runs
+compared against FP64 runs of the same problem.
+
+  python -m paper_1907_13415_gb300.experiments flat   [--gamma 2.7 --steps 2000]
+  python -m paper_1907_13415_gb300.experiments disc   [--delta 0.002 --steps 20000]
+  python -m paper_1907_13415_gb300.experiments sweep  [--steps 50000]
+
+flat  : flat interface (Sec. 2.1): interface position and velocity.
+disc  : circular droplet (Sec. 2.2): radius against time, spurious velocity.
+sweep : temperature sweep (Sec. 2.1, Fig. 1D inset): interface velocity
+        against gamma for the 64 uneven lattices of the batched workload, in
+        one batched context, next to the Allen-Cahn estimate.
+paper_circle : the almost static circle of Sec. 2.2 with the paper's own
+        parameters, for the spurious-velocity estimate.
+Each prints one JSON object.  FP32 results carry max|dQ| (normwise, against
+the FP64 run of the same problem) and the drift of the interface position or
+radius.
+"""
+import argparse
+import json
+import math
+import sys
+
+import numpy as np
+
+from . import nlc
+from . import workloads as wl
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _run(w, precision, steps, every):
+    """Runs w, returning observables every `every` steps and the final Q."""
+    s = nlc.Simulation(w.lattice, w.shape, w.params, precision=precision,
+                       stream=_stream())
+    s.set_fields(w.initial_q5())
+    trace = [s.observables()]
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        s.step(k)
+        done += k
+        trace.append(s.observables())
+    Q, _, _ = s.get_fields()
+    s.close()
+    return trace, Q
+
+
+def _drift(key, t32, t64, Q32, Q64):
+    a32 = np.array([o[key] for o in t32])
+    a64 = np.array([o[key] for o in t64])
+    return {"max_dQ_rel": float(np.abs(Q32 - Q64).max() / np.abs(Q64).max()),
+            f"{key}_drift_final": float(a32[-1] - a64[-1]),
+            f"{key}_drift_max": float(np.abs(a32 - a64).max())}
+
+
+def flat(gamma=2.7, steps=2000, lx=128, ly=8, every=100):
+    w = wl.flat_128x8().with_(shape=(1, ly, lx), size=lx // 2,
+                              params=dict(wl.BASE_PARAMS, gamma=gamma))
+    t64, Q64 = _run(w, nlc.NLC_FP64, steps, every)
+    t32, Q32 = _run(w, nlc.NLC_FP32, steps, every)
+    x = np.array([o["x_iface"] for o in t64])
+    half = len(x) // 2
+    v = float((x[-1] - x[half]) / ((len(x) - 1 - half) * every)) if len(x) > 2 else 0.0
+    return {"experiment": "flat interface", "gamma": gamma, "lattice": [lx, ly],
+            "steps": steps, "x_iface_fp64": float(x[-1]),
+            "velocity_fp64": v, "max_u_fp64": float(t64[-1]["max_u"]),
+            "fp32_vs_fp64": _drift("x_iface", t32, t64, Q32, Q64)}
+
+
+def disc(delta=0.0, steps=20000, n=256, radius=32, every=500):
+    w = wl.disc_256(delta).with_(shape=(1, n, n), size=radius)
+    t64, Q64 = _run(w, nlc.NLC_FP64, steps, every)
+    t32, Q32 = _run(w, nlc.NLC_FP32, steps, every)
+    R = np.array([o["radius"] for o in t64])
+    tail = max(2, len(R) // 4)
+    dRdt = float((R[-1] - R[-tail]) / ((tail - 1) * every))
+    return {"experiment": "circular droplet", "delta": delta,
+            "gamma": w.params["gamma"], "lattice": [n, n], "radius0": radius,
+            "steps": steps, "radius_fp64": [float(r) for r in R[:: max(1, len(R) // 10)]],
+            "dRdt_fp64": dRdt,
+            "max_u_fp64": float(t64[-1]["max_u"]),
+            "fp32_vs_fp64": _drift("radius", t32, t64, Q32, Q64)}
+
+
+def paper_circle(angle_deg=0.0, steps=35000, every=1000, gamma=2.707681):
+    """Sec. 2.2 / Fig. 2 with the paper's parameters (tau = 1.5, K = 0.04,
+    Gamma = 0.34, xi = 0.7, A0 = 0.1): a 100 x 100 lattice, disc of radius 25,
+    director at angle_deg from y, gamma = 2.707681.  Reports the interface
+    velocity dR/dt and max |u| at the end (the paper: u_i ~ 1.89e-7,
+    u_max = 8.97e-7 at 0 deg and 1.13e-6 at 20 deg, on D3Q19 with MRT)."""
+    a = math.radians(angle_deg)
+    p = dict(wl.PAPER_PARAMS, gamma=gamma)
+    w = wl.Workload("paper_circle", wl.D2Q9, (1, 100, 100), p, steps, "ball", 25,
+                    (math.sin(a), math.cos(a), 0.0), 0.0, 0)
+    t64, _ = _run(w, nlc.NLC_FP64, steps, every)
+    R = np.array([o["radius"] for o in t64])
+    tail = max(2, len(R) // 4)
+    return {"experiment": "paper circle", "angle_deg": angle_deg, "gamma": gamma,
+            "steps": steps, "radius_final": float(R[-1]),
+            "dRdt_final": float((R[-1] - R[-tail]) / ((tail - 1) * every)),
+            "max_u_final": float(t64[-1]["max_u"])}
+
+
+def sweep(steps=50000, every=2500, graph_steps=50):
+    """Interface velocity against gamma from one batched context."""
+    ws = wl.sweep_64()
+    b = nlc.Batch(wl.D2Q9, [w.shape for w in ws], [w.params for w in ws],
+                  precision=nlc.NLC_FP32, stream=_stream(), graph_steps=graph_steps)
+    for i, w in enumerate(ws):
+        b.set_fields(i, w.initial_q5())
+    xs = [[] for _ in ws]
+    done = 0
+    while done < steps:
+        b.step(every)
+        done += every
+        for i in range(len(ws)):
+            xs[i].append(b.observables(i)["x_iface"])
+    out = []
+    for i, w in enumerate(ws):
+        x = np.array(xs[i])
+        g = w.params["gamma"]
+        # fit over the second half, while an interface exists
+        sel = x[len(x) // 2:]
+        ok = bool(np.all(sel >= 0))
+        v = float(np.polyfit(np.arange(len(sel)) * every, sel, 1)[0]) if ok else None
+        lam = math.sqrt(27 * w.params["K"] / (w.params["A0"] * g))
+        v_est = 10 / 9 * w.params["Gamma"] * w.params["A0"] * lam * (g - 2.7)
+        out.append({"gamma": g, "lattice": [w.shape[2], w.shape[1]],
+                    "velocity": v, "allen_cahn_estimate": v_est,
+                    "interface_survives": ok})
+    b.close()
+    return {"experiment": "temperature sweep", "steps": steps, "instances": out}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", choices=["flat", "disc", "sweep", "paper_circle"])
+    ap.add_argument("--angle", type=float, default=0.0)
+    ap.add_argument("--gamma", type=float, default=2.7)
+    ap.add_argument("--delta", type=float, default=0.0)
+    ap.add_argument("--steps", type=int, default=None)
+    args = ap.parse_args(argv)
+    import torch
+    torch.cuda.set_device(0)
+    if args.which == "flat":
+        r = flat(args.gamma, args.steps or 2000)
+    elif args.which == "disc":
+        r = disc(args.delta, args.steps or 20000)
+    elif args.which == "paper_circle":
+        r = paper_circle(args.angle, args.steps or 35000)
+    else:
+        r = sweep(args.steps or 50000)
+    print(json.dumps(r))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
