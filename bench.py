@@ -166,6 +166,14 @@ def barrier(ws):
         dist.barrier()
 
 
+def whole_job_rate(cells_per_rank, steps, elapsed_ms, ws):
+    """Weak scaling over independent replicas: every rank advanced its own
+    lattice for `steps` steps; the job's rate is all ranks' lattice updates
+    over the slowest rank's time.  Returns (MLUPS, max elapsed ms)."""
+    t_max = max_over_ranks(elapsed_ms, ws)
+    return cells_per_rank * steps * ws / (t_max * 1e-3) / 1e6, t_max
+
+
 # -- the oracle as CPU baseline / reference arm ------------------------------
 
 def oracle_sample_rate(w, steps, shape=None):
@@ -296,8 +304,7 @@ def run_ours(args, w):
     kt = nlc.nlc_get_timing(sim.ctx)
     nlc.nlc_set_timing(sim.ctx, False)
     clocks = clk.summary()
-    t_max = max_over_ranks(elapsed_ms, ws)
-    value = cells * args.steps * ws / (t_max * 1e-3) / 1e6
+    value, t_max = whole_job_rate(cells, args.steps, elapsed_ms, ws)
     launches = sum(n for _, n in kt.values())
 
     # roofline of the dominant kernel

@@ -163,6 +163,12 @@ NLC_API nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps);
  * Synchronises the stream. */
 NLC_API nlc_status nlc_set_params(nlc_ctx* ctx, int32_t inst, const nlc_params* params);
 
+/* every > 0: nlc_step checks the state for non-finite values after every
+ * `every` steps of each call (one extra pass over the populations and Q, and
+ * a stream synchronisation) and stops with NLC_EUNSTABLE, naming the lattice
+ * and the step, when it finds any; 0 (default) never checks. */
+NLC_API nlc_status nlc_set_check(nlc_ctx* ctx, int32_t every);
+
 /* Selects the kernel schedule (NLC_SCHED_*) for later nlc_step calls. */
 NLC_API nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule);
 

@@ -93,6 +93,22 @@ __global__ void __launch_bounds__(256) k_field_out(Field<T> F, int nc, Dims d,
   for (int k = 0; k < nc; k++) out[k * d.n + idx] = (double)F.at(k, x, y, z);
 }
 
+// counts non-finite populations and Q components
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_count_nonfinite(const T* __restrict__ g, Field<T> Q,
+                                                         Dims d,
+                                                         unsigned long long* __restrict__ bad) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!decode(d, idx, x, y, z)) return;
+  int nbad = 0;
+#pragma unroll
+  for (int i = 0; i < Lat::Q; i++) nbad += !isfinite((double)g[(int64_t)i * d.n + idx]);
+#pragma unroll
+  for (int k = 0; k < 5; k++) nbad += !isfinite((double)Q.at(k, x, y, z));
+  if (nbad) atomicAdd(bad, (unsigned long long)nbad);
+}
+
 // interior of a padded 5-component field to a dense array of the same type
 // (checkpoints: bit-exact)
 template <class T>

@@ -151,6 +151,26 @@ class Engine final : public EngineBase {
 
   int count() const override { return (int)inst_.size(); }
 
+  nlc_status check_finite(int* bad) override {
+    cudaStream_t st = args_.stream;
+    *bad = -1;
+    for (size_t i = 0; i < inst_.size(); i++) {
+      InstHost<T>& I = inst_[i];
+      NLC_CK(cudaMemsetAsync(bad_, 0, sizeof(unsigned long long), st));
+      k_count_nonfinite<Lat, T><<<grid1(I.d.n), 256, 0, st>>>(I.g[cur_], I.q[cur_], I.d, bad_);
+      NLC_CK_LAUNCH("k_count_nonfinite");
+      unsigned long long nb = 0;
+      NLC_CK(cudaMemcpyAsync(&nb, bad_, sizeof(nb), cudaMemcpyDeviceToHost, st));
+      NLC_CK(cudaStreamSynchronize(st));
+      if (nb) {
+        *bad = (int)i;
+        err = std::to_string(nb) + " non-finite values in lattice " + std::to_string(i);
+        return NLC_EUNSTABLE;
+      }
+    }
+    return device_error();
+  }
+
   nlc_status set_params(int i, const nlc_params& q) override {
     InstHost<T>& I = inst_[i];
     I.p.A0 = (T)q.A0;

@@ -73,6 +73,9 @@ struct EngineBase {
   KernelTimer timer;
   int graph_steps = 0;  // >0: whole chunks of this many steps replay a CUDA graph
   virtual int count() const = 0;
+  // number of non-finite stored values of each lattice (syncs); first bad
+  // lattice in *bad (-1 if none)
+  virtual nlc_status check_finite(int* bad) = 0;
   virtual nlc_status set_params(int inst, const nlc_params& p) = 0;
   virtual nlc_status step(int64_t n, int schedule) = 0;
   virtual nlc_status set_fields(int inst, const double* Q5, const double* rho,

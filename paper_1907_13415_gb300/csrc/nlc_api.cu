@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -23,6 +24,7 @@ struct nlc_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   int schedule = NLC_SCHED_FUSED;
+  int check_every = 0;
   std::vector<int64_t> steps;  // per lattice, since its last nlc_set_fields
   std::unique_ptr<nlc::EngineBase> eng;
   std::string err;
@@ -208,9 +210,28 @@ nlc_status nlc_get_populations(nlc_ctx* ctx, int32_t inst, double* f) {
 nlc_status nlc_step(nlc_ctx* ctx, int64_t n) {
   if (!ctx) return NLC_EINVAL;
   if (n < 0) return fail(ctx, NLC_EINVAL, "negative step count");
-  nlc_status st = ctx->eng->step(n, ctx->schedule);
-  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
-  for (auto& s : ctx->steps) s += n;
+  const int64_t chunk = ctx->check_every > 0 ? ctx->check_every : n;
+  for (int64_t done = 0; done < n;) {
+    const int64_t k = std::min<int64_t>(chunk, n - done);
+    nlc_status st = ctx->eng->step(k, ctx->schedule);
+    if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+    for (auto& s : ctx->steps) s += k;
+    done += k;
+    if (ctx->check_every > 0) {
+      int bad = -1;
+      st = ctx->eng->check_finite(&bad);
+      if (st != NLC_OK)
+        return fail(ctx, st, ctx->eng->err + " after step " +
+                                 std::to_string(bad >= 0 ? ctx->steps[bad] : ctx->steps[0]));
+    }
+  }
+  return NLC_OK;
+}
+
+nlc_status nlc_set_check(nlc_ctx* ctx, int32_t every) {
+  if (!ctx) return NLC_EINVAL;
+  if (every < 0) return fail(ctx, NLC_EINVAL, "negative check interval");
+  ctx->check_every = every;
   return NLC_OK;
 }
 

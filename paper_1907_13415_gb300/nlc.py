@@ -92,6 +92,7 @@ def load(build_if_missing=True):
         "nlc_create_batch": ([I32, P, P, P, ctypes.POINTER(P)], I32),
         "nlc_count": ([P], I32),
         "nlc_set_graph": ([P, I32], I32),
+        "nlc_set_check": ([P, I32], I32),
         "nlc_set_params": ([P, I32, ctypes.POINTER(nlc_params)], I32),
         "nlc_set_schedule": ([P, I32], I32),
         "nlc_set_fields": ([P, I32, P, P, P], I32),
@@ -119,7 +120,7 @@ def load(build_if_missing=True):
 
 
 def exported_symbols():
-    return ["nlc_create", "nlc_create_batch", "nlc_count", "nlc_set_graph",
+    return ["nlc_create", "nlc_create_batch", "nlc_count", "nlc_set_graph", "nlc_set_check",
             "nlc_set_params",
             "nlc_set_schedule", "nlc_set_fields",
             "nlc_get_fields", "nlc_get_populations", "nlc_step",
@@ -179,6 +180,10 @@ def nlc_count(ctx):
 def nlc_set_params(ctx, inst, params):
     P = params if isinstance(params, nlc_params) else _params(params)
     _check(ctx, load().nlc_set_params(ctx, inst, ctypes.byref(P)))
+
+
+def nlc_set_check(ctx, every):
+    _check(ctx, load().nlc_set_check(ctx, int(every)))
 
 
 def nlc_set_graph(ctx, steps):

@@ -71,3 +71,26 @@ def test_corrupt_or_mismatched_checkpoint_is_rejected():
     assert ei.value.status == -1
     a.close()
     other.close()
+
+
+def test_periodic_check_reports_a_blow_up():
+    """Failure detection on the host side of a GPU run: a finite but absurd
+    initial Q (|Q| = 50) overflows within a few steps; with nlc_set_check the
+    step call stops with NLC_EUNSTABLE and names the step, and without the
+    check the observables count the non-finite values."""
+    from paper_1907_13415_gb300 import nlc
+    w = wl.flat_128x8().with_(shape=(1, 8, 32), size=16)
+    Q = w.initial_q5() * 150.0
+    s = make(w, 1)
+    s.set_fields(Q)
+    nlc.nlc_set_check(s.ctx, 2)
+    with pytest.raises(nlc.NlcError) as ei:
+        s.step(40)
+    assert ei.value.status == -4
+    assert "non-finite" in nlc.nlc_last_error(s.ctx)
+    s.close()
+    s = make(w, 1)
+    s.set_fields(Q)
+    s.step(40)
+    assert s.observables()["nonfinite"] > 0
+    s.close()
