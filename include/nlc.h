@@ -255,6 +255,30 @@ NLC_API const char* nlc_timing_name(int32_t k);
 NLC_API nlc_status nlc_adjoint(nlc_ctx* ctx, const nlc_loss* loss, int64_t nsteps,
                                int32_t ckpt_every, nlc_grad* out, double* dQ0);
 
+/* Observables of a state held by the caller in device memory, computed
+ * without allocating any device memory.  The paper has no counterpart: this
+ * serves callers that may not call cudaMalloc, such as code inside a host
+ * application that owns all device memory through its own pool, or
+ * monitoring code that must not trigger the device-wide synchronisation of
+ * an allocation.  Inputs (device pointers, float64, layouts as the host
+ * arrays above): f the pre-collision populations [q][nz][ny][nx] in the
+ * order nlc_lattice_velocities gives (as nlc_get_populations returns them),
+ * Q5 [5][nz][ny][nx].  *out (host) gets the same values nlc_observables
+ * reports for that state (step = 0).  All intermediates live in one fixed
+ * block of device memory inside the library (about 17 MB, held by every
+ * device that loads the library until the process exits); hence the limits
+ * nx*ny*nz <= NLC_STATIC_MAX_CELLS, nx <= NLC_STATIC_MAX_NX and
+ * (nx + 8)(ny + 4)(nz + 4) <= 262144 on D3Q19 ((nx + 8)(ny + 4) on D2Q9,
+ * nx + 8 rounded up to a multiple of 4); larger lattices get NLC_EINVAL.
+ * The first call on a device looks up that block's device address; make it
+ * before any stream capture.  Calls share the block: calls that overlap on
+ * the GPU race.  Queued on stream; synchronises it. */
+#define NLC_STATIC_MAX_CELLS 65536
+#define NLC_STATIC_MAX_NX 4096
+NLC_API nlc_status nlc_observables_static(const nlc_grid* grid, const nlc_params* params,
+                                          const double* f, const double* Q5, void* stream,
+                                          nlc_obs* out);
+
 /* Message of the last failed call on ctx (empty if none).  Owned by ctx. */
 NLC_API const char* nlc_last_error(const nlc_ctx* ctx);
 

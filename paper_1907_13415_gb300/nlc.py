@@ -19,6 +19,7 @@ STATUS = {0: "NLC_OK", -1: "NLC_EINVAL", -2: "NLC_ENOMEM", -3: "NLC_ECUDA",
 NLC_D2Q9, NLC_D3Q19 = 0, 1
 NLC_FP64, NLC_FP32 = 0, 1
 NLC_SCHED_FUSED, NLC_SCHED_UNFUSED = 0, 1
+NLC_STATIC_MAX_CELLS, NLC_STATIC_MAX_NX = 65536, 4096
 
 
 class NlcError(RuntimeError):
@@ -106,6 +107,8 @@ def load(build_if_missing=True):
         "nlc_set_timing": ([P, I32], I32),
         "nlc_save": ([P, P, ctypes.POINTER(ctypes.c_size_t)], I32),
         "nlc_adjoint": ([P, P, I64, I32, P, P], I32),
+        "nlc_observables_static": ([ctypes.POINTER(nlc_grid), ctypes.POINTER(nlc_params),
+                                    P, P, P, ctypes.POINTER(nlc_obs)], I32),
         "nlc_load": ([P, P, ctypes.c_size_t], I32),
         "nlc_get_timing": ([P, I32, P, P, P], I32),
         "nlc_timing_name": ([I32], ctypes.c_char_p),
@@ -127,7 +130,7 @@ def exported_symbols():
             "nlc_observables", "nlc_last_error", "nlc_destroy",
             "nlc_lattice_velocities", "nlc_version", "nlc_set_timing",
             "nlc_get_timing", "nlc_timing_name", "nlc_save", "nlc_load",
-            "nlc_adjoint"]
+            "nlc_adjoint", "nlc_observables_static"]
 
 
 def _check(ctx, status):
@@ -276,6 +279,20 @@ def nlc_adjoint(ctx, loss, nsteps, ckpt_every, dQ0=None):
                                    int(nsteps), int(ckpt_every),
                                    ctypes.cast(ctypes.pointer(out), ctypes.c_void_p),
                                    _ptr(dQ0)))
+    return out.as_dict()
+
+
+def nlc_observables_static(grid, params, f_dev, Q5_dev, stream=None):
+    """Observables of a state in caller-owned device memory (f_dev and
+    Q5_dev are device addresses of float64 arrays); allocates no device
+    memory (see include/nlc.h)."""
+    out = nlc_obs()
+    P = params if isinstance(params, nlc_params) else _params(params)
+    st = load().nlc_observables_static(ctypes.byref(grid), ctypes.byref(P),
+                                       ctypes.c_void_p(f_dev), ctypes.c_void_p(Q5_dev),
+                                       ctypes.c_void_p(stream or 0), ctypes.byref(out))
+    if st != NLC_OK:
+        raise NlcError(st, "nlc_observables_static failed")
     return out.as_dict()
 
 
