@@ -28,10 +28,12 @@
 #pragma once
 #include "common.cuh"
 #include "lattice.cuh"
+#include "packed.cuh"
 #include "physics.cuh"
 #include "step_unfused.cuh"
 #include "tma.cuh"
 
+#include <type_traits>
 #include <vector>
 
 namespace nlc {
@@ -48,6 +50,26 @@ static_assert(FNT >= A1 && FNT % 32 == 0, "ring phase needs one thread per cell"
 
 // box index of lattice offset (dx, dy) from the tile origin (x0, y0)
 __host__ __device__ constexpr int box_at(int dx, int dy) { return (dy + 2) * BXW + dx + 4; }
+
+// Ring-phase thread t -> cell (cx, cy) of the tile plus its one-cell ring,
+// cx in [-1, FTX], cy in [-1, FTY], and its index ri = (cy + 1) RX1 + cx + 1
+// in the ring-region arrays.  The first FTX (FTY + 2) threads take whole rows
+// of FTX cells, one warp per row, so every shared-memory access of those
+// warps is one contiguous run (no bank conflicts); the last 2 (FTY + 2)
+// threads take the left and right ring columns.
+static_assert(FTX == 32, "one warp per ring row");
+__device__ __forceinline__ void ring_cell(int t, int& cx, int& cy, int& ri) {
+  constexpr int NROW = FTX * (FTY + 2);
+  if (t < NROW) {
+    cx = t % FTX;
+    cy = t / FTX - 1;
+  } else {
+    const int k = t - NROW;
+    cx = (k & 1) ? FTX : -1;
+    cy = (k >> 1) - 1;
+  }
+  ri = (cy + 1) * RX1 + cx + 1;
+}
 
 template <class T>
 constexpr size_t align128(size_t bytes) {
@@ -88,39 +110,73 @@ struct LbCfg {
   static constexpr uint32_t tx_bytes = sizeof(T) * 5 * BA;
 };
 
-// stress on the ring-region cell c of a plane whose Q box is in sq (z
-// neighbours in sqm, sqp), into the Pi slot sp
+// 2d+1-point Laplacian from the centre value and its axis neighbours (zp, zm
+// unused on a single plane).  FP64 keeps the per-axis form; FP32 sums the
+// neighbours first and removes 2d v with one fused multiply-add.
 template <class T, int DIM>
-__device__ __forceinline__ void stress_ring_cell(int c, const T* __restrict__ sq,
+__device__ __forceinline__ T lap_points(T v, T xp, T xm, T yp, T ym, T zp, T zm) {
+  if constexpr (std::is_same<T, float>::value) {
+    float s = (xp + xm) + (yp + ym);
+    if (DIM == 3) s += zp + zm;
+    return fmaf(-2.0f * DIM, v, s);
+  } else {
+    T l = (xp + xm - T(2) * v) + (yp + ym - T(2) * v);
+    if (DIM == 3) l += zp + zm - T(2) * v;
+    return l;
+  }
+}
+
+// stress on the ring-region cell of ring-phase thread t of a plane whose Q
+// box is in sq (z neighbours in sqm, sqp), into the Pi slot sp.  The first derivatives are
+// kept as plain differences (twice the central difference); the stress sees
+// them with K/4, which gives K dQ:dQ exactly (scalings by powers of two are
+// exact).
+template <class T, int DIM>
+__device__ __forceinline__ void stress_ring_cell(int t, const T* __restrict__ sq,
                                                  const T* __restrict__ sqm,
                                                  const T* __restrict__ sqp,
                                                  T* __restrict__ sp, const Par<T>& p) {
-  const int o = box_at(c % RX1 - 1, c / RX1 - 1);
-  T q[5], dq[3][5], lap[5], h[5], P[3][3];
+  int cx, cy, c;
+  ring_cell(t, cx, cy, c);
+  const int o = box_at(cx, cy);
+  T q[5], dq2[3][5], lap[5], h[5], P[3][3];
 #pragma unroll
   for (int k = 0; k < 5; k++) {
     const T* F = sq + k * BA;
     const T v = F[o], xp = F[o + 1], xm = F[o - 1], yp = F[o + BXW], ym = F[o - BXW];
     q[k] = v;
-    dq[0][k] = (xp - xm) / T(2);
-    dq[1][k] = (yp - ym) / T(2);
-    T l = (xp + xm - T(2) * v) + (yp + ym - T(2) * v);
+    dq2[0][k] = xp - xm;
+    dq2[1][k] = yp - ym;
+    T zp = T(0), zm = T(0);
     if (DIM == 3) {
-      const T zp = sqp[k * BA + o], zm = sqm[k * BA + o];
-      dq[2][k] = (zp - zm) / T(2);
-      l += zp + zm - T(2) * v;
-    } else {
-      dq[2][k] = T(0);
+      zp = sqp[k * BA + o];
+      zm = sqm[k * BA + o];
     }
-    lap[k] = l;
+    dq2[2][k] = zp - zm;
+    lap[k] = lap_points<T, DIM>(v, xp, xm, yp, ym, zp, zm);
   }
   molecular_field(q, lap, p, h);
-  stress<T, DIM>(q, h, dq, p, P);
+  Par<T> p4 = p;
+  p4.K = p.K * T(0.25);
+  stress<T, DIM>(q, h, dq2, p4, P);
 #pragma unroll
   for (int a = 0; a < DIM; a++)
 #pragma unroll
     for (int b = 0; b < DIM; b++) sp[(a * DIM + b) * A1 + c] = P[a][b];
 }
+
+// Populations of one cell as the lb kernel holds them in registers: FP32
+// keeps the rest value and the opposite pairs (packed arithmetic), FP64 a
+// plain array.
+template <class Lat, class T>
+struct CellPops {
+  T g[Lat::Q];
+};
+template <class Lat>
+struct CellPops<Lat, float> {
+  float g0;
+  float2 gp[(Lat::Q - 1) / 2];
+};
 
 template <class Lat, class T>
 __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
@@ -199,7 +255,9 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   // The populations of the next plane are pulled into registers (gn) as
   // soon as the current plane is done, so their loads are in flight while
   // the block computes the next plane's stress.
-  T gn[Lat::Q];
+  constexpr bool kPacked = std::is_same<T, float>::value;
+  constexpr int NP = (Lat::Q - 1) / 2;
+  CellPops<Lat, T> gn;
   auto pull_next = [&](int z) {
     if (!cell) return;
     int plane[3];
@@ -209,11 +267,21 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     // 32-bit element offsets within a population plane; the plane of
     // population i starts i * n elements after gin
     const unsigned n32 = (unsigned)d.n;
-#pragma unroll
-    for (int i = 0; i < Lat::Q; i++) {
+    auto ld = [&](int i) {
       const unsigned off = (unsigned)(plane[Lat::c(i, 2) + 1] + rowy[Lat::c(i, 1) + 1] +
                                       colx[Lat::c(i, 0) + 1]);
-      gn[i] = __ldg(gin + (size_t)i * n32 + off);
+      return __ldg(gin + (size_t)i * n32 + off);
+    };
+    if constexpr (kPacked) {
+      gn.g0 = ld(0);
+#pragma unroll
+      for (int q = 0; q < NP; q++) {
+        const int i = pair_first<Lat>(q);
+        gn.gp[q] = make_float2(ld(i), ld(Lat::opp(i)));
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < Lat::Q; i++) gn.g[i] = ld(i);
     }
   };
 
@@ -225,20 +293,38 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     const T* Pp = DIM == 3 ? sP(pslot(z + 1)) : Pc;
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
-      T s = (Pc[(a * DIM + 0) * A1 + ic + 1] - Pc[(a * DIM + 0) * A1 + ic - 1]) / T(2);
-      s += (Pc[(a * DIM + 1) * A1 + ic + RX1] - Pc[(a * DIM + 1) * A1 + ic - RX1]) / T(2);
-      if (DIM == 3) s += (Pp[(a * DIM + 2) * A1 + ic] - Pm[(a * DIM + 2) * A1 + ic]) / T(2);
-      F[a] = s;
+      // F_a = sum_b [Pi_ab(x + e_b) - Pi_ab(x - e_b)] / 2
+      T s = Pc[(a * DIM + 0) * A1 + ic + 1] - Pc[(a * DIM + 0) * A1 + ic - 1];
+      s += Pc[(a * DIM + 1) * A1 + ic + RX1] - Pc[(a * DIM + 1) * A1 + ic - RX1];
+      if (DIM == 3) s += Pp[(a * DIM + 2) * A1 + ic] - Pm[(a * DIM + 2) * A1 + ic];
+      F[a] = s * T(0.5);
     }
-    T g[Lat::Q], rho, u[3];
-#pragma unroll
-    for (int i = 0; i < Lat::Q; i++) g[i] = gn[i];
-    moments<Lat, T>(g, F, p, rho, u);
-    collide_bgk<Lat, T>(g, rho, u, F, p);
     const unsigned o = (unsigned)(z * nxy + rowy[1] + x);
     const unsigned n32 = (unsigned)d.n;
+    T rho, u[3];
+    if constexpr (kPacked) {
+      float g0 = gn.g0, drho;
+      float2 gp[NP];
 #pragma unroll
-    for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = g[i];
+      for (int q = 0; q < NP; q++) gp[q] = gn.gp[q];
+      moments_pairs<Lat>(g0, gp, F, p.rho0, rho, drho, u);
+      collide_bgk_pairs<Lat>(g0, gp, rho, drho, u, F, p.inv_tau, p.guo);
+      gout[o] = g0;
+#pragma unroll
+      for (int q = 0; q < NP; q++) {
+        const int i = pair_first<Lat>(q);
+        gout[(size_t)i * n32 + o] = gp[q].x;
+        gout[(size_t)Lat::opp(i) * n32 + o] = gp[q].y;
+      }
+    } else {
+      T g[Lat::Q];
+#pragma unroll
+      for (int i = 0; i < Lat::Q; i++) g[i] = gn.g[i];
+      moments<Lat, T>(g, F, p, rho, u);
+      collide_bgk<Lat, T>(g, rho, u, F, p);
+#pragma unroll
+      for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = g[i];
+    }
     store_with_images<T, DIM, DIM>(U, d, x, y, z, u);
     if (z + 1 < z1) pull_next(z + 1);
   };
@@ -399,35 +485,39 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     }
   };
 
-  // predictor on ring cell c of plane z: R(Q^n) and Q^P = Q^n + R
-  auto predict = [&](int z, int c) {
-    const int o = box_at(c % RX1 - 1, c / RX1 - 1);
+  // predictor on the ring cell of ring-phase thread t of plane z: R(Q^n) and
+  // Q^P = Q^n + R
+  auto predict = [&](int z, int t) {
+    int cx, cy, c;
+    ring_cell(t, cx, cy, c);
+    const int o = box_at(cx, cy);
     const T* qc = sQ(qs(z));
     const T* qm = DIM == 3 ? sQ(qs(z - 1)) : qc;
     const T* qp = DIM == 3 ? sQ(qs(z + 1)) : qc;
     const T* uc = sU(us(z));
     const T* um = DIM == 3 ? sU(us(z - 1)) : uc;
     const T* up = DIM == 3 ? sU(us(z + 1)) : uc;
-    T q[5], dq[3][5], lap[5], u[3], G[3][3], r[5];
+    T q[5], dq2[3][5], lap[5], u[3], G[3][3], r[5];
 #pragma unroll
     for (int k = 0; k < 5; k++) {
       const T* F = qc + k * BA;
       const T v = F[o], xp = F[o + 1], xm = F[o - 1], yp = F[o + BXW], ym = F[o - BXW];
       q[k] = v;
-      dq[0][k] = (xp - xm) / T(2);
-      dq[1][k] = (yp - ym) / T(2);
-      T l = (xp + xm - T(2) * v) + (yp + ym - T(2) * v);
+      dq2[0][k] = xp - xm;
+      dq2[1][k] = yp - ym;
+      T zp = T(0), zm = T(0);
       if (DIM == 3) {
-        const T zp = qp[k * BA + o], zm = qm[k * BA + o];
-        dq[2][k] = (zp - zm) / T(2);
-        l += zp + zm - T(2) * v;
-      } else {
-        dq[2][k] = T(0);
+        zp = qp[k * BA + o];
+        zm = qm[k * BA + o];
       }
-      lap[k] = l;
+      dq2[2][k] = zp - zm;
+      lap[k] = lap_points<T, DIM>(v, xp, xm, yp, ym, zp, zm);
     }
     box_ugrad<T, DIM>(uc, um, up, o, u, G);
-    be_rhs<T, DIM>(q, dq, lap, u, G, p, r);
+    // advection u.dQ from the plain differences: (u/2).(2 dQ), exact
+#pragma unroll
+    for (int a = 0; a < 3; a++) u[a] *= T(0.5);
+    be_rhs<T, DIM>(q, dq2, lap, u, G, p, r);
     T* qpo = sQP(ps(z));
     T* ro = sR(rs(z));
 #pragma unroll
@@ -449,27 +539,27 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     const T* pc = sQP(ps(z));
     const T* pm = DIM == 3 ? sQP(ps(z - 1)) : pc;
     const T* pp = DIM == 3 ? sQP(ps(z + 1)) : pc;
-    T qp[5], dq[3][5], lap[5], u[3], G[3][3], r2[5], out[5];
+    T qp[5], dq2[3][5], lap[5], u[3], G[3][3], r2[5], out[5];
 #pragma unroll
     for (int k = 0; k < 5; k++) {
       const T* F = pc + k * A1;
       const T v = F[ic], xp = F[ic + 1], xm = F[ic - 1], yp = F[ic + RX1], ym = F[ic - RX1];
       qp[k] = v;
-      dq[0][k] = (xp - xm) / T(2);
-      dq[1][k] = (yp - ym) / T(2);
-      T l = (xp + xm - T(2) * v) + (yp + ym - T(2) * v);
+      dq2[0][k] = xp - xm;
+      dq2[1][k] = yp - ym;
+      T zp = T(0), zm = T(0);
       if (DIM == 3) {
-        const T zp = pp[k * A1 + ic], zm = pm[k * A1 + ic];
-        dq[2][k] = (zp - zm) / T(2);
-        l += zp + zm - T(2) * v;
-      } else {
-        dq[2][k] = T(0);
+        zp = pp[k * A1 + ic];
+        zm = pm[k * A1 + ic];
       }
-      lap[k] = l;
+      dq2[2][k] = zp - zm;
+      lap[k] = lap_points<T, DIM>(v, xp, xm, yp, ym, zp, zm);
     }
     box_ugrad<T, DIM>(sU(us(z)), DIM == 3 ? sU(us(z - 1)) : sU(us(z)),
                       DIM == 3 ? sU(us(z + 1)) : sU(us(z)), o2, u, G);
-    be_rhs<T, DIM>(qp, dq, lap, u, G, p, r2);
+#pragma unroll
+    for (int a = 0; a < 3; a++) u[a] *= T(0.5);
+    be_rhs<T, DIM>(qp, dq2, lap, u, G, p, r2);
     const T* qn = sQ(qs(z));
     const T* r1 = sR(rs(z));
 #pragma unroll
