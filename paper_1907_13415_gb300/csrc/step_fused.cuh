@@ -101,7 +101,10 @@ struct LbCfg {
   static constexpr int DIM = Lat::DIM;
   static constexpr int NPI = DIM * DIM;
   static constexpr int NSQ = DIM == 3 ? 4 : 1;  // Q plane slots
-  static constexpr int NSP = DIM == 3 ? 3 : 1;  // Pi plane slots
+  // Pi plane slots: the ring phase of plane z+1 may start while slower
+  // threads still read Pi(z-2..z) for plane z-1, so four slots let one
+  // barrier per plane suffice
+  static constexpr int NSP = DIM == 3 ? 4 : 1;
   static constexpr size_t q_slot = align128<T>(sizeof(T) * 5 * BA);
   static constexpr size_t p_slot = align128<T>(sizeof(T) * NPI * A1);
   static constexpr size_t off_p = NSQ * q_slot;
@@ -359,7 +362,8 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
       stress_ring_cell<T, DIM>(tid, sQ(qslot(z0)), sQ(qslot(z0 - 1)), sQ(qslot(z0 + 1)),
                                sP(pslot(z0)), p);
     for (int z = z0; z < z1; z++) {
-      __syncthreads();
+      // Q(z+3) reuses the slot of Q(z-1), last read by the ring phase of
+      // plane z, which every thread finished before the previous barrier
       if (tid == 0 && z + 3 <= z1 + 1) issue(z + 3);
       wait(z + 2);
       if (tid < A1)
@@ -382,17 +386,19 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
 template <class Lat, class T>
 struct BeCfg {
   static constexpr int DIM = Lat::DIM;
-  static constexpr int NSQ = DIM == 3 ? 4 : 1;   // Q^n plane slots
-  static constexpr int NSU = DIM == 3 ? 5 : 1;   // u plane slots
-  static constexpr int NSP = DIM == 3 ? 3 : 1;   // Q^P plane slots
-  static constexpr int NSR = DIM == 3 ? 2 : 1;   // R(Q^n) plane slots
+  // Plane slots, sized so that one barrier per plane suffices: at plane z
+  // the predictor of z+1 and the copies of plane z+3 may overlap slower
+  // threads still correcting plane z-1 (which reads Q^n(z-1), u(z-2..z) and
+  // Q^P(z-2..z)).
+  static constexpr int NSQ = DIM == 3 ? 5 : 1;   // Q^n plane slots
+  static constexpr int NSU = DIM == 3 ? 6 : 1;   // u plane slots
+  static constexpr int NSP = DIM == 3 ? 4 : 1;   // Q^P plane slots
   static constexpr size_t q_slot = align128<T>(sizeof(T) * 5 * BA);
   static constexpr size_t u_slot = align128<T>(sizeof(T) * DIM * BA);
   static constexpr size_t p_slot = align128<T>(sizeof(T) * 5 * A1);
   static constexpr size_t off_u = NSQ * q_slot;
   static constexpr size_t off_p = off_u + NSU * u_slot;
-  static constexpr size_t off_r = off_p + NSP * p_slot;
-  static constexpr size_t off_bar = off_r + NSR * p_slot;
+  static constexpr size_t off_bar = off_p + NSP * p_slot;
   static constexpr size_t bytes = off_bar + 8 * (NSQ + NSU);
   static constexpr uint32_t q_tx = sizeof(T) * 5 * BA;
   static constexpr uint32_t u_tx = sizeof(T) * DIM * BA;
@@ -435,7 +441,6 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   auto sQ = [&](int s) { return reinterpret_cast<T*>(smem + s * C::q_slot); };
   auto sU = [&](int s) { return reinterpret_cast<T*>(smem + C::off_u + s * C::u_slot); };
   auto sQP = [&](int s) { return reinterpret_cast<T*>(smem + C::off_p + s * C::p_slot); };
-  auto sR = [&](int s) { return reinterpret_cast<T*>(smem + C::off_r + s * C::p_slot); };
 
   const TileRef tile = tiles[blockIdx.x];
   const InstDev<T>& I = insts[tile.inst];
@@ -457,7 +462,6 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   auto us = [&](int z) { return (z - zl0) % C::NSU; };
   auto upar = [&](int z) { return (uint32_t)(((z - zl0) / C::NSU) & 1); };
   auto ps = [&](int z) { return (z - zr0) % C::NSP; };
-  auto rs = [&](int z) { return (z - zr0) % C::NSR; };
 
   if (tid == 0) {
     for (int s = 0; s < C::NSQ + C::NSU; s++) mbar_init(&qbar[s], 1);
@@ -519,12 +523,8 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     for (int a = 0; a < 3; a++) u[a] *= T(0.5);
     be_rhs<T, DIM>(q, dq2, lap, u, G, p, r);
     T* qpo = sQP(ps(z));
-    T* ro = sR(rs(z));
 #pragma unroll
-    for (int k = 0; k < 5; k++) {
-      ro[k * A1 + c] = r[k];
-      qpo[k * A1 + c] = q[k] + r[k];
-    }
+    for (int k = 0; k < 5; k++) qpo[k * A1 + c] = q[k] + r[k];
   };
 
   const int tx = tid % FTX, ty = tid / FTX;
@@ -560,10 +560,11 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
     for (int a = 0; a < 3; a++) u[a] *= T(0.5);
     be_rhs<T, DIM>(qp, dq2, lap, u, G, p, r2);
+    // Q^{n+1} = Q^n + [R(Q^n) + R(Q^P)]/2 = [Q^n + Q^P + R(Q^P)]/2, since
+    // Q^P = Q^n + R(Q^n)
     const T* qn = sQ(qs(z));
-    const T* r1 = sR(rs(z));
 #pragma unroll
-    for (int k = 0; k < 5; k++) out[k] = qn[k * BA + o2] + (r1[k * A1 + ic] + r2[k]) / T(2);
+    for (int k = 0; k < 5; k++) out[k] = (qn[k * BA + o2] + qp[k] + r2[k]) * T(0.5);
     store_with_images<T, 5, DIM>(Qout, d, x, y, z, out);
   };
 
@@ -581,10 +582,11 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     }
     correct(0);
   } else {
-    if (tid == 0) {
-      for (int z = z0 - 2; z <= z0 + 1; z++) issue_q(z);
-      for (int z = z0 - 2; z <= z0 + 2; z++) issue_u(z);
-    }
+    if (tid == 0)
+      for (int z = z0 - 2; z <= z0 + 2; z++) {
+        issue_q(z);
+        issue_u(z);
+      }
     for (int z = z0 - 2; z <= z0; z++) {
       wait_q(z);
       wait_u(z);
@@ -594,12 +596,10 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
       abort_block();
       return;
     }
-    if (tid == 0) issue_q(z0 + 2);
     wait_q(z0 + 1);
     wait_u(z0 + 1);
     if (tid < A1) predict(z0, tid);
     for (int z = z0; z < z1; z++) {
-      __syncthreads();
       if (tid == 0 && z + 3 <= z1 + 1) {
         issue_q(z + 3);
         issue_u(z + 3);
