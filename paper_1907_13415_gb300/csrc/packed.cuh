@@ -34,9 +34,10 @@ __host__ __device__ __forceinline__ float2 padd(float2 a, float2 b) {
 #endif
 }
 
+// a - b as one fused multiply-add, fma(b, -1, a), exact like a subtraction
 __host__ __device__ __forceinline__ float2 psub(float2 a, float2 b) {
 #ifdef __CUDA_ARCH__
-  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
 #else
   return make_float2(a.x - b.x, a.y - b.y);
 #endif

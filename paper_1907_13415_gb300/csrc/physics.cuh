@@ -9,6 +9,16 @@
 
 namespace nlc {
 
+// fused multiply-add, written out where the pointwise physics wants one
+// rounding per product-and-sum (other scalar types, such as the complex
+// type of the derivative checks, add their own overload)
+__host__ __device__ __forceinline__ double fma_(double a, double b, double c) {
+  return fma(a, b, c);
+}
+__host__ __device__ __forceinline__ float fma_(float a, float b, float c) {
+  return fmaf(a, b, c);
+}
+
 template <class T>
 struct Par {
   T A0, K, gamma, Gamma, xi, tau, rho0;
@@ -48,7 +58,7 @@ __host__ __device__ __forceinline__ void molecular_field(const T q[5], const T l
   const T tr2 = a * a + d * d + f * f + T(2) * (b * b + c * c + e * e);
   const T Ag = p.A0 * p.gamma;
   const T c1 = -p.A0 * (T(1) - p.gamma / T(3)) - Ag * tr2;
-  const T c3 = -Ag * tr2 / T(3);
+  const T c3 = (-Ag / T(3)) * tr2;  // parameter factor, no division per cell
   h[0] = c1 * a + Ag * qq0 + c3 + p.K * lap[0];
   h[1] = c1 * b + Ag * qq1 + p.K * lap[1];
   h[2] = c1 * c + Ag * qq2 + p.K * lap[2];
@@ -70,27 +80,29 @@ __host__ __device__ __forceinline__ void stress(const T q[5], const T h[5],
   const T Q[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], -q[0] - q[3]}};
   const T H[3][3] = {{h[0], h[1], h[2]}, {h[1], h[3], h[4]}, {h[2], h[4], -h[0] - h[3]}};
   // Q:H over all nine entries
-  const T qh = Q[0][0] * H[0][0] + Q[1][1] * H[1][1] + Q[2][2] * H[2][2] +
-               T(2) * (q[1] * h[1] + q[2] * h[2] + q[4] * h[4]);
+  const T qh = fma_(Q[0][0], H[0][0], fma_(Q[1][1], H[1][1], Q[2][2] * H[2][2])) +
+               T(2) * fma_(q[1], h[1], fma_(q[2], h[2], q[4] * h[4]));
   const T xm1 = p.xi - T(1), xp1 = p.xi + T(1), x23 = T(2) * p.xi / T(3);
+  const T xqh = T(2) * p.xi * qh;
   T X[3][3];  // X = Q H
 #pragma unroll
   for (int a = 0; a < DIM; a++)
 #pragma unroll
     for (int b = 0; b < DIM; b++)
-      X[a][b] = Q[a][0] * H[0][b] + Q[a][1] * H[1][b] + Q[a][2] * H[2][b];
+      X[a][b] = fma_(Q[a][0], H[0][b], fma_(Q[a][1], H[1][b], Q[a][2] * H[2][b]));
 #pragma unroll
   for (int a = 0; a < DIM; a++)
 #pragma unroll
     for (int b = a; b < DIM; b++) {
       // d_a Q : d_b Q over all nine entries (off-diagonals twice, zz included)
-      const T el = T(2) * (dq[a][0] * dq[b][0] + dq[a][3] * dq[b][3]) +
-                   dq[a][0] * dq[b][3] + dq[a][3] * dq[b][0] +
-                   T(2) * (dq[a][1] * dq[b][1] + dq[a][2] * dq[b][2] + dq[a][4] * dq[b][4]);
+      const T el = T(2) * fma_(dq[a][0], dq[b][0], dq[a][3] * dq[b][3]) +
+                   fma_(dq[a][0], dq[b][3], dq[a][3] * dq[b][0]) +
+                   T(2) * fma_(dq[a][1], dq[b][1],
+                               fma_(dq[a][2], dq[b][2], dq[a][4] * dq[b][4]));
       const T qt = Q[a][b] + (a == b ? T(1) / T(3) : T(0));
-      const T sym = T(2) * p.xi * qt * qh - x23 * H[a][b] - p.K * el;
-      Pi[a][b] = sym - xm1 * X[a][b] - xp1 * X[b][a];
-      if (b != a) Pi[b][a] = sym - xm1 * X[b][a] - xp1 * X[a][b];
+      const T sym = fma_(xqh, qt, fma_(-x23, H[a][b], -p.K * el));
+      Pi[a][b] = fma_(-xm1, X[a][b], fma_(-xp1, X[b][a], sym));
+      if (b != a) Pi[b][a] = fma_(-xm1, X[b][a], fma_(-xp1, X[a][b], sym));
     }
 }
 
@@ -103,26 +115,29 @@ __host__ __device__ __forceinline__ void stress(const T q[5], const T h[5],
 template <class T>
 __host__ __device__ __forceinline__ void corotation(const T G[3][3], const T q[5],
                                            T xi, T s[5]) {
-  const T Qt[3][3] = {{q[0] + T(1) / T(3), q[1], q[2]},
-                      {q[1], q[3] + T(1) / T(3), q[4]},
-                      {q[2], q[4], -q[0] - q[3] + T(1) / T(3)}};
+  const T third = T(1) / T(3);
+  const T Qt[3][3] = {{q[0] + third, q[1], q[2]},
+                      {q[1], q[3] + third, q[4]},
+                      {q[2], q[4], third - q[0] - q[3]}};
   const T hp = (xi + T(1)) * T(0.5), hm = (xi - T(1)) * T(0.5);
   T M[3][3];
 #pragma unroll
   for (int a = 0; a < 3; a++)
 #pragma unroll
-    for (int b = 0; b < 3; b++) M[a][b] = hp * G[a][b] + hm * G[b][a];
+    for (int b = 0; b < 3; b++) M[a][b] = fma_(hp, G[a][b], hm * G[b][a]);
   // Q_ge d_g u_e = sum Q_ge G_eg
-  const T qg = q[0] * G[0][0] + q[3] * G[1][1] + (-q[0] - q[3]) * G[2][2] +
-               q[1] * (G[0][1] + G[1][0]) + q[2] * (G[0][2] + G[2][0]) +
-               q[4] * (G[1][2] + G[2][1]);
-  auto P = [&](int a, int b) { return M[a][0] * Qt[0][b] + M[a][1] * Qt[1][b] + M[a][2] * Qt[2][b]; };
+  const T qg = fma_(q[0], G[0][0] - G[2][2], fma_(q[3], G[1][1] - G[2][2],
+               fma_(q[1], G[0][1] + G[1][0], fma_(q[2], G[0][2] + G[2][0],
+                                                  q[4] * (G[1][2] + G[2][1])))));
+  auto P = [&](int a, int b) {
+    return fma_(M[a][0], Qt[0][b], fma_(M[a][1], Qt[1][b], M[a][2] * Qt[2][b]));
+  };
   const T t = T(2) * xi * qg;
-  s[0] = T(2) * P(0, 0) - t * Qt[0][0];
-  s[1] = P(0, 1) + P(1, 0) - t * Qt[0][1];
-  s[2] = P(0, 2) + P(2, 0) - t * Qt[0][2];
-  s[3] = T(2) * P(1, 1) - t * Qt[1][1];
-  s[4] = P(1, 2) + P(2, 1) - t * Qt[1][2];
+  s[0] = fma_(-t, Qt[0][0], T(2) * P(0, 0));
+  s[1] = fma_(-t, Qt[0][1], P(0, 1) + P(1, 0));
+  s[2] = fma_(-t, Qt[0][2], P(0, 2) + P(2, 0));
+  s[3] = fma_(-t, Qt[1][1], T(2) * P(1, 1));
+  s[4] = fma_(-t, Qt[1][2], P(1, 2) + P(2, 1));
 }
 
 // Right-hand side of Eq. 1 at one cell,
@@ -132,29 +147,36 @@ __host__ __device__ __forceinline__ void corotation(const T G[3][3], const T q[5
 // 2 xi div(u)/3 identically, so Tr(R) = 2 xi (G_xx + G_yy + G_zz)/3.
 // Inputs: q (5), its central first derivatives dq[g][k], its Laplacian
 // lap[k], u (3), G.
+// The same from the advection term adv[k] = u_g d_g Q_k already formed.
+template <class T>
+__host__ __device__ __forceinline__ void be_rhs_adv(const T q[5], const T adv[5],
+                                           const T lap[5], const T G[3][3],
+                                           const Par<T>& p, T r[5]) {
+  T h[5], s[5];
+  molecular_field(q, lap, p, h);
+  corotation(G, q, p.xi, s);
+  // parameter factor first: no division per cell
+  const T tr3 = (T(2) * p.xi / T(9)) * (G[0][0] + G[1][1] + G[2][2]);
+  r[0] = fma_(p.Gamma, h[0], s[0] - adv[0]) - tr3;
+  r[1] = fma_(p.Gamma, h[1], s[1] - adv[1]);
+  r[2] = fma_(p.Gamma, h[2], s[2] - adv[2]);
+  r[3] = fma_(p.Gamma, h[3], s[3] - adv[3]) - tr3;
+  r[4] = fma_(p.Gamma, h[4], s[4] - adv[4]);
+}
+
 template <class T, int DIM>
 __host__ __device__ __forceinline__ void be_rhs(const T q[5], const T dq[3][5],
                                        const T lap[5], const T u[3],
                                        const T G[3][3], const Par<T>& p,
                                        T r[5]) {
-  T h[5], s[5];
-  molecular_field(q, lap, p, h);
-  corotation(G, q, p.xi, s);
   T adv[5];
 #pragma unroll
   for (int k = 0; k < 5; k++) {
-    T a = u[0] * dq[0][k] + u[1] * dq[1][k];
-    if (DIM == 3) a += u[2] * dq[2][k];
+    T a = fma_(u[0], dq[0][k], u[1] * dq[1][k]);
+    if (DIM == 3) a = fma_(u[2], dq[2][k], a);
     adv[k] = a;
   }
-  const T tr3 = T(2) * p.xi * (G[0][0] + G[1][1] + G[2][2]) / T(9);
-  const T rxx = -adv[0] + s[0] + p.Gamma * h[0];
-  const T ryy = -adv[3] + s[3] + p.Gamma * h[3];
-  r[0] = rxx - tr3;
-  r[1] = -adv[1] + s[1] + p.Gamma * h[1];
-  r[2] = -adv[2] + s[2] + p.Gamma * h[2];
-  r[3] = ryy - tr3;
-  r[4] = -adv[4] + s[4] + p.Gamma * h[4];
+  be_rhs_adv(q, adv, lap, G, p, r);
 }
 
 // Equilibrium deviation g^eq_i = f^eq_i - w_i rho0, with

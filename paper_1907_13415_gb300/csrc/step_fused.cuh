@@ -22,9 +22,13 @@
 // tile box is a plain rectangle; the kernels that write them also write the
 // images.  Populations are read by pull with precomputed periodic offsets.
 //
-// Block = 11 warps: the 340 cells of the tile plus its one-cell ring get one
-// thread each in the ring phase, the 256 tile cells one thread each in the
-// cell phase.
+// Block = 11 warps.  Per plane, a ring phase gives each of the 340 cells of
+// the tile plus its one-cell ring one thread (whole rows per warp), and a
+// cell phase gives each of the 256 tile cells one thread; one barrier per
+// plane separates them, with enough plane slots in shared memory that the
+// ring phase of plane z+1 may overlap slower threads still in the cell phase
+// of plane z.  FP32 runs the collision on packed pairs of opposite
+// populations (packed.cuh).
 #pragma once
 #include "common.cuh"
 #include "lattice.cuh"
@@ -42,11 +46,9 @@ constexpr int FTX = 32;                  // tile width (x)
 constexpr int FTY = 8;                   // tile height (y)
 constexpr int RX1 = FTX + 2, RY1 = FTY + 2;  // tile + 1-cell ring
 constexpr int A1 = RX1 * RY1;            // 340 ring-region cells
-constexpr int FNT = 352;                 // 11 warps >= A1
 constexpr int BXW = FTX + 8;             // TMA box width: x0-4 .. x0+35
 constexpr int BYH = FTY + 4;             // TMA box height: y0-2 .. y0+9
 constexpr int BA = BXW * BYH;            // box plane area (480)
-static_assert(FNT >= A1 && FNT % 32 == 0, "ring phase needs one thread per cell");
 
 // box index of lattice offset (dx, dy) from the tile origin (x0, y0)
 __host__ __device__ constexpr int box_at(int dx, int dy) { return (dy + 2) * BXW + dx + 4; }
@@ -59,7 +61,7 @@ __host__ __device__ constexpr int box_at(int dx, int dy) { return (dy + 2) * BXW
 // threads take the left and right ring columns.
 static_assert(FTX == 32, "one warp per ring row");
 __device__ __forceinline__ void ring_cell(int t, int& cx, int& cy, int& ri) {
-  constexpr int NROW = FTX * (FTY + 2);
+  constexpr int NROW = FTX * RY1;
   if (t < NROW) {
     cx = t % FTX;
     cy = t / FTX - 1;
@@ -100,6 +102,12 @@ template <class Lat, class T>
 struct LbCfg {
   static constexpr int DIM = Lat::DIM;
   static constexpr int NPI = DIM * DIM;
+  // ring phase on threads [0, RING_T), cell phase on [CELL0, CELL0 + 256)
+  static constexpr int RING_T = A1;
+  static constexpr int CELL0 = 0;
+  static constexpr int THREADS = 352;  // 11 warps
+  static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;
+  static_assert(THREADS >= RING_T && THREADS >= CELL0 + FTX * FTY, "block too small");
   static constexpr int NSQ = DIM == 3 ? 4 : 1;  // Q plane slots
   // Pi plane slots: the ring phase of plane z+1 may start while slower
   // threads still read Pi(z-2..z) for plane z-1, so four slots let one
@@ -118,27 +126,28 @@ struct LbCfg {
 // neighbours first and removes 2d v with one fused multiply-add.
 template <class T, int DIM>
 __device__ __forceinline__ T lap_points(T v, T xp, T xm, T yp, T ym, T zp, T zm) {
-  if constexpr (std::is_same<T, float>::value) {
-    float s = (xp + xm) + (yp + ym);
-    if (DIM == 3) s += zp + zm;
-    return fmaf(-2.0f * DIM, v, s);
-  } else {
+  if constexpr (std::is_same<T, double>::value) {
     T l = (xp + xm - T(2) * v) + (yp + ym - T(2) * v);
     if (DIM == 3) l += zp + zm - T(2) * v;
     return l;
+  } else {
+    T s = (xp + xm) + (yp + ym);
+    if (DIM == 3) s += zp + zm;
+    return fma_(T(-2.0 * DIM), v, s);
   }
 }
 
 // stress on the ring-region cell of ring-phase thread t of a plane whose Q
-// box is in sq (z neighbours in sqm, sqp), into the Pi slot sp.  The first derivatives are
-// kept as plain differences (twice the central difference); the stress sees
-// them with K/4, which gives K dQ:dQ exactly (scalings by powers of two are
-// exact).
+// box is in sq (z neighbours in sqm, sqp), into the Pi slot sp.  The first
+// derivatives are kept as plain differences (twice the central difference);
+// the stress sees them with K/4, which gives K dQ:dQ exactly (scalings by
+// powers of two are exact).
 template <class T, int DIM>
 __device__ __forceinline__ void stress_ring_cell(int t, const T* __restrict__ sq,
                                                  const T* __restrict__ sqm,
                                                  const T* __restrict__ sqp,
-                                                 T* __restrict__ sp, const Par<T>& p) {
+                                                 T* __restrict__ sp,
+                                                 const Par<T>& p) {
   int cx, cy, c;
   ring_cell(t, cx, cy, c);
   const int o = box_at(cx, cy);
@@ -146,14 +155,15 @@ __device__ __forceinline__ void stress_ring_cell(int t, const T* __restrict__ sq
 #pragma unroll
   for (int k = 0; k < 5; k++) {
     const T* F = sq + k * BA;
-    const T v = F[o], xp = F[o + 1], xm = F[o - 1], yp = F[o + BXW], ym = F[o - BXW];
+    const T v = F[o], xp = F[o + 1], xm = F[o - 1];
+    const T yp = F[o + BXW], ym = F[o - BXW];
     q[k] = v;
     dq2[0][k] = xp - xm;
     dq2[1][k] = yp - ym;
     T zp = T(0), zm = T(0);
     if (DIM == 3) {
-      zp = sqp[k * BA + o];
-      zm = sqm[k * BA + o];
+      zp = (sqp + k * BA)[o];
+      zm = (sqm + k * BA)[o];
     }
     dq2[2][k] = zp - zm;
     lap[k] = lap_points<T, DIM>(v, xp, xm, yp, ym, zp, zm);
@@ -182,7 +192,7 @@ struct CellPops<Lat, float> {
 };
 
 template <class Lat, class T>
-__global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     k_fused_lb(const InstDev<T>* __restrict__ insts,
                const CUtensorMap* __restrict__ qmaps,
                const TileRef* __restrict__ tiles, int cur,
@@ -237,9 +247,10 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
   };
 
   // per-thread pull offsets (x, y fixed for the whole chunk)
-  const int tx = tid % FTX, ty = tid / FTX;
+  const int ct = tid - C::CELL0;
+  const int tx = ct % FTX, ty = ct / FTX;
   const int x = x0 + tx, y = y0 + ty;
-  const bool cell = tid < FTX * FTY && x < d.nx && y < d.ny;
+  const bool cell = ct >= 0 && ct < FTX * FTY && x < d.nx && y < d.ny;
   // source offsets within a plane for c_x, c_y in {-1, 0, 1} (index c + 1);
   // a lattice holds fewer than 2^31 cells, so 32-bit offsets suffice
   int colx[3] = {0, 0, 0};
@@ -336,7 +347,7 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     if (tid == 0) issue(0);
     pull_next(0);
     wait(0);
-    if (tid < A1) stress_ring_cell<T, DIM>(tid, sQ(0), sQ(0), sQ(0), sP(0), p);
+    if (tid < C::RING_T) stress_ring_cell<T, DIM>(tid, sQ(0), sQ(0), sQ(0), sP(0), p);
     if (__syncthreads_or(late)) {
       abort_block();
       return;
@@ -349,7 +360,7 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     wait(z0 - 2);
     wait(z0 - 1);
     wait(z0);
-    if (tid < A1)
+    if (tid < C::RING_T)
       stress_ring_cell<T, DIM>(tid, sQ(qslot(z0 - 1)), sQ(qslot(z0 - 2)), sQ(qslot(z0)),
                                sP(pslot(z0 - 1)), p);
     if (__syncthreads_or(late)) {
@@ -358,7 +369,7 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     }
     if (tid == 0) issue(z0 + 2);
     wait(z0 + 1);
-    if (tid < A1)
+    if (tid < C::RING_T)
       stress_ring_cell<T, DIM>(tid, sQ(qslot(z0)), sQ(qslot(z0 - 1)), sQ(qslot(z0 + 1)),
                                sP(pslot(z0)), p);
     for (int z = z0; z < z1; z++) {
@@ -366,7 +377,7 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
       // plane z, which every thread finished before the previous barrier
       if (tid == 0 && z + 3 <= z1 + 1) issue(z + 3);
       wait(z + 2);
-      if (tid < A1)
+      if (tid < C::RING_T)
         stress_ring_cell<T, DIM>(tid, sQ(qslot(z + 1)), sQ(qslot(z)), sQ(qslot(z + 2)),
                                  sP(pslot(z + 1)), p);
       if (__syncthreads_or(late)) {
@@ -390,6 +401,13 @@ struct BeCfg {
   // the predictor of z+1 and the copies of plane z+3 may overlap slower
   // threads still correcting plane z-1 (which reads Q^n(z-1), u(z-2..z) and
   // Q^P(z-2..z)).
+  // predictor on threads [0, RING_T), corrector on [CELL0, CELL0 + CELL_T)
+  static constexpr int RING_T = A1;
+  static constexpr int CELL_T = FTX * FTY;
+  static constexpr int CELL0 = 0;
+  static constexpr int THREADS = 352;  // 11 warps
+  static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;
+  static_assert(THREADS >= RING_T && THREADS >= CELL0 + CELL_T, "block too small");
   static constexpr int NSQ = DIM == 3 ? 5 : 1;   // Q^n plane slots
   static constexpr int NSU = DIM == 3 ? 6 : 1;   // u plane slots
   static constexpr int NSP = DIM == 3 ? 4 : 1;   // Q^P plane slots
@@ -404,21 +422,23 @@ struct BeCfg {
   static constexpr uint32_t u_tx = sizeof(T) * DIM * BA;
 };
 
-// u and G[a][b] = d_b u_a at box offset o (z neighbours from the planes
-// above and below)
+// u and G[a][b] = d_b u_a at box offset o (z neighbours from
+// the planes above and below)
 template <class T, int DIM>
 __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
                                           const T* __restrict__ m,
                                           const T* __restrict__ pp, int o,
                                           T u[3], T G[3][3]) {
+  const T half = T(0.5);
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     if (a < DIM) {
       const T* F = c + a * BA;
       u[a] = F[o];
-      G[a][0] = (F[o + 1] - F[o - 1]) / T(2);
-      G[a][1] = (F[o + BXW] - F[o - BXW]) / T(2);
-      G[a][2] = DIM == 3 ? (pp[a * BA + o] - m[a * BA + o]) / T(2) : T(0);
+      G[a][0] = (F[o + 1] - F[o - 1]) * half;
+      G[a][1] = (F[o + BXW] - F[o - BXW]) * half;
+      G[a][2] = DIM == 3 ? ((pp + a * BA)[o] - (m + a * BA)[o]) * half
+                         : T(0);
     } else {
       u[a] = T(0);
       G[a][0] = G[a][1] = G[a][2] = T(0);
@@ -426,8 +446,36 @@ __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
   }
 }
 
+// Q, the advection u.grad Q and the Laplacian at offset o
+// of a plane array c (row stride row, component stride comp; z neighbours in
+// m and pp).  The differences are kept plain (twice the central difference)
+// and meet u/2: (u/2).(2 dQ) = u.dQ exactly.
+template <class T, int DIM>
+__device__ __forceinline__ void stencil_adv(const T* __restrict__ c, const T* __restrict__ m,
+                                            const T* __restrict__ pp, int o, int row, int comp,
+                                            const T u[3], T q[5], T adv[5], T lap[5]) {
+  const T uh0 = u[0] * T(0.5), uh1 = u[1] * T(0.5), uh2 = u[2] * T(0.5);
+#pragma unroll
+  for (int k = 0; k < 5; k++) {
+    const T* F = c + k * comp;
+    const T v = F[o], xp = F[o + 1],
+            xm = F[o - 1];
+    const T yp = F[o + row], ym = F[o - row];
+    q[k] = v;
+    T a = fma_(uh0, xp - xm, uh1 * (yp - ym));
+    T zp = T(0), zm = T(0);
+    if (DIM == 3) {
+      zp = (pp + k * comp)[o];
+      zm = (m + k * comp)[o];
+      a = fma_(uh2, zp - zm, a);
+    }
+    adv[k] = a;
+    lap[k] = lap_points<T, DIM>(v, xp, xm, yp, ym, zp, zm);
+  }
+}
+
 template <class Lat, class T>
-__global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     k_fused_be(const InstDev<T>* __restrict__ insts,
                const CUtensorMap* __restrict__ qmaps,
                const CUtensorMap* __restrict__ umaps,
@@ -489,8 +537,8 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     }
   };
 
-  // predictor on the ring cell of ring-phase thread t of plane z: R(Q^n) and
-  // Q^P = Q^n + R
+  // predictor on the ring cell of ring-phase thread t of plane z: R(Q^n)
+  // and Q^P = Q^n + R
   auto predict = [&](int z, int t) {
     int cx, cy, c;
     ring_cell(t, cx, cy, c);
@@ -501,35 +549,20 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     const T* uc = sU(us(z));
     const T* um = DIM == 3 ? sU(us(z - 1)) : uc;
     const T* up = DIM == 3 ? sU(us(z + 1)) : uc;
-    T q[5], dq2[3][5], lap[5], u[3], G[3][3], r[5];
-#pragma unroll
-    for (int k = 0; k < 5; k++) {
-      const T* F = qc + k * BA;
-      const T v = F[o], xp = F[o + 1], xm = F[o - 1], yp = F[o + BXW], ym = F[o - BXW];
-      q[k] = v;
-      dq2[0][k] = xp - xm;
-      dq2[1][k] = yp - ym;
-      T zp = T(0), zm = T(0);
-      if (DIM == 3) {
-        zp = qp[k * BA + o];
-        zm = qm[k * BA + o];
-      }
-      dq2[2][k] = zp - zm;
-      lap[k] = lap_points<T, DIM>(v, xp, xm, yp, ym, zp, zm);
-    }
+    T q[5], adv[5], lap[5], u[3], G[3][3], r[5];
     box_ugrad<T, DIM>(uc, um, up, o, u, G);
-    // advection u.dQ from the plain differences: (u/2).(2 dQ), exact
-#pragma unroll
-    for (int a = 0; a < 3; a++) u[a] *= T(0.5);
-    be_rhs<T, DIM>(q, dq2, lap, u, G, p, r);
+    stencil_adv<T, DIM>(qc, qm, qp, o, BXW, BA, u, q, adv, lap);
+    be_rhs_adv<T>(q, adv, lap, G, p, r);
     T* qpo = sQP(ps(z));
 #pragma unroll
     for (int k = 0; k < 5; k++) qpo[k * A1 + c] = q[k] + r[k];
   };
 
-  const int tx = tid % FTX, ty = tid / FTX;
+  // corrector threads: one tile cell each
+  const int ct = tid - C::CELL0;
+  const int tx = ct % FTX, ty = ct / FTX;
   const int x = x0 + tx, y = y0 + ty;
-  const bool cell = tid < FTX * FTY && x < d.nx && y < d.ny;
+  const bool cell = ct >= 0 && ct < C::CELL_T && x < d.nx && y < d.ny;
   const int ic = (ty + 1) * RX1 + (tx + 1);
   const int o2 = box_at(tx, ty);
 
@@ -539,30 +572,15 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     const T* pc = sQP(ps(z));
     const T* pm = DIM == 3 ? sQP(ps(z - 1)) : pc;
     const T* pp = DIM == 3 ? sQP(ps(z + 1)) : pc;
-    T qp[5], dq2[3][5], lap[5], u[3], G[3][3], r2[5], out[5];
-#pragma unroll
-    for (int k = 0; k < 5; k++) {
-      const T* F = pc + k * A1;
-      const T v = F[ic], xp = F[ic + 1], xm = F[ic - 1], yp = F[ic + RX1], ym = F[ic - RX1];
-      qp[k] = v;
-      dq2[0][k] = xp - xm;
-      dq2[1][k] = yp - ym;
-      T zp = T(0), zm = T(0);
-      if (DIM == 3) {
-        zp = pp[k * A1 + ic];
-        zm = pm[k * A1 + ic];
-      }
-      dq2[2][k] = zp - zm;
-      lap[k] = lap_points<T, DIM>(v, xp, xm, yp, ym, zp, zm);
-    }
+    T qp[5], adv[5], lap[5], u[3], G[3][3], r2[5];
     box_ugrad<T, DIM>(sU(us(z)), DIM == 3 ? sU(us(z - 1)) : sU(us(z)),
-                      DIM == 3 ? sU(us(z + 1)) : sU(us(z)), o2, u, G);
-#pragma unroll
-    for (int a = 0; a < 3; a++) u[a] *= T(0.5);
-    be_rhs<T, DIM>(qp, dq2, lap, u, G, p, r2);
+                         DIM == 3 ? sU(us(z + 1)) : sU(us(z)), o2, u, G);
+    stencil_adv<T, DIM>(pc, pm, pp, ic, RX1, A1, u, qp, adv, lap);
+    be_rhs_adv<T>(qp, adv, lap, G, p, r2);
     // Q^{n+1} = Q^n + [R(Q^n) + R(Q^P)]/2 = [Q^n + Q^P + R(Q^P)]/2, since
     // Q^P = Q^n + R(Q^n)
     const T* qn = sQ(qs(z));
+    T out[5];
 #pragma unroll
     for (int k = 0; k < 5; k++) out[k] = (qn[k * BA + o2] + qp[k] + r2[k]) * T(0.5);
     store_with_images<T, 5, DIM>(Qout, d, x, y, z, out);
@@ -575,7 +593,7 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
     }
     wait_q(0);
     wait_u(0);
-    if (tid < A1) predict(0, tid);
+    if (tid < C::RING_T) predict(0, tid);
     if (__syncthreads_or(late)) {
       abort_block();
       return;
@@ -591,14 +609,14 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
       wait_q(z);
       wait_u(z);
     }
-    if (tid < A1) predict(z0 - 1, tid);
+    if (tid < C::RING_T) predict(z0 - 1, tid);
     if (__syncthreads_or(late)) {
       abort_block();
       return;
     }
     wait_q(z0 + 1);
     wait_u(z0 + 1);
-    if (tid < A1) predict(z0, tid);
+    if (tid < C::RING_T) predict(z0, tid);
     for (int z = z0; z < z1; z++) {
       if (tid == 0 && z + 3 <= z1 + 1) {
         issue_q(z + 3);
@@ -606,7 +624,7 @@ __global__ void __launch_bounds__(FNT, sizeof(T) == 4 ? 2 : 1)
       }
       wait_q(z + 2);
       wait_u(z + 2);
-      if (tid < A1) predict(z + 1, tid);
+      if (tid < C::RING_T) predict(z + 1, tid);
       if (__syncthreads_or(late)) {
         abort_block();
         return;
@@ -660,7 +678,7 @@ cudaError_t launch_fused_lb(const InstDev<T>* insts, const CUtensorMap* qmaps,
   static unsigned long long configured = 0;
   cudaError_t e = set_smem(k_fused_lb<Lat, T>, LbCfg<Lat, T>::bytes, &configured);
   if (e != cudaSuccess) return e;
-  k_fused_lb<Lat, T><<<ntiles, FNT, LbCfg<Lat, T>::bytes, st>>>(insts, qmaps, tiles, cur, err);
+  k_fused_lb<Lat, T><<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(insts, qmaps, tiles, cur, err);
   return cudaGetLastError();
 }
 
@@ -671,7 +689,7 @@ cudaError_t launch_fused_be(const InstDev<T>* insts, const CUtensorMap* qmaps,
   static unsigned long long configured = 0;
   cudaError_t e = set_smem(k_fused_be<Lat, T>, BeCfg<Lat, T>::bytes, &configured);
   if (e != cudaSuccess) return e;
-  k_fused_be<Lat, T><<<ntiles, FNT, BeCfg<Lat, T>::bytes, st>>>(insts, qmaps, umaps, tiles,
+  k_fused_be<Lat, T><<<ntiles, BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::bytes, st>>>(insts, qmaps, umaps, tiles,
                                                                  cur, err);
   return cudaGetLastError();
 }

@@ -1,6 +1,16 @@
 // Host build of the library's pointwise physics (csrc/physics.cuh) for CPU
 // tests against the oracle.  Test infrastructure only: exposes plain C
 // wrappers around the same templates the CUDA kernels instantiate.
+#include <complex>
+
+namespace nlc {
+// complex-step twin of the fused multiply-add the physics templates use
+inline std::complex<double> fma_(std::complex<double> a, std::complex<double> b,
+                                 std::complex<double> c) {
+  return a * b + c;
+}
+}  // namespace nlc
+
 #include "../paper_1907_13415_gb300/csrc/lattice.cuh"
 #include "../paper_1907_13415_gb300/csrc/physics.cuh"
 
