@@ -80,16 +80,13 @@ __device__ __forceinline__ void rhs_stencil_gather(const Field<T>& U, const T* _
 //    lQP = J^T rbar (pointwise at Q^P plus stencil gathers); the adjoints of
 //    u (advection) and of G = grad u are stored for the lb adjoint.
 template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_adj_be2(Field<T> QP, Field<T> U,
-                                                 const T* __restrict__ lQn,
-                                                 T* __restrict__ lQP, T* __restrict__ lUa,
-                                                 T* __restrict__ lGv, Dims d, Par<T> p,
-                                                 double* __restrict__ acc) {
+__device__ __forceinline__ void adj_be2_at(const Field<T>& QP, const Field<T>& U,
+                                           const T* __restrict__ lQn, T* __restrict__ lQP,
+                                           T* __restrict__ lUa, T* __restrict__ lGv,
+                                           const Dims& d, const Par<T>& p, ParBar<T>& pb,
+                                           int64_t idx, int x, int y, int z) {
   constexpr int DIM = Lat::DIM;
-  int x, y, z;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  ParBar<T> pb{T(0), T(0), T(0)};
-  if (decode(d, idx, x, y, z)) {
+  {
     T q[5], dq[3][5], lap[5], u[3], G[3][3], rb[5];
     q_stencil<T, DIM>(QP, x, y, z, q, dq, lap);
     u_stencil<T, DIM>(U, x, y, z, u, G);
@@ -107,6 +104,19 @@ __global__ void __launch_bounds__(256) k_adj_be2(Field<T> QP, Field<T> U,
       for (int b = 0; b < DIM; b++) lGv[(a * DIM + b) * d.n + idx] = Gb[a][b];
     }
   }
+}
+
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_adj_be2(Field<T> QP, Field<T> U,
+                                                 const T* __restrict__ lQn,
+                                                 T* __restrict__ lQP, T* __restrict__ lUa,
+                                                 T* __restrict__ lGv, Dims d, Par<T> p,
+                                                 double* __restrict__ acc) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  ParBar<T> pb{T(0), T(0), T(0)};
+  if (decode(d, idx, x, y, z))
+    adj_be2_at<Lat, T>(QP, U, lQn, lQP, lUa, lGv, d, p, pb, idx, x, y, z);
   add_param_bar(pb, acc);
 }
 
@@ -114,17 +124,14 @@ __global__ void __launch_bounds__(256) k_adj_be2(Field<T> QP, Field<T> U,
 //    rbar = lQn / 2 + lQP (R1 enters Q^{n+1} with 1/2 and Q^P with 1), and
 //    of Q^{n+1} = Q^n + ..., Q^P = Q^n + R1:  lQ = lQn + lQP + J^T rbar.
 template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_adj_be1(Field<T> Q, Field<T> U,
-                                                 const T* __restrict__ lQn,
-                                                 const T* __restrict__ lQP,
-                                                 T* __restrict__ lQ, T* __restrict__ lUa,
-                                                 T* __restrict__ lGv, Dims d, Par<T> p,
-                                                 double* __restrict__ acc) {
+__device__ __forceinline__ void adj_be1_at(const Field<T>& Q, const Field<T>& U,
+                                           const T* __restrict__ lQn,
+                                           const T* __restrict__ lQP, T* __restrict__ lQ,
+                                           T* __restrict__ lUa, T* __restrict__ lGv,
+                                           const Dims& d, const Par<T>& p, ParBar<T>& pb,
+                                           int64_t idx, int x, int y, int z) {
   constexpr int DIM = Lat::DIM;
-  int x, y, z;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  ParBar<T> pb{T(0), T(0), T(0)};
-  if (decode(d, idx, x, y, z)) {
+  {
     T q[5], dq[3][5], lap[5], u[3], G[3][3], rb[5];
     q_stencil<T, DIM>(Q, x, y, z, q, dq, lap);
     u_stencil<T, DIM>(U, x, y, z, u, G);
@@ -143,6 +150,20 @@ __global__ void __launch_bounds__(256) k_adj_be1(Field<T> Q, Field<T> U,
       for (int b = 0; b < DIM; b++) lGv[(a * DIM + b) * d.n + idx] += Gb[a][b];
     }
   }
+}
+
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_adj_be1(Field<T> Q, Field<T> U,
+                                                 const T* __restrict__ lQn,
+                                                 const T* __restrict__ lQP,
+                                                 T* __restrict__ lQ, T* __restrict__ lUa,
+                                                 T* __restrict__ lGv, Dims d, Par<T> p,
+                                                 double* __restrict__ acc) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  ParBar<T> pb{T(0), T(0), T(0)};
+  if (decode(d, idx, x, y, z))
+    adj_be1_at<Lat, T>(Q, U, lQn, lQP, lQ, lUa, lGv, d, p, pb, idx, x, y, z);
   add_param_bar(pb, acc);
 }
 
@@ -152,17 +173,13 @@ __global__ void __launch_bounds__(256) k_adj_be1(Field<T> Q, Field<T> U,
 //    Writes the force adjoint lF for the stress adjoint.
 //    lGn == nullptr: seed mode (no collision; only u of the final state).
 template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_adj_lb(const T* __restrict__ gin,
-                                                const T* __restrict__ Pi,
-                                                const T* __restrict__ lGn,
-                                                const T* __restrict__ lUa,
-                                                const T* __restrict__ lGv,
-                                                T* __restrict__ lG, T* __restrict__ lF,
-                                                Dims d, Par<T> p, T seed_u) {
+__device__ __forceinline__ void adj_lb_at(const T* __restrict__ gin, const T* __restrict__ Pi,
+                                          const T* __restrict__ lGn,
+                                          const T* __restrict__ lUa,
+                                          const T* __restrict__ lGv, T* __restrict__ lG,
+                                          T* __restrict__ lF, const Dims& d, const Par<T>& p,
+                                          T seed_u, int64_t idx, int x, int y, int z) {
   constexpr int DIM = Lat::DIM;
-  int x, y, z;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (!decode(d, idx, x, y, z)) return;
   T F[3], g[Lat::Q], rho, u[3];
   force_at<T, DIM>(Pi, d, x, y, z, F);
   pull<Lat, T>(gin, d, x, y, z, g);
@@ -201,19 +218,31 @@ __global__ void __launch_bounds__(256) k_adj_lb(const T* __restrict__ gin,
   for (int a = 0; a < DIM; a++) lF[a * d.n + idx] = Fb[a];
 }
 
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_adj_lb(const T* __restrict__ gin,
+                                                const T* __restrict__ Pi,
+                                                const T* __restrict__ lGn,
+                                                const T* __restrict__ lUa,
+                                                const T* __restrict__ lGv,
+                                                T* __restrict__ lG, T* __restrict__ lF,
+                                                Dims d, Par<T> p, T seed_u) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (decode(d, idx, x, y, z))
+    adj_lb_at<Lat, T>(gin, Pi, lGn, lUa, lGv, lG, lF, d, p, seed_u, idx, x, y, z);
+}
+
 // 4. adjoint of the stress at cell y: Pibar from the divergence transpose of
 //    lF, then stress and molecular-field adjoints; adds the pointwise Q
 //    adjoint to lQ and stores the derivative/Laplacian adjoints for step 5.
 template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_adj_stress(Field<T> Q, const T* __restrict__ lF,
-                                                    T* __restrict__ lQ, T* __restrict__ lDq,
-                                                    T* __restrict__ lLap, Dims d, Par<T> p,
-                                                    double* __restrict__ acc) {
+__device__ __forceinline__ void adj_stress_at(const Field<T>& Q, const T* __restrict__ lF,
+                                              T* __restrict__ lQ, T* __restrict__ lDq,
+                                              T* __restrict__ lLap, const Dims& d,
+                                              const Par<T>& p, ParBar<T>& pb, int64_t idx,
+                                              int x, int y, int z) {
   constexpr int DIM = Lat::DIM;
-  int x, y, z;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  ParBar<T> pb{T(0), T(0), T(0)};
-  if (decode(d, idx, x, y, z)) {
+  {
     T Pib[3][3] = {};
 #pragma unroll
     for (int a = 0; a < DIM; a++)
@@ -235,19 +264,29 @@ __global__ void __launch_bounds__(256) k_adj_stress(Field<T> Q, const T* __restr
       for (int g = 0; g < DIM; g++) lDq[(g * 5 + k) * d.n + idx] = dqb[g][k];
     }
   }
+}
+
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_adj_stress(Field<T> Q, const T* __restrict__ lF,
+                                                    T* __restrict__ lQ, T* __restrict__ lDq,
+                                                    T* __restrict__ lLap, Dims d, Par<T> p,
+                                                    double* __restrict__ acc) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  ParBar<T> pb{T(0), T(0), T(0)};
+  if (decode(d, idx, x, y, z))
+    adj_stress_at<Lat, T>(Q, lF, lQ, lDq, lLap, d, p, pb, idx, x, y, z);
   add_param_bar(pb, acc);
 }
 
 // 5. stencil transposes of the stress adjoint: lQ += div-transpose(lDq) +
 //    Laplacian-transpose(lLap)
 template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_adj_stencil(const T* __restrict__ lDq,
-                                                     const T* __restrict__ lLap,
-                                                     T* __restrict__ lQ, Dims d) {
+__device__ __forceinline__ void adj_stencil_at(const T* __restrict__ lDq,
+                                               const T* __restrict__ lLap, T* __restrict__ lQ,
+                                               const Dims& d, int64_t idx, int x, int y,
+                                               int z) {
   constexpr int DIM = Lat::DIM;
-  int x, y, z;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (!decode(d, idx, x, y, z)) return;
 #pragma unroll
   for (int k = 0; k < 5; k++) {
     T s = -T(2) * DIM * lLap[k * d.n + idx];
@@ -259,6 +298,15 @@ __global__ void __launch_bounds__(256) k_adj_stencil(const T* __restrict__ lDq,
     }
     lQ[k * d.n + idx] += s;
   }
+}
+
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_adj_stencil(const T* __restrict__ lDq,
+                                                     const T* __restrict__ lLap,
+                                                     T* __restrict__ lQ, Dims d) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (decode(d, idx, x, y, z)) adj_stencil_at<Lat, T>(lDq, lLap, lQ, d, idx, x, y, z);
 }
 
 // loss seed on Q: lQ = c_R dS/dq with S = sqrt(3/2 Tr Q^2) (0 where S = 0)

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "adjoint.cuh"
+#include "adjoint_segment.cuh"
 #include "aux_kernels.cuh"
 #include "engine.h"
 #include "step_fused.cuh"
@@ -64,6 +65,12 @@ struct InstHost {
   int64_t ck_count = 0;
   T* ring = nullptr;      // states of one segment, (Q + 5) n each
   int64_t ring_count = 0;
+  // segment records of the persistent adjoint kernels (adjoint_segment.cuh)
+  T *rec_g = nullptr, *rec_q = nullptr, *rec_pi = nullptr, *rec_u = nullptr,
+    *rec_qp = nullptr;
+  int64_t rec_len = 0;
+  GridBarrier* bar = nullptr;
+  int seg_grid = 0;  // blocks of the cooperative launches (0: not available)
 };
 
 template <class Lat, class T>
@@ -340,7 +347,9 @@ class Engine final : public EngineBase {
     const int64_t S = (int64_t)(Q + 5) * n;  // one state
     cudaStream_t st = args_.stream;
     nlc_status s;
-    if ((s = ensure_staging(I)) || (s = ensure_adjoint(I, nseg + 1, ckpt_every))) return s;
+    if ((s = ensure_staging(I)) || (s = ensure_segment(I, ckpt_every)) ||
+        (s = ensure_adjoint(I, nseg + 1, I.seg_grid > 0 ? 0 : ckpt_every)))
+      return s;
     if (!maps_ok_) {
       err = "TMA tensor maps unavailable; the adjoint needs the fused step";
       return NLC_EUNSUPPORTED;
@@ -366,7 +375,7 @@ class Engine final : public EngineBase {
     out->u_l2 = obs.u_l2;
     out->loss = loss->w_radius * (R - loss->target_radius) * (R - loss->target_radius) +
                 loss->w_velocity * obs.u_l2;
-    NLC_CK(cudaMemsetAsync(I.acc, 0, sizeof(double) * 3 * 3 * grid1(n), st));
+    NLC_CK(cudaMemsetAsync(I.acc, 0, sizeof(double) * 3 * (3 * grid1(n) + I.seg_grid), st));
     int lc = 0;  // lQ[lc], lG[lc] hold the adjoint of the current state
     {
       const unsigned gb = grid1(n);
@@ -379,9 +388,16 @@ class Engine final : public EngineBase {
       k_adj_stencil<Lat, T><<<gb, 256, 0, st>>>(I.lDq, I.lLap, I.lQ[lc], I.d);
       NLC_CK_LAUNCH("adjoint seed");
     }
-    // backward sweep, segment by segment
+    // backward sweep, segment by segment: two persistent kernels per segment
+    // (record, reverse) where cooperative launches are available, else the
+    // recomputation into the state ring and one reverse step at a time
     for (int64_t k = nseg - 1; k >= 0; k--) {
       const int64_t len = std::min<int64_t>(ckpt_every, nsteps - k * ckpt_every);
+      if (I.seg_grid > 0) {
+        if ((s = segment_adjoint(I, I.ck + k * S, (int)len, lc))) return s;
+        if (len & 1) lc ^= 1;
+        continue;
+      }
       if ((s = state_in(I, I.ck + k * S))) return s;
       for (int64_t j = 0; j < len; j++) {
         if ((s = state_out(I, I.ring + j * S))) return s;
@@ -393,9 +409,9 @@ class Engine final : public EngineBase {
         lc ^= 1;
       }
     }
-    // gradients
+    // gradients: every block slot of every kernel, summed in a fixed order
     const unsigned gb = grid1(n);
-    std::vector<double> acc((size_t)3 * 3 * gb);
+    std::vector<double> acc((size_t)3 * (3 * gb + I.seg_grid));
     NLC_CK(cudaMemcpyAsync(acc.data(), I.acc, sizeof(double) * acc.size(),
                            cudaMemcpyDeviceToHost, st));
     if (dQ0) {
@@ -408,9 +424,7 @@ class Engine final : public EngineBase {
     NLC_CK(cudaStreamSynchronize(st));
     if ((s = device_error())) return s;
     double g3[3] = {0, 0, 0};
-    for (int kern = 0; kern < 3; kern++)
-      for (unsigned b = 0; b < gb; b++)
-        for (int c = 0; c < 3; c++) g3[c] += acc[((size_t)kern * gb + b) * 3 + c];
+    for (size_t i = 0; i < acc.size(); i++) g3[i % 3] += acc[i];
     out->dgamma = g3[0];
     out->dK = g3[1];
     out->dGamma = g3[2];
@@ -494,8 +508,10 @@ class Engine final : public EngineBase {
     unsigned e = 0;
     NLC_CK(cudaMemcpy(&e, derr_, sizeof(e), cudaMemcpyDeviceToHost));
     if (e != DEV_ERR_NONE) {
-      err = "a bounded wait on a tile copy ran out inside a step kernel (code " +
-            std::to_string(e) + ")";
+      err = e == DEV_ERR_GRID_TIMEOUT
+                ? "a bounded grid-barrier wait ran out inside an adjoint segment kernel"
+                : "a bounded wait on a tile copy ran out inside a step kernel (code " +
+                      std::to_string(e) + ")";
       return NLC_ETIMEOUT;
     }
     return NLC_OK;
@@ -543,7 +559,7 @@ class Engine final : public EngineBase {
           (s = alloc(&I.lQP, (size_t)5 * n)) || (s = alloc(&I.lUa, (size_t)DIM * n)) ||
           (s = alloc(&I.lGv, (size_t)DIM * DIM * n)) || (s = alloc(&I.lF, (size_t)DIM * n)) ||
           (s = alloc(&I.lDq, (size_t)DIM * 5 * n)) || (s = alloc(&I.lLap, (size_t)5 * n)) ||
-          (s = alloc(&I.acc, (size_t)3 * 3 * grid1(n))))
+          (s = alloc(&I.acc, (size_t)3 * (3 * grid1(n) + seg_grid_max()))))
         return s;
     }
     if (I.ck_count < ck_count) {
@@ -554,6 +570,91 @@ class Engine final : public EngineBase {
       if ((s = alloc(&I.ring, (size_t)(ring_count * S)))) return s;
       I.ring_count = ring_count;
     }
+    return NLC_OK;
+  }
+
+  // blocks of a cooperative launch of the segment kernels: every block must
+  // be resident, so at most the SM count times the blocks per SM that fit
+  int seg_grid_max() {
+    int dev = 0, sms = 0, nb1 = 0, nb2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_seg_record<Lat, T>, SEG_THREADS,
+                                                      0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_seg_reverse<Lat, T>,
+                                                      SEG_THREADS, 0) != cudaSuccess)
+      return 0;
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+      return 0;
+    return sms * std::min(nb1, nb2);
+  }
+
+  // record slots for segments of up to len steps
+  nlc_status ensure_segment(InstHost<T>& I, int64_t len) {
+    nlc_status s;
+    if (!I.bar) {
+      if ((s = ensure_unfused(I))) return s;  // r1 scratch
+      if ((s = alloc(&I.bar, 1))) return s;
+      const int64_t want = (I.d.n + SEG_THREADS - 1) / SEG_THREADS;
+      I.seg_grid = (int)std::min<int64_t>(seg_grid_max(), want);
+    }
+    if (I.seg_grid <= 0 || I.rec_len >= len) return NLC_OK;
+    const int64_t n = I.d.n, comp = I.L.comp;
+    if ((s = alloc(&I.rec_g, (size_t)((len + 1) * Q * n))) ||
+        (s = alloc(&I.rec_q, (size_t)((len + 1) * 5 * comp))) ||
+        (s = alloc(&I.rec_pi, (size_t)(len * DIM * DIM * n))) ||
+        (s = alloc(&I.rec_u, (size_t)(len * DIM * comp))) ||
+        (s = alloc(&I.rec_qp, (size_t)(len * 5 * comp))))
+      return s;
+    I.rec_len = len;
+    return NLC_OK;
+  }
+
+  // one segment of len steps from the checkpoint at ck: record, then reverse;
+  // the adjoint of the segment's end state is in (lQ[lc], lG[lc])
+  nlc_status segment_adjoint(InstHost<T>& I, const T* ck, int len, int lc) {
+    const int64_t n = I.d.n;
+    cudaStream_t st = args_.stream;
+    const int e0 = mark();
+    NLC_CK(cudaMemcpyAsync(I.rec_g, ck, sizeof(T) * Q * n, cudaMemcpyDeviceToDevice, st));
+    k_field_raw_in<T, DIM><<<grid1(n), 256, 0, st>>>(ck + (int64_t)Q * n, I.d,
+                                                       Field<T>{I.rec_q, I.L});
+    NLC_CK_LAUNCH("k_field_raw_in");
+    SegArgs<T> a;
+    a.d = I.d;
+    a.p = I.p;
+    a.L = I.L;
+    a.len = len;
+    a.lc0 = lc;
+    a.g = I.rec_g;
+    a.q = I.rec_q;
+    a.pi = I.rec_pi;
+    a.u = I.rec_u;
+    a.qp = I.rec_qp;
+    a.r1 = I.r1;
+    a.lQ[0] = I.lQ[0];
+    a.lQ[1] = I.lQ[1];
+    a.lG[0] = I.lG[0];
+    a.lG[1] = I.lG[1];
+    a.lQP = I.lQP;
+    a.lUa = I.lUa;
+    a.lGv = I.lGv;
+    a.lF = I.lF;
+    a.lDq = I.lDq;
+    a.lLap = I.lLap;
+    a.acc = I.acc + (size_t)3 * 3 * grid1(n);
+    a.bar = I.bar;
+    a.err = derr_;
+    void* args[] = {&a};
+    NLC_CK(cudaMemsetAsync(I.bar, 0, sizeof(GridBarrier), st));
+    NLC_CK(cudaLaunchCooperativeKernel((const void*)k_seg_record<Lat, T>, dim3(I.seg_grid),
+                                       dim3(SEG_THREADS), args, 0, st));
+    NLC_CK(cudaMemsetAsync(I.bar, 0, sizeof(GridBarrier), st));
+    NLC_CK(cudaLaunchCooperativeKernel((const void*)k_seg_reverse<Lat, T>, dim3(I.seg_grid),
+                                       dim3(SEG_THREADS), args, 0, st));
+    const int e1 = mark();
+    if (timer.on) timer.span(KID_ADJOINT, e0, e1);
     return NLC_OK;
   }
 

@@ -74,13 +74,13 @@ __device__ __forceinline__ bool decode(const Dims& d, int64_t idx, int& x,
   return true;
 }
 
+// The four stages at one cell (x, y, z) = decode(idx); the kernels below run
+// one cell per thread, the adjoint's segment kernels (adjoint_segment.cuh)
+// loop over cells with the same functions.
 template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_stress(Field<T> Q, T* __restrict__ Pi,
-                                                Dims d, Par<T> p) {
+__device__ __forceinline__ void stress_at(const Field<T>& Q, T* __restrict__ Pi, const Dims& d,
+                                          const Par<T>& p, int64_t idx, int x, int y, int z) {
   constexpr int DIM = Lat::DIM;
-  int x, y, z;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (!decode(d, idx, x, y, z)) return;
   T q[5], dq[3][5], lap[5], h[5], P[3][3];
   q_stencil<T, DIM>(Q, x, y, z, q, dq, lap);
   molecular_field(q, lap, p, h);
@@ -89,6 +89,14 @@ __global__ void __launch_bounds__(256) k_stress(Field<T> Q, T* __restrict__ Pi,
   for (int a = 0; a < DIM; a++)
 #pragma unroll
     for (int b = 0; b < DIM; b++) Pi[(a * DIM + b) * d.n + idx] = P[a][b];
+}
+
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_stress(Field<T> Q, T* __restrict__ Pi,
+                                                Dims d, Par<T> p) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (decode(d, idx, x, y, z)) stress_at<Lat, T>(Q, Pi, d, p, idx, x, y, z);
 }
 
 // F_a = sum_b [Pi_ab(x + e_b) - Pi_ab(x - e_b)] / 2  (Pi unpadded: wrap)
@@ -128,13 +136,10 @@ __device__ __forceinline__ void pull(const T* __restrict__ gin, const Dims& d,
 }
 
 template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_lb(const T* __restrict__ gin,
-                                            T* __restrict__ gout,
-                                            const T* __restrict__ Pi,
-                                            Field<T> U, Dims d, Par<T> p) {
-  int x, y, z;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (!decode(d, idx, x, y, z)) return;
+__device__ __forceinline__ void lb_at(const T* __restrict__ gin, T* __restrict__ gout,
+                                      const T* __restrict__ Pi, const Field<T>& U,
+                                      const Dims& d, const Par<T>& p, int64_t idx, int x,
+                                      int y, int z) {
   T F[3], g[Lat::Q], rho, u[3];
   force_at<T, Lat::DIM>(Pi, d, x, y, z, F);
   pull<Lat, T>(gin, d, x, y, z, g);
@@ -146,14 +151,21 @@ __global__ void __launch_bounds__(256) k_lb(const T* __restrict__ gin,
 }
 
 template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_predict(Field<T> Q, Field<T> U,
-                                                 Field<T> QP,
-                                                 T* __restrict__ R1, Dims d,
-                                                 Par<T> p) {
-  constexpr int DIM = Lat::DIM;
+__global__ void __launch_bounds__(256) k_lb(const T* __restrict__ gin,
+                                            T* __restrict__ gout,
+                                            const T* __restrict__ Pi,
+                                            Field<T> U, Dims d, Par<T> p) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (!decode(d, idx, x, y, z)) return;
+  if (decode(d, idx, x, y, z)) lb_at<Lat, T>(gin, gout, Pi, U, d, p, idx, x, y, z);
+}
+
+template <class Lat, class T>
+__device__ __forceinline__ void predict_at(const Field<T>& Q, const Field<T>& U,
+                                           const Field<T>& QP, T* __restrict__ R1,
+                                           const Dims& d, const Par<T>& p, int64_t idx,
+                                           int x, int y, int z) {
+  constexpr int DIM = Lat::DIM;
   T q[5], dq[3][5], lap[5], u[3], G[3][3], r[5], qp[5];
   q_stencil<T, DIM>(Q, x, y, z, q, dq, lap);
   u_stencil<T, DIM>(U, x, y, z, u, G);
@@ -167,14 +179,22 @@ __global__ void __launch_bounds__(256) k_predict(Field<T> Q, Field<T> U,
 }
 
 template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_correct(Field<T> Q, Field<T> QP,
-                                                 const T* __restrict__ R1,
-                                                 Field<T> U, Field<T> Qout,
-                                                 Dims d, Par<T> p) {
-  constexpr int DIM = Lat::DIM;
+__global__ void __launch_bounds__(256) k_predict(Field<T> Q, Field<T> U,
+                                                 Field<T> QP,
+                                                 T* __restrict__ R1, Dims d,
+                                                 Par<T> p) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (!decode(d, idx, x, y, z)) return;
+  if (decode(d, idx, x, y, z)) predict_at<Lat, T>(Q, U, QP, R1, d, p, idx, x, y, z);
+}
+
+template <class Lat, class T>
+__device__ __forceinline__ void correct_at(const Field<T>& Q, const Field<T>& QP,
+                                           const T* __restrict__ R1, const Field<T>& U,
+                                           const Field<T>& Qout, const Dims& d,
+                                           const Par<T>& p, int64_t idx, int x, int y,
+                                           int z) {
+  constexpr int DIM = Lat::DIM;
   T qp[5], dq[3][5], lap[5], u[3], G[3][3], r2[5], out[5];
   q_stencil<T, DIM>(QP, x, y, z, qp, dq, lap);
   u_stencil<T, DIM>(U, x, y, z, u, G);
@@ -183,6 +203,16 @@ __global__ void __launch_bounds__(256) k_correct(Field<T> Q, Field<T> QP,
   for (int k = 0; k < 5; k++)
     out[k] = Q.at(k, x, y, z) + (R1[k * d.n + idx] + r2[k]) / T(2);
   store_with_images<T, 5, DIM>(Qout, d, x, y, z, out);
+}
+
+template <class Lat, class T>
+__global__ void __launch_bounds__(256) k_correct(Field<T> Q, Field<T> QP,
+                                                 const T* __restrict__ R1,
+                                                 Field<T> U, Field<T> Qout,
+                                                 Dims d, Par<T> p) {
+  int x, y, z;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (decode(d, idx, x, y, z)) correct_at<Lat, T>(Q, QP, R1, U, Qout, d, p, idx, x, y, z);
 }
 
 }  // namespace nlc

@@ -16,7 +16,7 @@ namespace nlc {
 constexpr uint64_t kWaitNs = 200ull * 1000 * 1000;
 
 // error codes written to the device error word
-enum : unsigned { DEV_ERR_NONE = 0, DEV_ERR_TMA_TIMEOUT = 1 };
+enum : unsigned { DEV_ERR_NONE = 0, DEV_ERR_TMA_TIMEOUT = 1, DEV_ERR_GRID_TIMEOUT = 2 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
