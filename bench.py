@@ -470,11 +470,14 @@ def run_adjoint(args):
                          stream=stream.cuda_stream)
     Q0 = w.initial_q5()
 
-    def fwd():
+    def fwd(graph_steps=0):
+        sim.set_graph(graph_steps)
         sim.set_fields(Q0)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim.step(steps)
         torch.cuda.synchronize()
+        sim.set_graph(0)
         return time.perf_counter() - t0
 
     def adj():
@@ -484,8 +487,10 @@ def run_adjoint(args):
         return time.perf_counter() - t0, g
 
     fwd()
+    fwd(ckpt)
     adj()
     tf = min(fwd() for _ in range(3))
+    tfg = min(fwd(ckpt) for _ in range(3))
     runs = [adj() for _ in range(3)]
     ta = min(r[0] for r in runs)
     g = runs[0][1]
@@ -494,6 +499,7 @@ def run_adjoint(args):
            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
            "config": {"workload": w.name, "steps": steps, "ckpt_every": ckpt},
            "forward_s": tf, "adjoint_s": ta,
+           "forward_graph_s": tfg, "ratio_vs_graph_forward": ta / tfg,
            "gradient": {k: g[k] for k in ("loss", "radius", "dgamma", "dK", "dGamma")}}
     print(json.dumps(out), flush=True)
     return 0

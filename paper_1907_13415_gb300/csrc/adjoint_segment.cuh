@@ -26,39 +26,41 @@
 
 namespace nlc {
 
-// cumulative arrival counter and published generation; zeroed before each
-// launch
+// cumulative arrival counter, zeroed before each launch
 struct GridBarrier {
   unsigned arrived;
-  unsigned gen;
 };
 
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier of a cooperative launch.  Thread 0 of each block adds
-// its arrival; the arrival that completes generation g publishes g + 1, the
-// other blocks wait for it (bounded).  Returns false in every thread of the
-// block if the wait ran out.
+// its arrival with release semantics and polls the counter with acquire
+// semantics until every block of this generation has arrived (the counter
+// is cumulative: generation g completes at (g + 1) gridDim.x).  The poll is
+// bounded; returns false in every thread of the block if it ran out.
 __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen, unsigned* err) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
-    const unsigned next = gen + 1;
-    __threadfence();
-    const unsigned a = atomicAdd(&b->arrived, 1u) + 1u;
-    if (a == next * gridDim.x) {
-      atomicExch(&b->gen, next);
-    } else {
-      volatile unsigned* pg = &b->gen;
+    const unsigned target = (gen + 1) * gridDim.x;
+    red_release_gpu_add(&b->arrived, 1u);
+    if (ld_acquire_gpu(&b->arrived) < target) {
       const uint64_t t0 = global_ns();
-      while (*pg < next) {
+      while (ld_acquire_gpu(&b->arrived) < target) {
         if (global_ns() - t0 > kWaitNs) {
           ok = 0;
           atomicExch(err, DEV_ERR_GRID_TIMEOUT);
           break;
         }
-        __nanosleep(32);
       }
     }
-    __threadfence();
   }
   gen++;
   return __syncthreads_and(ok) != 0;

@@ -65,12 +65,13 @@ struct InstHost {
   int64_t ck_count = 0;
   T* ring = nullptr;      // states of one segment, (Q + 5) n each
   int64_t ring_count = 0;
-  // segment records of the persistent adjoint kernels (adjoint_segment.cuh)
-  T *rec_g = nullptr, *rec_q = nullptr, *rec_pi = nullptr, *rec_u = nullptr,
-    *rec_qp = nullptr;
+  // segment records of the persistent adjoint kernels (adjoint_segment.cuh),
+  // two sets: the record of segment k-1 is written while segment k reverses
+  T *rec_g[2] = {}, *rec_q[2] = {}, *rec_pi[2] = {}, *rec_u[2] = {}, *rec_qp[2] = {},
+    *rec_r1[2] = {};
   int64_t rec_len = 0;
-  GridBarrier* bar = nullptr;
-  int seg_grid = 0;  // blocks of the cooperative launches (0: not available)
+  GridBarrier* bar = nullptr;  // [0], [1]: record kernels; [2]: reverse kernel
+  int seg_grid = 0;            // blocks of the cooperative launches (0: not available)
 };
 
 template <class Lat, class T>
@@ -85,6 +86,10 @@ class Engine final : public EngineBase {
     for (int c = 0; c < 2; c++)
       if (graph_[c]) cudaGraphExecDestroy(graph_[c]);
     if (cap_stream_) cudaStreamDestroy(cap_stream_);
+    for (const SweepGraph& e : sweep_graphs_) cudaGraphExecDestroy(e.exec);
+    if (side_stream_) cudaStreamDestroy(side_stream_);
+    for (cudaEvent_t e : seg_ev_)
+      if (e) cudaEventDestroy(e);
     for (void* ptr : allocs_) cudaFree(ptr);
   }
 
@@ -358,8 +363,7 @@ class Engine final : public EngineBase {
     for (int64_t k = 0; k < nseg; k++) {
       if ((s = state_out(I, I.ck + k * S))) return s;
       const int64_t len = std::min<int64_t>(ckpt_every, nsteps - k * ckpt_every);
-      for (int64_t j = 0; j < len; j++)
-        if ((s = step_fused(st))) return s;
+      if ((s = fused_steps(len))) return s;
     }
     if ((s = state_out(I, I.ck + nseg * S))) return s;  // final state
     // loss and its seed on the final state
@@ -391,13 +395,9 @@ class Engine final : public EngineBase {
     // backward sweep, segment by segment: two persistent kernels per segment
     // (record, reverse) where cooperative launches are available, else the
     // recomputation into the state ring and one reverse step at a time
-    for (int64_t k = nseg - 1; k >= 0; k--) {
+    if (I.seg_grid > 0 && (s = segments_backward(I, nsteps, ckpt_every, nseg, S, lc))) return s;
+    for (int64_t k = I.seg_grid > 0 ? -1 : nseg - 1; k >= 0; k--) {
       const int64_t len = std::min<int64_t>(ckpt_every, nsteps - k * ckpt_every);
-      if (I.seg_grid > 0) {
-        if ((s = segment_adjoint(I, I.ck + k * S, (int)len, lc))) return s;
-        if (len & 1) lc ^= 1;
-        continue;
-      }
       if ((s = state_in(I, I.ck + k * S))) return s;
       for (int64_t j = 0; j < len; j++) {
         if ((s = state_out(I, I.ring + j * S))) return s;
@@ -590,49 +590,46 @@ class Engine final : public EngineBase {
     return sms * std::min(nb1, nb2);
   }
 
-  // record slots for segments of up to len steps
+  // record slots (two sets) for segments of up to len steps
   nlc_status ensure_segment(InstHost<T>& I, int64_t len) {
     nlc_status s;
     if (!I.bar) {
-      if ((s = ensure_unfused(I))) return s;  // r1 scratch
-      if ((s = alloc(&I.bar, 1))) return s;
+      if ((s = alloc(&I.bar, 3))) return s;
       const int64_t want = (I.d.n + SEG_THREADS - 1) / SEG_THREADS;
       I.seg_grid = (int)std::min<int64_t>(seg_grid_max(), want);
     }
     if (I.seg_grid <= 0 || I.rec_len >= len) return NLC_OK;
     const int64_t n = I.d.n, comp = I.L.comp;
-    if ((s = alloc(&I.rec_g, (size_t)((len + 1) * Q * n))) ||
-        (s = alloc(&I.rec_q, (size_t)((len + 1) * 5 * comp))) ||
-        (s = alloc(&I.rec_pi, (size_t)(len * DIM * DIM * n))) ||
-        (s = alloc(&I.rec_u, (size_t)(len * DIM * comp))) ||
-        (s = alloc(&I.rec_qp, (size_t)(len * 5 * comp))))
-      return s;
+    for (int b = 0; b < 2; b++)
+      if ((s = alloc(&I.rec_g[b], (size_t)((len + 1) * Q * n))) ||
+          (s = alloc(&I.rec_q[b], (size_t)((len + 1) * 5 * comp))) ||
+          (s = alloc(&I.rec_pi[b], (size_t)(len * DIM * DIM * n))) ||
+          (s = alloc(&I.rec_u[b], (size_t)(len * DIM * comp))) ||
+          (s = alloc(&I.rec_qp[b], (size_t)(len * 5 * comp))) ||
+          (s = alloc(&I.rec_r1[b], (size_t)(5 * n))))
+        return s;
     I.rec_len = len;
+    if (!side_stream_) {
+      NLC_CK(cudaStreamCreateWithFlags(&side_stream_, cudaStreamNonBlocking));
+      for (int k = 0; k < 5; k++)
+        NLC_CK(cudaEventCreateWithFlags(&seg_ev_[k], cudaEventDisableTiming));
+    }
     return NLC_OK;
   }
 
-  // one segment of len steps from the checkpoint at ck: record, then reverse;
-  // the adjoint of the segment's end state is in (lQ[lc], lG[lc])
-  nlc_status segment_adjoint(InstHost<T>& I, const T* ck, int len, int lc) {
-    const int64_t n = I.d.n;
-    cudaStream_t st = args_.stream;
-    const int e0 = mark();
-    NLC_CK(cudaMemcpyAsync(I.rec_g, ck, sizeof(T) * Q * n, cudaMemcpyDeviceToDevice, st));
-    k_field_raw_in<T, DIM><<<grid1(n), 256, 0, st>>>(ck + (int64_t)Q * n, I.d,
-                                                       Field<T>{I.rec_q, I.L});
-    NLC_CK_LAUNCH("k_field_raw_in");
+  SegArgs<T> seg_args(InstHost<T>& I, int b, int len, int lc) {
     SegArgs<T> a;
     a.d = I.d;
     a.p = I.p;
     a.L = I.L;
     a.len = len;
     a.lc0 = lc;
-    a.g = I.rec_g;
-    a.q = I.rec_q;
-    a.pi = I.rec_pi;
-    a.u = I.rec_u;
-    a.qp = I.rec_qp;
-    a.r1 = I.r1;
+    a.g = I.rec_g[b];
+    a.q = I.rec_q[b];
+    a.pi = I.rec_pi[b];
+    a.u = I.rec_u[b];
+    a.qp = I.rec_qp[b];
+    a.r1 = I.rec_r1[b];
     a.lQ[0] = I.lQ[0];
     a.lQ[1] = I.lQ[1];
     a.lG[0] = I.lG[0];
@@ -643,16 +640,74 @@ class Engine final : public EngineBase {
     a.lF = I.lF;
     a.lDq = I.lDq;
     a.lLap = I.lLap;
-    a.acc = I.acc + (size_t)3 * 3 * grid1(n);
-    a.bar = I.bar;
+    a.acc = I.acc + (size_t)3 * 3 * grid1(I.d.n);
     a.err = derr_;
+    return a;
+  }
+
+  // record of a segment of len steps from the checkpoint at ck into set b,
+  // on stream ss
+  nlc_status segment_record(InstHost<T>& I, int b, const T* ck, int len, cudaStream_t ss) {
+    const int64_t n = I.d.n;
+    NLC_CK(cudaMemcpyAsync(I.rec_g[b], ck, sizeof(T) * Q * n, cudaMemcpyDeviceToDevice, ss));
+    k_field_raw_in<T, DIM><<<grid1(n), 256, 0, ss>>>(ck + (int64_t)Q * n, I.d,
+                                                       Field<T>{I.rec_q[b], I.L});
+    NLC_CK_LAUNCH("k_field_raw_in");
+    SegArgs<T> a = seg_args(I, b, len, 0);
+    a.bar = I.bar + b;
     void* args[] = {&a};
-    NLC_CK(cudaMemsetAsync(I.bar, 0, sizeof(GridBarrier), st));
+    NLC_CK(cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), ss));
     NLC_CK(cudaLaunchCooperativeKernel((const void*)k_seg_record<Lat, T>, dim3(I.seg_grid),
-                                       dim3(SEG_THREADS), args, 0, st));
-    NLC_CK(cudaMemsetAsync(I.bar, 0, sizeof(GridBarrier), st));
+                                       dim3(SEG_THREADS), args, 0, ss));
+    return NLC_OK;
+  }
+
+  // reverse of the segment recorded in set b; the adjoint of its end state
+  // is in (lQ[lc], lG[lc])
+  nlc_status segment_reverse(InstHost<T>& I, int b, int len, int lc, cudaStream_t st) {
+    SegArgs<T> a = seg_args(I, b, len, lc);
+    a.bar = I.bar + 2;
+    void* args[] = {&a};
+    NLC_CK(cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st));
     NLC_CK(cudaLaunchCooperativeKernel((const void*)k_seg_reverse<Lat, T>, dim3(I.seg_grid),
                                        dim3(SEG_THREADS), args, 0, st));
+    return NLC_OK;
+  }
+
+  // All segments, last to first: the record of segment k-1 runs on the side
+  // stream while segment k reverses on the main stream.  Record set k % 2
+  // is rewritten only after the reverse that read it (segment k+2) is done.
+  nlc_status segments_backward(InstHost<T>& I, int64_t nsteps, int ckpt_every, int64_t nseg,
+                               int64_t S, int& lc) {
+    cudaStream_t st = args_.stream, ss = side_stream_;
+    cudaEvent_t ev_main = seg_ev_[0], ev_rec[2] = {seg_ev_[1], seg_ev_[2]},
+                ev_rev[2] = {seg_ev_[3], seg_ev_[4]};
+    auto seg_len = [&](int64_t k) {
+      return (int)std::min<int64_t>(ckpt_every, nsteps - k * ckpt_every);
+    };
+    nlc_status s;
+    const int e0 = mark();
+    NLC_CK(cudaEventRecord(ev_main, st));  // checkpoints and seed are done
+    NLC_CK(cudaStreamWaitEvent(ss, ev_main, 0));
+    if ((s = segment_record(I, (int)((nseg - 1) & 1), I.ck + (nseg - 1) * S, seg_len(nseg - 1),
+                            ss)))
+      return s;
+    NLC_CK(cudaEventRecord(ev_rec[(nseg - 1) & 1], ss));
+    for (int64_t k = nseg - 1; k >= 0; k--) {
+      const int b = (int)(k & 1);
+      NLC_CK(cudaStreamWaitEvent(st, ev_rec[b], 0));
+      if (k > 0) {
+        const int bp = (int)((k - 1) & 1);
+        if (k + 1 < nseg) NLC_CK(cudaStreamWaitEvent(ss, ev_rev[bp], 0));
+        if ((s = segment_record(I, bp, I.ck + (k - 1) * S, seg_len(k - 1), ss))) return s;
+        NLC_CK(cudaEventRecord(ev_rec[bp], ss));
+      }
+      if ((s = segment_reverse(I, b, seg_len(k), lc, st))) return s;
+      NLC_CK(cudaEventRecord(ev_rev[b], st));
+      if (seg_len(k) & 1) lc ^= 1;
+    }
+    NLC_CK(cudaEventRecord(ev_main, ss));
+    NLC_CK(cudaStreamWaitEvent(st, ev_main, 0));
     const int e1 = mark();
     if (timer.on) timer.span(KID_ADJOINT, e0, e1);
     return NLC_OK;
@@ -775,19 +830,38 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
-  // captures graph_steps fused steps starting from buffer parity c
-  nlc_status ensure_graph(int c) {
-    if (graph_[c] && graph_len_[c] == graph_steps) return NLC_OK;
-    if (graph_[c]) {
-      cudaGraphExecDestroy(graph_[c]);
-      graph_[c] = nullptr;
+  // len fused steps on the context's stream; runs of a few steps or more
+  // replay a captured graph of exactly len steps (cached per buffer parity
+  // and length) instead of launching kernel by kernel
+  nlc_status fused_steps(int64_t len) {
+    if (len < 4 || timer.on) {
+      for (int64_t j = 0; j < len; j++) {
+        nlc_status s = step_fused(args_.stream);
+        if (s) return s;
+      }
+      return NLC_OK;
     }
+    cudaGraphExec_t ex = nullptr;
+    for (const SweepGraph& e : sweep_graphs_)
+      if (e.parity == cur_ && e.len == len) ex = e.exec;
+    if (!ex) {
+      nlc_status s = capture_steps(cur_, (int)len, &ex);
+      if (s) return s;
+      sweep_graphs_.push_back(SweepGraph{cur_, len, ex});
+    }
+    NLC_CK(cudaGraphLaunch(ex, args_.stream));
+    if (len & 1) cur_ ^= 1;
+    return NLC_OK;
+  }
+
+  // captures len fused steps starting from buffer parity c
+  nlc_status capture_steps(int c, int len, cudaGraphExec_t* out) {
     if (!cap_stream_) NLC_CK(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
     const int saved = cur_;
     cur_ = c;
     NLC_CK(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
     nlc_status s = NLC_OK;
-    for (int k = 0; k < graph_steps && s == NLC_OK; k++) s = step_fused(cap_stream_);
+    for (int k = 0; k < len && s == NLC_OK; k++) s = step_fused(cap_stream_);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap_stream_, &g);
     cur_ = saved;
@@ -799,12 +873,24 @@ class Engine final : public EngineBase {
       err = std::string("stream capture: ") + cudaGetErrorString(e);
       return NLC_ECUDA;
     }
-    e = cudaGraphInstantiate(&graph_[c], g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
       err = std::string("graph instantiate: ") + cudaGetErrorString(e);
       return NLC_ECUDA;
     }
+    return NLC_OK;
+  }
+
+  // captures graph_steps fused steps starting from buffer parity c
+  nlc_status ensure_graph(int c) {
+    if (graph_[c] && graph_len_[c] == graph_steps) return NLC_OK;
+    if (graph_[c]) {
+      cudaGraphExecDestroy(graph_[c]);
+      graph_[c] = nullptr;
+    }
+    nlc_status s = capture_steps(c, graph_steps, &graph_[c]);
+    if (s) return s;
     graph_len_[c] = graph_steps;
     return NLC_OK;
   }
@@ -823,6 +909,14 @@ class Engine final : public EngineBase {
   int cur_ = 0;
   cudaStream_t cap_stream_ = nullptr;
   cudaGraphExec_t graph_[2] = {nullptr, nullptr};
+  struct SweepGraph {
+    int parity;
+    int64_t len;
+    cudaGraphExec_t exec;
+  };
+  std::vector<SweepGraph> sweep_graphs_;  // the adjoint's forward sweeps
+  cudaStream_t side_stream_ = nullptr;    // adjoint segment records
+  cudaEvent_t seg_ev_[5] = {};
   int graph_len_[2] = {0, 0};
 };
 
