@@ -1,11 +1,12 @@
-// adjoint.cuh -- one reverse time step of the hybrid scheme (hand-written
-// adjoint) and the seed of the droplet loss, as one-cell-per-thread kernels.
+// adjoint.cuh -- the stages of one reverse time step of the hybrid scheme
+// (hand-written adjoint) as per-cell functions, run by the segment kernels of
+// adjoint_segment.cuh, and the kernels of the droplet loss's seed.
 //
 // Notation: the state at step n is (Q^n, g^n) with g the post-collision
 // deviations in pull layout (step_unfused.cuh).  Adjoints are dense [comp][n]
 // arrays (neighbours by periodic wrap).  Given the adjoints of the state at
-// n+1 (lQn, lGn) the kernels produce the adjoints at n (lQ, lG), reading the
-// forward intermediates of step n recomputed from the state (Pi, u^n, Q^P, R1).
+// n+1 (lQn, lGn) the stages produce the adjoints at n (lQ, lG), reading the
+// forward intermediates of step n (Pi, u^n, Q^P) recorded for the segment.
 //
 // The transposes of the stencils are written in gather form:
 //   central difference  d_g v(x) = [v(x+e_g) - v(x-e_g)]/2
@@ -106,20 +107,6 @@ __device__ __forceinline__ void adj_be2_at(const Field<T>& QP, const Field<T>& U
   }
 }
 
-template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_adj_be2(Field<T> QP, Field<T> U,
-                                                 const T* __restrict__ lQn,
-                                                 T* __restrict__ lQP, T* __restrict__ lUa,
-                                                 T* __restrict__ lGv, Dims d, Par<T> p,
-                                                 double* __restrict__ acc) {
-  int x, y, z;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  ParBar<T> pb{T(0), T(0), T(0)};
-  if (decode(d, idx, x, y, z))
-    adj_be2_at<Lat, T>(QP, U, lQn, lQP, lUa, lGv, d, p, pb, idx, x, y, z);
-  add_param_bar(pb, acc);
-}
-
 // 2. adjoint of the predictor evaluation R1 = R(Q^n; u), with
 //    rbar = lQn / 2 + lQP (R1 enters Q^{n+1} with 1/2 and Q^P with 1), and
 //    of Q^{n+1} = Q^n + ..., Q^P = Q^n + R1:  lQ = lQn + lQP + J^T rbar.
@@ -150,21 +137,6 @@ __device__ __forceinline__ void adj_be1_at(const Field<T>& Q, const Field<T>& U,
       for (int b = 0; b < DIM; b++) lGv[(a * DIM + b) * d.n + idx] += Gb[a][b];
     }
   }
-}
-
-template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_adj_be1(Field<T> Q, Field<T> U,
-                                                 const T* __restrict__ lQn,
-                                                 const T* __restrict__ lQP,
-                                                 T* __restrict__ lQ, T* __restrict__ lUa,
-                                                 T* __restrict__ lGv, Dims d, Par<T> p,
-                                                 double* __restrict__ acc) {
-  int x, y, z;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  ParBar<T> pb{T(0), T(0), T(0)};
-  if (decode(d, idx, x, y, z))
-    adj_be1_at<Lat, T>(Q, U, lQn, lQP, lQ, lUa, lGv, d, p, pb, idx, x, y, z);
-  add_param_bar(pb, acc);
 }
 
 // 3. adjoint of the LB update at cell x: u-bar from the Beris-Edwards side

@@ -63,8 +63,6 @@ struct InstHost {
   double* acc = nullptr;  // [3 kernels][blocks][3]
   T* ck = nullptr;        // checkpoints, (Q + 5) n each
   int64_t ck_count = 0;
-  T* ring = nullptr;      // states of one segment, (Q + 5) n each
-  int64_t ring_count = 0;
   // segment records of the persistent adjoint kernels (adjoint_segment.cuh),
   // two sets: the record of segment k-1 is written while segment k reverses
   T *rec_g[2] = {}, *rec_q[2] = {}, *rec_pi[2] = {}, *rec_u[2] = {}, *rec_qp[2] = {},
@@ -353,8 +351,12 @@ class Engine final : public EngineBase {
     cudaStream_t st = args_.stream;
     nlc_status s;
     if ((s = ensure_staging(I)) || (s = ensure_segment(I, ckpt_every)) ||
-        (s = ensure_adjoint(I, nseg + 1, I.seg_grid > 0 ? 0 : ckpt_every)))
+        (s = ensure_adjoint(I, nseg + 1)))
       return s;
+    if (I.seg_grid <= 0) {
+      err = "the adjoint needs cooperative launches of its segment kernels";
+      return NLC_EUNSUPPORTED;
+    }
     if (!maps_ok_) {
       err = "TMA tensor maps unavailable; the adjoint needs the fused step";
       return NLC_EUNSUPPORTED;
@@ -392,23 +394,8 @@ class Engine final : public EngineBase {
       k_adj_stencil<Lat, T><<<gb, 256, 0, st>>>(I.lDq, I.lLap, I.lQ[lc], I.d);
       NLC_CK_LAUNCH("adjoint seed");
     }
-    // backward sweep, segment by segment: two persistent kernels per segment
-    // (record, reverse) where cooperative launches are available, else the
-    // recomputation into the state ring and one reverse step at a time
-    if (I.seg_grid > 0 && (s = segments_backward(I, nsteps, ckpt_every, nseg, S, lc))) return s;
-    for (int64_t k = I.seg_grid > 0 ? -1 : nseg - 1; k >= 0; k--) {
-      const int64_t len = std::min<int64_t>(ckpt_every, nsteps - k * ckpt_every);
-      if ((s = state_in(I, I.ck + k * S))) return s;
-      for (int64_t j = 0; j < len; j++) {
-        if ((s = state_out(I, I.ring + j * S))) return s;
-        if (j + 1 < len && (s = step_fused(st))) return s;
-      }
-      for (int64_t j = len - 1; j >= 0; j--) {
-        if ((s = state_in(I, I.ring + j * S))) return s;
-        if ((s = adjoint_step(I, lc))) return s;
-        lc ^= 1;
-      }
-    }
+    // backward sweep, segment by segment (adjoint_segment.cuh)
+    if ((s = segments_backward(I, nsteps, ckpt_every, nseg, S, lc))) return s;
     // gradients: every block slot of every kernel, summed in a fixed order
     const unsigned gb = grid1(n);
     std::vector<double> acc((size_t)3 * (3 * gb + I.seg_grid));
@@ -549,10 +536,11 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
-  nlc_status ensure_adjoint(InstHost<T>& I, int64_t ck_count, int64_t ring_count) {
+  nlc_status ensure_adjoint(InstHost<T>& I, int64_t ck_count) {
     nlc_status s;
     const int64_t n = I.d.n;
     const int64_t S = (int64_t)(Q + 5) * n;
+    if ((s = ensure_unfused(I))) return s;  // Pi for the loss seed
     if (!I.lQP) {
       if ((s = alloc(&I.lQ[0], (size_t)5 * n)) || (s = alloc(&I.lQ[1], (size_t)5 * n)) ||
           (s = alloc(&I.lG[0], (size_t)Q * n)) || (s = alloc(&I.lG[1], (size_t)Q * n)) ||
@@ -565,10 +553,6 @@ class Engine final : public EngineBase {
     if (I.ck_count < ck_count) {
       if ((s = alloc(&I.ck, (size_t)(ck_count * S)))) return s;
       I.ck_count = ck_count;
-    }
-    if (I.ring_count < ring_count) {
-      if ((s = alloc(&I.ring, (size_t)(ring_count * S)))) return s;
-      I.ring_count = ring_count;
     }
     return NLC_OK;
   }
@@ -729,35 +713,6 @@ class Engine final : public EngineBase {
     NLC_CK(cudaMemcpyAsync(I.g[cur_], src, sizeof(T) * Q * n, cudaMemcpyDeviceToDevice, st));
     k_field_raw_in<T, DIM><<<grid1(n), 256, 0, st>>>(src + (int64_t)Q * n, I.d, I.q[cur_]);
     NLC_CK_LAUNCH("k_field_raw_in");
-    return NLC_OK;
-  }
-
-  // one reverse step: the current buffers hold the state of step n; the
-  // adjoint of the state at n+1 is in (lQ[lc], lG[lc]); writes the adjoint
-  // at n into (lQ[lc^1], lG[lc^1])
-  nlc_status adjoint_step(InstHost<T>& I, int lc) {
-    const int64_t n = I.d.n;
-    const unsigned gb = grid1(n);
-    cudaStream_t st = args_.stream;
-    const int a = cur_, b = cur_ ^ 1;
-    const int e0 = mark();
-    // forward intermediates of the step
-    k_stress<Lat, T><<<gb, 256, 0, st>>>(I.q[a], I.pi, I.d, I.p);
-    k_lb<Lat, T><<<gb, 256, 0, st>>>(I.g[a], I.g[b], I.pi, I.u, I.d, I.p);
-    k_predict<Lat, T><<<gb, 256, 0, st>>>(I.q[a], I.u, I.qp, I.r1, I.d, I.p);
-    // reverse
-    k_adj_be2<Lat, T><<<gb, 256, 0, st>>>(I.qp, I.u, I.lQ[lc], I.lQP, I.lUa, I.lGv, I.d, I.p,
-                                          I.acc);
-    k_adj_be1<Lat, T><<<gb, 256, 0, st>>>(I.q[a], I.u, I.lQ[lc], I.lQP, I.lQ[lc ^ 1], I.lUa,
-                                          I.lGv, I.d, I.p, I.acc + 3 * gb);
-    k_adj_lb<Lat, T><<<gb, 256, 0, st>>>(I.g[a], I.pi, I.lG[lc], I.lUa, I.lGv, I.lG[lc ^ 1],
-                                         I.lF, I.d, I.p, T(0));
-    k_adj_stress<Lat, T><<<gb, 256, 0, st>>>(I.q[a], I.lF, I.lQ[lc ^ 1], I.lDq, I.lLap, I.d,
-                                             I.p, I.acc + 2 * 3 * gb);
-    k_adj_stencil<Lat, T><<<gb, 256, 0, st>>>(I.lDq, I.lLap, I.lQ[lc ^ 1], I.d);
-    NLC_CK_LAUNCH("adjoint step");
-    const int e1 = mark();
-    if (timer.on) timer.span(KID_ADJOINT, e0, e1);
     return NLC_OK;
   }
 
