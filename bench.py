@@ -48,8 +48,8 @@ ALG_BYTES = {"fused_lb": (2 * Q3 + 5) * WORD,  # 172 B
 # on; reported as null once those sources change.
 NCU_TRAFFIC = {
     # 256 x 256 x 64 capture (4,194,304 cells), see profiles/
-    "fused_lb": ((417.0e6 + 335.0e6) / 4194304, "3ae25dfef694eeee"),
-    "fused_be": ((154.0e6 + 62.9e6) / 4194304, "3ae25dfef694eeee"),
+    "fused_lb": ((417.036e6 + 338.242e6) / 4194304, "de845dbf17f24908"),
+    "fused_be": ((153.700e6 + 62.329e6) / 4194304, "de845dbf17f24908"),
 }
 
 KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",
@@ -465,7 +465,7 @@ def run_adjoint(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     w = wl.adjoint_disc_128()
-    steps, ckpt = w.steps, w.extra["ckpt_every"]
+    steps, ckpt = (args.adjoint_steps or w.steps), w.extra["ckpt_every"]
     sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
                          stream=stream.cuda_stream)
     Q0 = w.initial_q5()
@@ -522,6 +522,8 @@ def main():
     ap.add_argument("--workload", default="sphere256",
                     choices=["sphere256", "sweep64", "adjoint128"],
                     help="sweep64: batched vs sequential temperature sweep")
+    ap.add_argument("--adjoint-steps", type=int, default=0,
+                    help="steps of the adjoint workload (default: its own 2000)")
     ap.add_argument("--graph-steps", type=int, default=50)
     args = ap.parse_args()
     # at least three untimed warm-up steps (reported as the count used)
