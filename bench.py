@@ -188,13 +188,38 @@ def oracle_sample_rate(w, steps, shape=None):
     Q = ws.initial_q5()
     f = orc.init_equilibrium(ws.lattice, ws.shape)
     p = wl.param_vector(ws.params)
+    threads = orc.set_threads(0)
     t0 = time.perf_counter()
     orc.step(ws.lattice, p, f, Q, steps)
     dt = time.perf_counter() - t0
     nz, ny, nx = ws.shape
     desc = (f"{steps} step(s) of the oracle on a {nx}x{ny}x{nz} D3Q19 lattice "
             f"with the droplet recipe, FP64, OpenMP")
-    return nx * ny * nz * steps / dt / 1e6, int(os.environ["OMP_NUM_THREADS"]), desc
+    return nx * ny * nz * steps / dt / 1e6, threads, desc
+
+
+def oracle_single_thread_rate(w):
+    """The same oracle on one host thread, one step of an 8-plane slab of the
+    workload.  Returns (MLUPS, description)."""
+    import oracle
+    from paper_1907_13415_gb300 import workloads as wl
+    orc = oracle.get()
+    nz, ny, nx = w.shape
+    ws = wl.scaled(w, (min(8, nz), ny, nx))
+    Q = ws.initial_q5()
+    f = orc.init_equilibrium(ws.lattice, ws.shape)
+    p = wl.param_vector(ws.params)
+    saved = orc.set_threads(0)
+    orc.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        orc.step(ws.lattice, p, f, Q, 1)
+        dt = time.perf_counter() - t0
+    finally:
+        orc.set_threads(saved)
+    cells = ws.shape[0] * ny * nx
+    return cells / dt / 1e6, (f"1 step of the oracle on a {nx}x{ny}x{ws.shape[0]} slab, "
+                              f"FP64, one thread")
 
 
 def mem_available_gb():
@@ -360,8 +385,11 @@ def run_ours(args, w):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         shape = baseline_shape(w)
         rate, cores, desc = oracle_sample_rate(w, 1, shape)
+        rate1, desc1 = oracle_single_thread_rate(w)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": desc}
+               "sample": desc,
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": desc1}}
 
     if rank == 0:
         nz, ny, nx = w.shape

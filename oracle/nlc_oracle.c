@@ -700,3 +700,21 @@ int API(orc_observables)(int lattice, int nx, int ny, int nz, const rt *p,
   free(prof);
   return 0;
 }
+
+#ifndef ORC_COMPLEX
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+/* Threads of the OpenMP cell loops (for timing; the results do not depend on
+ * it: every loop writes disjoint cells and the reductions are serial).
+ * n <= 0 leaves the count unchanged.  Returns the count now in effect. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+#endif

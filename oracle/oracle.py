@@ -28,6 +28,7 @@ class Oracle:
 
     def __init__(self, lib, complex_step=False):
         self.cs = complex_step
+        self._lib = lib
         self.dtype = np.complex128 if complex_step else np.float64
         sfx = "_cs" if complex_step else ""
         self._f = {}
@@ -79,6 +80,14 @@ class Oracle:
             else:
                 conv.append(a)
         return fn(*conv)
+
+    def set_threads(self, n=0):
+        """OpenMP threads of the cell loops (n <= 0: unchanged); returns the
+        count in effect."""
+        fn = self._lib.orc_set_threads
+        fn.argtypes = [_I]
+        fn.restype = _I
+        return int(fn(int(n)))
 
     # -- lattice -------------------------------------------------------
     def lattice(self, lattice):
