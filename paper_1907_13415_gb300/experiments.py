@@ -11,7 +11,10 @@ sweep : temperature sweep (Sec. 2.1, Fig. 1D inset): interface velocity
         against gamma for the 64 uneven lattices of the batched workload, in
         one batched context, next to the Allen-Cahn estimate.
 paper_circle : the almost static circle of Sec. 2.2 with the paper's own
-        parameters, for the spurious-velocity estimate.
+        parameters, for the spurious-velocity estimate (with --dump, the
+        final Q, u and vorticity fields as .npz).
+flat_paper : the flat interface of Sec. 2.1 with the paper's own parameters
+        to t = 350000: interface velocity and the profile against Eq. 7.
 Each prints one JSON object.  FP32 results carry max|dQ| (normwise, against
 the FP64 run of the same problem) and the drift of the interface position or
 radius.
@@ -86,23 +89,90 @@ def disc(delta=0.0, steps=20000, n=256, radius=32, every=500):
             "fp32_vs_fp64": _drift("radius", t32, t64, Q32, Q64)}
 
 
-def paper_circle(angle_deg=0.0, steps=35000, every=1000, gamma=2.707681):
+def vorticity(u):
+    """omega_z = d_x u_y - d_y u_x of a (3, nz, ny, nx) velocity field by
+    periodic central differences (the field the paper's Fig. 2B colours)."""
+    ux, uy = u[0], u[1]
+    return ((np.roll(uy, -1, axis=-1) - np.roll(uy, 1, axis=-1))
+            - (np.roll(ux, -1, axis=-2) - np.roll(ux, 1, axis=-2))) / 2.0
+
+
+def paper_circle(angle_deg=0.0, steps=35000, every=1000, gamma=2.707681,
+                 lattice=wl.D2Q9, dump=None):
     """Sec. 2.2 / Fig. 2 with the paper's parameters (tau = 1.5, K = 0.04,
     Gamma = 0.34, xi = 0.7, A0 = 0.1): a 100 x 100 lattice, disc of radius 25,
     director at angle_deg from y, gamma = 2.707681.  Reports the interface
     velocity dR/dt and max |u| at the end (the paper: u_i ~ 1.89e-7,
-    u_max = 8.97e-7 at 0 deg and 1.13e-6 at 20 deg, on D3Q19 with MRT)."""
+    u_max = 8.97e-7 at 0 deg and 1.13e-6 at 20 deg, on D3Q19 with MRT).
+    lattice: D2Q9, or D3Q19 on a single plane (nz = 1) as in the paper.
+    dump: path of an .npz file for the final Q, u and vorticity fields."""
     a = math.radians(angle_deg)
     p = dict(wl.PAPER_PARAMS, gamma=gamma)
-    w = wl.Workload("paper_circle", wl.D2Q9, (1, 100, 100), p, steps, "ball", 25,
+    w = wl.Workload("paper_circle", lattice, (1, 100, 100), p, steps, "ball", 25,
                     (math.sin(a), math.cos(a), 0.0), 0.0, 0)
-    t64, _ = _run(w, nlc.NLC_FP64, steps, every)
-    R = np.array([o["radius"] for o in t64])
+    s = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP64,
+                       stream=_stream())
+    s.set_fields(w.initial_q5())
+    trace = [s.observables()]
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        s.step(k)
+        done += k
+        trace.append(s.observables())
+    Q, rho, u = s.get_fields()
+    s.close()
+    om = vorticity(u)
+    if dump:
+        np.savez_compressed(dump, Q=Q, rho=rho, u=u, vorticity=om)
+    R = np.array([o["radius"] for o in trace])
     tail = max(2, len(R) // 4)
     return {"experiment": "paper circle", "angle_deg": angle_deg, "gamma": gamma,
+            "lattice": "D2Q9" if lattice == wl.D2Q9 else "D3Q19 (nz = 1)",
             "steps": steps, "radius_final": float(R[-1]),
             "dRdt_final": float((R[-1] - R[-tail]) / ((tail - 1) * every)),
-            "max_u_final": float(t64[-1]["max_u"])}
+            "max_u_final": float(trace[-1]["max_u"]),
+            "max_abs_vorticity": float(np.abs(om).max())}
+
+
+def flat_paper(gamma=2.7, steps=350000, lx=200, ly=8, every=10000):
+    """Sec. 2.1 / Fig. 1 with the paper's parameters: a nematic slab in the
+    middle of an lx x ly lattice (director along y), run to t = 350000.
+    Reports the right interface's position and velocity, max |u|, and the
+    largest deviation of the S(x) profile from Eq. 7 with S_n = 1/3 and
+    lambda = 2 (fitted interface position), FP64."""
+    p = dict(wl.PAPER_PARAMS, gamma=gamma)
+    w = wl.Workload("flat_paper", wl.D2Q9, (1, ly, lx), p, steps, "slab", lx // 2,
+                    (0, 1, 0), 0.0, 0)
+    # nematic in the centre: S = 1/3 for lx/4 <= x < 3 lx/4
+    S = np.where((np.arange(lx) >= lx // 4) & (np.arange(lx) < 3 * lx // 4), wl.S_COEX, 0.0)
+    Q0 = wl.uniaxial_q5(np.broadcast_to(S, (1, ly, lx)).copy(), (0, 1, 0))
+    s = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP64,
+                       stream=_stream())
+    s.set_fields(Q0)
+    xs, done = [], 0
+    while done < steps:
+        k = min(every, steps - done)
+        s.step(k)
+        done += k
+        xs.append(s.observables()["x_iface"])
+    o = s.observables(profile=True)
+    s.close()
+    prof = np.asarray(o["s_profile"])
+    x = np.arange(lx, dtype=np.float64)
+    lam, Sn = 2.0, 1.0 / 3.0
+    xr = o["x_iface"]
+    # Eq. 7 around the right interface: S = S_n/2 [1 - tanh((x - x_i)/(2 lambda))]
+    win = np.abs(x - xr) < 6 * lam
+    best = min((np.abs(prof[win] - Sn / 2 * (1 - np.tanh((x[win] - xi) / (2 * lam)))).max(), xi)
+               for xi in np.linspace(xr - 0.5, xr + 0.5, 201))
+    xs = np.array(xs)
+    half = len(xs) // 2
+    v = float(np.polyfit(np.arange(half, len(xs)) * every, xs[half:], 1)[0]) if len(xs) > 3 else 0.0
+    return {"experiment": "flat interface (paper parameters)", "gamma": gamma,
+            "lattice": [lx, ly], "steps": steps, "x_iface": float(xr),
+            "velocity": v, "max_u": float(o["max_u"]),
+            "eq7_max_deviation": float(best[0]), "eq7_fit_x_iface": float(best[1])}
 
 
 def sweep(steps=50000, every=2500, graph_steps=50):
@@ -138,8 +208,10 @@ def sweep(steps=50000, every=2500, graph_steps=50):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["flat", "disc", "sweep", "paper_circle"])
+    ap.add_argument("which", choices=["flat", "disc", "sweep", "paper_circle", "flat_paper"])
     ap.add_argument("--angle", type=float, default=0.0)
+    ap.add_argument("--lattice", choices=["d2q9", "d3q19"], default="d2q9")
+    ap.add_argument("--dump", default=None, help="paper_circle: .npz of the final fields")
     ap.add_argument("--gamma", type=float, default=2.7)
     ap.add_argument("--delta", type=float, default=0.0)
     ap.add_argument("--steps", type=int, default=None)
@@ -151,7 +223,11 @@ def main(argv=None):
     elif args.which == "disc":
         r = disc(args.delta, args.steps or 20000)
     elif args.which == "paper_circle":
-        r = paper_circle(args.angle, args.steps or 35000)
+        r = paper_circle(args.angle, args.steps or 35000,
+                         lattice=wl.D3Q19 if args.lattice == "d3q19" else wl.D2Q9,
+                         dump=args.dump)
+    elif args.which == "flat_paper":
+        r = flat_paper(args.gamma, args.steps or 350000)
     else:
         r = sweep(args.steps or 50000)
     print(json.dumps(r))

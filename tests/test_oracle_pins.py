@@ -67,6 +67,33 @@ def free_energy_np(Q5, p):
     return np.sum(bulk) + K / 2 * np.sum(grad)
 
 
+@pytest.mark.parametrize("lattice,shape", [(wl.D2Q9, (1, 12, 14)),
+                                           (wl.D3Q19, (6, 7, 8))])
+def test_free_energy_decreases_without_flow(orc, lattice, shape):
+    """With u = 0, Eq. 1 is the gradient flow dQ/dt = Gamma H = -Gamma dF/dQ
+    of the discrete free energy, so F (Eq. 2, written independently above)
+    never increases under the predictor-corrector steps of the oracle's
+    right-hand side (small steps: Gamma K 4d << 1).  Also pins the oracle's
+    free-energy observable to that independent F."""
+    w = wl.sphere_256().with_(lattice=lattice, shape=shape, geometry="ball",
+                              size=0.35 * min(shape[1:]), noise=2e-2, seed=11)
+    p = params(gamma=2.7)
+    Q = w.initial_q5()
+    u0 = np.zeros((3,) + shape)
+    f = orc.init_equilibrium(lattice, shape)
+    F = [free_energy_np(Q, p)]
+    assert orc.observables(lattice, p, f, Q)["free_energy"] == pytest.approx(
+        F[0], rel=1e-12)
+    for _ in range(60):
+        R1 = orc.rhs(lattice, p, Q, u0)
+        R2 = orc.rhs(lattice, p, Q + R1, u0)
+        Q = Q + 0.5 * (R1 + R2)
+        F.append(free_energy_np(Q, p))
+    F = np.array(F)
+    assert np.all(np.diff(F) <= 1e-14 * np.abs(F[:-1]))
+    assert F[-1] < F[0]
+
+
 @pytest.mark.parametrize("lattice,shape", [(wl.D2Q9, (1, 5, 6)),
                                            (wl.D3Q19, (3, 4, 5))])
 def test_H_is_minus_gradient_of_free_energy(orc, lattice, shape):
