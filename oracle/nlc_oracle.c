@@ -27,6 +27,9 @@
  *       the predictor-corrector use that same u^n (and its gradient).
  *   R2  Collision is BGK with the single relaxation time tau (Sec. 1.2.1 gives
  *       the source term in its BGK form; the MRT matrices are not given).
+ *       orc_set_mrt switches to a multiple-relaxation-time collision on an
+ *       orthogonal moment basis with caller-given rates (see collide_mrt);
+ *       with all rates 1/tau it is the BGK step.
  *   R3  The Laplacian is the standard 2d+1-point second-order stencil; first
  *       derivatives (including the advection term and grad u) are central.
  *   R4  The right-hand side of Eq. 1 is made traceless by the orthogonal
@@ -313,6 +316,124 @@ static void guo_source(int lattice, rt tau, const rt u[3], const rt F[3],
 }
 
 /* ------------------------------------------------------------------ */
+/* Multiple-relaxation-time collision (Sec. 1.2.1 names MRT as the       */
+/* operator used; its matrices and rates are not given, so the rates are */
+/* the caller's).  Moment space: the polynomials below, evaluated on the */
+/* lattice velocities and made orthogonal by Gram-Schmidt with unit      */
+/* weights in the listed order, rows v_k.  With S = diag(s_k) and the    */
+/* force term without its BGK prefactor,                                 */
+/*   Ft_i = w_i [c_i/cs^2 (1 + c_i.u/cs^2) - u/cs^2] . F,                 */
+/* the post-collision populations are                                   */
+/*   f* = f - M^-1 S M (f - feq + Ft/2) + Ft,                            */
+/* i.e. f - sum_k v_k s_k (v_k . y)/(v_k . v_k) + Ft with y = f - feq +   */
+/* Ft/2.  With every s_k = 1/tau this is the BGK step with its source    */
+/* term.  Moments, D2Q9: 1, c^2, c^4, cx, c^2 cx, cy, c^2 cy,            */
+/* cx^2 - cy^2, cx cy.  D3Q19: 1, c^2, c^4, cx, c^2 cx, cy, c^2 cy, cz,    */
+/* c^2 cz, 3cx^2 - c^2, (3cx^2 - c^2) c^2, cy^2 - cz^2,                   */
+/* (cy^2 - cz^2) c^2, cx cy, cy cz, cx cz, cx (cy^2 - cz^2),              */
+/* cy (cz^2 - cx^2), cz (cx^2 - cy^2).                                    */
+/* ------------------------------------------------------------------ */
+static double moment_poly(int lattice, int k, const int cv[3]) {
+  double x = cv[0], y = cv[1], z = cv[2], c2 = x * x + y * y + z * z;
+  if (lattice == ORC_D2Q9) {
+    switch (k) {
+      case 0: return 1.0;
+      case 1: return c2;
+      case 2: return c2 * c2;
+      case 3: return x;
+      case 4: return c2 * x;
+      case 5: return y;
+      case 6: return c2 * y;
+      case 7: return x * x - y * y;
+      default: return x * y;
+    }
+  }
+  switch (k) {
+    case 0: return 1.0;
+    case 1: return c2;
+    case 2: return c2 * c2;
+    case 3: return x;
+    case 4: return c2 * x;
+    case 5: return y;
+    case 6: return c2 * y;
+    case 7: return z;
+    case 8: return c2 * z;
+    case 9: return 3.0 * x * x - c2;
+    case 10: return (3.0 * x * x - c2) * c2;
+    case 11: return y * y - z * z;
+    case 12: return (y * y - z * z) * c2;
+    case 13: return x * y;
+    case 14: return y * z;
+    case 15: return x * z;
+    case 16: return x * (y * y - z * z);
+    case 17: return y * (z * z - x * x);
+    default: return z * (x * x - y * y);
+  }
+}
+
+static int mrt_on = 0;
+static double mrt_rate[19];
+static double mrt_v[19][19];   /* orthogonal rows v_k[i] */
+static double mrt_n2[19];      /* v_k . v_k */
+
+static void mrt_basis(int lattice) {
+  int q = nvel(lattice);
+  const int(*cv)[3] = vel(lattice);
+  for (int k = 0; k < q; k++) {
+    for (int i = 0; i < q; i++) mrt_v[k][i] = moment_poly(lattice, k, cv[i]);
+    for (int j = 0; j < k; j++) {
+      double d = 0.0;
+      for (int i = 0; i < q; i++) d += mrt_v[k][i] * mrt_v[j][i];
+      for (int i = 0; i < q; i++) mrt_v[k][i] -= d / mrt_n2[j] * mrt_v[j][i];
+    }
+    mrt_n2[k] = 0.0;
+    for (int i = 0; i < q; i++) mrt_n2[k] += mrt_v[k][i] * mrt_v[k][i];
+  }
+}
+
+/* rates: q relaxation rates in the moment order above (those of the
+ * conserved moments, 1 and c, have no effect), or NULL for BGK. */
+int API(orc_set_mrt)(int lattice, const double *rates) {
+  if (!rates) {
+    mrt_on = 0;
+    return 0;
+  }
+  if (lattice != ORC_D2Q9 && lattice != ORC_D3Q19) return -1;
+  mrt_basis(lattice);
+  for (int k = 0; k < nvel(lattice); k++) mrt_rate[k] = rates[k];
+  mrt_on = lattice + 1;
+  return 0;
+}
+
+/* Ft_i: the force term of Sec. 1.2.1 without the factor (1 - 1/(2 tau)) */
+static void force_term(int lattice, const rt u[3], const rt F[3], rt *ft) {
+  int q = nvel(lattice);
+  const int(*cv)[3] = vel(lattice);
+  const double *w = wgt(lattice);
+  for (int i = 0; i < q; i++) {
+    rt cu = cv[i][0] * u[0] + cv[i][1] * u[1] + cv[i][2] * u[2];
+    rt s = 0;
+    for (int a = 0; a < 3; a++)
+      s += (cv[i][a] / CS2 * (1.0 + cu / CS2) - u[a] / CS2) * F[a];
+    ft[i] = w[i] * s;
+  }
+}
+
+static void collide_mrt(int lattice, const rt *f, const rt *feq, const rt *ft,
+                        rt *post) {
+  int q = nvel(lattice);
+  rt y[19];
+  for (int i = 0; i < q; i++) y[i] = f[i] - feq[i] + ft[i] / 2.0;
+  for (int i = 0; i < q; i++) post[i] = f[i] + ft[i];
+  for (int k = 0; k < q; k++) {
+    rt m = 0;
+    for (int i = 0; i < q; i++) m += mrt_v[k][i] * y[i];
+    rt a = mrt_rate[k] * m / mrt_n2[k];
+    for (int i = 0; i < q; i++) post[i] -= mrt_v[k][i] * a;
+  }
+}
+
+/* ------------------------------------------------------------------ */
 /* Whole-lattice stages.                                                  */
 /* ------------------------------------------------------------------ */
 
@@ -373,7 +494,8 @@ static void stage_moments(const grid_t *g, const rt *f, const rt *F3, rt *rho,
   }
 }
 
-/* BGK collision with source, then streaming f_i(x + c_i, t + 1) = f*_i(x). */
+/* BGK (or, after orc_set_mrt for this lattice, MRT) collision with the   */
+/* source term, then streaming f_i(x + c_i, t + 1) = f*_i(x).             */
 static void stage_collide_stream(const grid_t *g, const rt *p, const rt *f,
                                  const rt *rho, const rt *u3, const rt *F3,
                                  rt *fnew) {
@@ -385,14 +507,21 @@ static void stage_collide_stream(const grid_t *g, const rt *p, const rt *f,
   for (long c = 0; c < N; c++) {
     rt u[3] = {u3[0 * N + c], u3[1 * N + c], u3[2 * N + c]};
     rt F[3] = {F3[0 * N + c], F3[1 * N + c], F3[2 * N + c]};
-    rt feq[19], src[19];
+    rt feq[19], src[19], fc[19], post[19];
     equilibrium(g->lattice, rho[c], u, feq);
-    guo_source(g->lattice, tau, u, F, src);
-    for (int i = 0; i < q; i++) {
-      rt fi = f[i * N + c];
-      rt post = fi - (fi - feq[i]) / tau + src[i];
-      fnew[i * N + neighbour(g, c, cv[i][0], cv[i][1], cv[i][2])] = post;
+    if (mrt_on == g->lattice + 1) {
+      force_term(g->lattice, u, F, src);
+      for (int i = 0; i < q; i++) fc[i] = f[i * N + c];
+      collide_mrt(g->lattice, fc, feq, src, post);
+    } else {
+      guo_source(g->lattice, tau, u, F, src);
+      for (int i = 0; i < q; i++) {
+        rt fi = f[i * N + c];
+        post[i] = fi - (fi - feq[i]) / tau + src[i];
+      }
     }
+    for (int i = 0; i < q; i++)
+      fnew[i * N + neighbour(g, c, cv[i][0], cv[i][1], cv[i][2])] = post[i];
   }
 }
 
@@ -485,6 +614,26 @@ void API(orc_corotation_point)(const rt *Gu9, const rt *Q9, rt xi, rt *S9) {
 
 void API(orc_equilibrium_point)(int lattice, rt rho, const rt *u, rt *feq) {
   equilibrium(lattice, rho, u, feq);
+}
+
+/* one MRT collision at a point (after orc_set_mrt): post from f, rho, u, F */
+int API(orc_mrt_point)(int lattice, const rt *f, rt rho, const rt *u, const rt *F,
+                       rt *post) {
+  if (mrt_on != lattice + 1) return -1;
+  rt feq[19], ft[19];
+  equilibrium(lattice, rho, u, feq);
+  force_term(lattice, u, F, ft);
+  collide_mrt(lattice, f, feq, ft, post);
+  return 0;
+}
+
+/* the orthogonal moment rows after orc_set_mrt: v[k * q + i] */
+int API(orc_mrt_basis)(int lattice, double *v) {
+  if (mrt_on != lattice + 1) return -1;
+  int q = nvel(lattice);
+  for (int k = 0; k < q; k++)
+    for (int i = 0; i < q; i++) v[k * q + i] = mrt_v[k][i];
+  return q;
 }
 
 void API(orc_guo_point)(int lattice, rt tau, const rt *u, const rt *F,

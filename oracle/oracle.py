@@ -81,6 +81,37 @@ class Oracle:
                 conv.append(a)
         return fn(*conv)
 
+    def set_mrt(self, lattice, rates=None):
+        """MRT collision with q rates in the oracle's moment order (see
+        nlc_oracle.c), or BGK again with rates=None."""
+        fn = getattr(self._lib, "orc_set_mrt" + ("_cs" if self.cs else ""))
+        fn.restype = _I
+        r = None if rates is None else np.ascontiguousarray(rates, dtype=np.float64)
+        rc = fn(_I(lattice), _P(None) if r is None else _P(r.ctypes.data))
+        assert rc == 0
+        self._mrt_rates = r  # keep alive
+
+    def mrt_point(self, lattice, f, rho, u, F):
+        fn = getattr(self._lib, "orc_mrt_point" + ("_cs" if self.cs else ""))
+        fn.restype = _I
+        f = self._arr(f)
+        u = self._arr(u, (3,))
+        F = self._arr(F, (3,))
+        post = np.zeros_like(f)
+        rc = fn(_I(lattice), _P(f.ctypes.data), self._scalar(rho), _P(u.ctypes.data),
+                _P(F.ctypes.data), _P(post.ctypes.data))
+        assert rc == 0
+        return post
+
+    def mrt_basis(self, lattice):
+        fn = getattr(self._lib, "orc_mrt_basis" + ("_cs" if self.cs else ""))
+        fn.restype = _I
+        q = nvel(lattice)
+        v = np.zeros((q, q))
+        rc = fn(_I(lattice), _P(v.ctypes.data))
+        assert rc == q
+        return v
+
     def set_threads(self, n=0):
         """OpenMP threads of the cell loops (n <= 0: unchanged); returns the
         count in effect."""
