@@ -157,6 +157,27 @@ NLC_API int32_t nlc_count(const nlc_ctx* ctx);
  * Not used while timing is enabled. */
 NLC_API nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps);
 
+/* Collision operator of lattice inst.  The paper (Sec. 1.2.1) uses a
+ * multiple-relaxation-time (MRT) collision but gives neither its moment
+ * matrices nor its rates; the default is BGK with the single tau of
+ * nlc_params.  With rates != NULL the collision becomes
+ *   f* = f - M^-1 S M (f - f^eq + Ft/2) + Ft,   S = diag(rates),
+ * with Ft_i = w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F (the source term of
+ * Sec. 1.2.1 without its BGK prefactor) and M the orthogonal moment basis
+ * obtained by Gram-Schmidt (unit weights) from, in this order,
+ *   D2Q9 : 1, c^2, c^4, cx, c^2 cx, cy, c^2 cy, cx^2 - cy^2, cx cy
+ *   D3Q19: 1, c^2, c^4, cx, c^2 cx, cy, c^2 cy, cz, c^2 cz, 3cx^2 - c^2,
+ *          (3cx^2 - c^2) c^2, cy^2 - cz^2, (cy^2 - cz^2) c^2, cx cy, cy cz,
+ *          cx cz, cx (cy^2 - cz^2), cy (cz^2 - cx^2), cz (cx^2 - cy^2).
+ * rates: n = q host doubles in that order (copied; the rates of the
+ * conserved moments 1, cx, cy, cz have no effect), each in (0, 2); the
+ * shear viscosity is (1/s - 1/2)/3 for the rate s of the second-order
+ * traceless moments.  With every rate 1/tau this is the BGK step.
+ * rates == NULL returns to BGK.  Errors: NLC_EINVAL (instance, n, a rate
+ * outside (0, 2)).  nlc_adjoint returns NLC_EUNSUPPORTED while any lattice of
+ * the context uses MRT.  Synchronises the stream. */
+NLC_API nlc_status nlc_set_mrt(nlc_ctx* ctx, int32_t inst, const double* rates, int32_t n);
+
 /* Replaces the parameters of lattice inst (same checks as nlc_create);
  * the state is kept.  The step kernels (and captured step graphs) read the
  * parameters from device memory, so the change applies to the next step.

@@ -44,6 +44,7 @@ struct InstHost {
   Field<T> q[2];
   Field<T> u;
   int tz = 1;
+  T* mrt = nullptr;  // MRT coefficients s_k / |v_k|^2 on the device, or nullptr (BGK)
   // lazily allocated: unfused schedule, read-back staging, checkpoints
   T* pi = nullptr;
   Field<T> qp;
@@ -94,6 +95,7 @@ class Engine final : public EngineBase {
   nlc_status init() {
     const int n = args_.n;
     inst_.resize(n);
+    mrt_on_.assign(n, false);
     std::vector<InstDev<T>> dev(n);
     std::vector<CUtensorMap> qmaps(2 * n), umaps(n);
     std::vector<TileRef> tiles;
@@ -143,6 +145,7 @@ class Engine final : public EngineBase {
       dev[i].q[0] = I.q[0];
       dev[i].q[1] = I.q[1];
       dev[i].u = I.u;
+      dev[i].mrt = nullptr;
       dev[i].tz = I.tz;
     }
     if ((s = alloc(&bad_, 1)) || (s = alloc(&derr_, 1)) || (s = alloc(&insts_dev_, (size_t)n)) ||
@@ -179,6 +182,41 @@ class Engine final : public EngineBase {
       }
     }
     return device_error();
+  }
+
+  // MRT collision for lattice i with q rates in the moment order of
+  // lattice.cuh, or BGK again (rates == nullptr).  Captured step graphs hold
+  // the kernel variant, so they are dropped.
+  nlc_status set_mrt(int i, const double* rates) override {
+    InstHost<T>& I = inst_[i];
+    cudaStream_t st = args_.stream;
+    nlc_status s;
+    if (rates) {
+      if (!I.mrt && (s = alloc(&I.mrt, (size_t)Q))) return s;
+      constexpr MomentBasis<Lat> B = make_moment_basis<Lat>();
+      T a[Q];
+      for (int k = 0; k < Q; k++) a[k] = (T)(rates[k] / B.n2[k]);
+      NLC_CK(cudaMemcpyAsync(I.mrt, a, sizeof(a), cudaMemcpyHostToDevice, st));
+    }
+    const T* ptr = rates ? I.mrt : nullptr;
+    NLC_CK(cudaMemcpyAsync(&insts_dev_[i].mrt, &ptr, sizeof(ptr), cudaMemcpyHostToDevice, st));
+    NLC_CK(cudaStreamSynchronize(st));
+    mrt_on_[i] = rates != nullptr;
+    any_mrt_ = false;
+    for (bool b : mrt_on_) any_mrt_ = any_mrt_ || b;
+    drop_graphs();
+    return NLC_OK;
+  }
+
+  void drop_graphs() {
+    for (int c = 0; c < 2; c++)
+      if (graph_[c]) {
+        cudaGraphExecDestroy(graph_[c]);
+        graph_[c] = nullptr;
+        graph_len_[c] = 0;
+      }
+    for (const SweepGraph& e : sweep_graphs_) cudaGraphExecDestroy(e.exec);
+    sweep_graphs_.clear();
   }
 
   nlc_status set_params(int i, const nlc_params& q) override {
@@ -355,6 +393,10 @@ class Engine final : public EngineBase {
       return s;
     if (I.seg_grid <= 0) {
       err = "the adjoint needs cooperative launches of its segment kernels";
+      return NLC_EUNSUPPORTED;
+    }
+    if (any_mrt_) {
+      err = "the adjoint covers the BGK collision only";
       return NLC_EUNSUPPORTED;
     }
     if (!maps_ok_) {
@@ -739,7 +781,8 @@ class Engine final : public EngineBase {
       k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.pi, I.d, I.p);
       NLC_CK_LAUNCH("k_stress");
       const int e1 = mark();
-      k_lb<Lat, T><<<grid1(n), 256, 0, st>>>(I.g[a], I.g[b], I.pi, I.u, I.d, I.p);
+      k_lb<Lat, T><<<grid1(n), 256, 0, st>>>(I.g[a], I.g[b], I.pi, I.u, I.d, I.p,
+                                             mrt_on_[&I - inst_.data()] ? I.mrt : nullptr);
       NLC_CK_LAUNCH("k_lb");
       const int e2 = mark();
       k_predict<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.u, I.qp, I.r1, I.d, I.p);
@@ -764,7 +807,7 @@ class Engine final : public EngineBase {
     const int a = cur_;
     const int e0 = mark();
     cudaError_t e = launch_fused_lb<Lat, T>(insts_dev_, qmaps_dev_, tiles_dev_, ntiles_, a,
-                                            derr_, st);
+                                            derr_, st, any_mrt_);
     if (e != cudaSuccess) {
       err = std::string("fused lb kernel: ") + cudaGetErrorString(e);
       return NLC_ECUDA;
@@ -871,6 +914,8 @@ class Engine final : public EngineBase {
   };
   std::vector<SweepGraph> sweep_graphs_;  // the adjoint's forward sweeps
   cudaStream_t side_stream_ = nullptr;    // adjoint segment records
+  std::vector<bool> mrt_on_;              // per lattice: MRT collision
+  bool any_mrt_ = false;
   cudaEvent_t seg_ev_[5] = {};
   int graph_len_[2] = {0, 0};
 };

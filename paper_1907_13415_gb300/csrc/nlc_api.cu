@@ -159,6 +159,22 @@ nlc_status nlc_set_params(nlc_ctx* ctx, int32_t inst, const nlc_params* params) 
   return NLC_OK;
 }
 
+nlc_status nlc_set_mrt(nlc_ctx* ctx, int32_t inst, const double* rates, int32_t n) {
+  if (!ctx) return NLC_EINVAL;
+  if (inst < 0 || inst >= (int32_t)ctx->grids.size())
+    return fail(ctx, NLC_EINVAL, "instance out of range");
+  if (rates) {
+    const int32_t q = ctx->grids[inst].lattice == NLC_D2Q9 ? 9 : 19;
+    if (n != q) return fail(ctx, NLC_EINVAL, "one rate per velocity (moment) is needed");
+    for (int32_t k = 0; k < n; k++)
+      if (!(rates[k] > 0.0 && rates[k] < 2.0))
+        return fail(ctx, NLC_EINVAL, "relaxation rates must lie in (0, 2)");
+  }
+  nlc_status st = ctx->eng->set_mrt(inst, rates);
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  return NLC_OK;
+}
+
 nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps) {
   if (!ctx) return NLC_EINVAL;
   if (steps < 0) return fail(ctx, NLC_EINVAL, "negative graph length");

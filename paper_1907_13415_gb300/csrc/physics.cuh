@@ -220,6 +220,51 @@ __host__ __device__ __forceinline__ void collide_bgk(T g[Lat::Q], T rho, const T
   }
 }
 
+// Multiple-relaxation-time collision with the source term in moment space
+// (Sec. 1.2.1 names MRT; its rates are the caller's), on deviations:
+//   y = g - g^eq + Ft/2,  g* = g + Ft - sum_k v_k a_k (v_k . y),
+// with the moment rows v_k of lattice.cuh, a_k = s_k / |v_k|^2 (a[k]), and
+// Ft_i = w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F the source term without its
+// BGK prefactor.  Equal rates s_k = 1/tau give collide_bgk.  The conserved
+// rows (mass, momentum) have v_k . y = 0 and are skipped.
+template <class Lat, class T>
+__host__ __device__ __forceinline__ void collide_mrt(T g[Lat::Q], T rho, const T u[3],
+                                                     const T F[3], const Par<T>& p,
+                                                     const T* a) {
+  constexpr MomentBasis<Lat> B = make_moment_basis<Lat>();
+  const T uu = u[0] * u[0] + u[1] * u[1] + (Lat::DIM == 3 ? u[2] * u[2] : T(0));
+  const T uF = u[0] * F[0] + u[1] * F[1] + (Lat::DIM == 3 ? u[2] * F[2] : T(0));
+  const T drho = rho - p.rho0;
+  T y[Lat::Q], ft[Lat::Q];
+#pragma unroll
+  for (int i = 0; i < Lat::Q; i++) {
+    T cu = T(Lat::c(i, 0)) * u[0] + T(Lat::c(i, 1)) * u[1];
+    T cF = T(Lat::c(i, 0)) * F[0] + T(Lat::c(i, 1)) * F[1];
+    if (Lat::DIM == 3) {
+      cu += T(Lat::c(i, 2)) * u[2];
+      cF += T(Lat::c(i, 2)) * F[2];
+    }
+    const T w = T(Lat::w(i));
+    const T geq = w * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+    ft[i] = w * (T(3) * (cF - uF) + T(9) * cu * cF);
+    y[i] = g[i] - geq + T(0.5) * ft[i];
+  }
+#pragma unroll
+  for (int i = 0; i < Lat::Q; i++) g[i] += ft[i];
+#pragma unroll
+  for (int k = 0; k < Lat::Q; k++) {
+    if (moment_conserved<Lat>(k)) continue;
+    T m = T(0);
+#pragma unroll
+    for (int i = 0; i < Lat::Q; i++)
+      if (B.v[k][i] != 0.0) m += T(B.v[k][i]) * y[i];
+    m *= a[k];
+#pragma unroll
+    for (int i = 0; i < Lat::Q; i++)
+      if (B.v[k][i] != 0.0) g[i] -= T(B.v[k][i]) * m;
+  }
+}
+
 // rho = rho0 + sum g, u = (sum c g + F/2) / rho  (Eq. 6; sum c w rho0 = 0)
 template <class Lat, class T>
 __host__ __device__ __forceinline__ void moments(const T g[Lat::Q], const T F[3],

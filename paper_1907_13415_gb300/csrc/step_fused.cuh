@@ -86,6 +86,7 @@ struct InstDev {
   T* g[2];         // populations, ping-pong
   Field<T> q[2];   // Q, ping-pong
   Field<T> u;      // u^n handed from the lb to the Beris-Edwards kernel
+  const T* mrt;    // Q coefficients s_k / |v_k|^2 of the MRT collision, or nullptr
   int tz;          // z planes per tile (1 on a single plane)
 };
 
@@ -191,7 +192,9 @@ struct CellPops<Lat, float> {
   float2 gp[(Lat::Q - 1) / 2];
 };
 
-template <class Lat, class T>
+// MRT: the multiple-relaxation-time collision (physics.cuh: collide_mrt);
+// a lattice of the launch without its own rates gets the BGK rates 1/tau
+template <class Lat, class T, bool MRT>
 __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     k_fused_lb(const InstDev<T>* __restrict__ insts,
                const CUtensorMap* __restrict__ qmaps,
@@ -225,6 +228,13 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
   auto qpar = [&](int z) { return (uint32_t)(((z - zq0) / C::NSQ) & 1); };
   auto pslot = [&](int z) { return (z - zp0) % C::NSP; };
 
+  __shared__ T s_mrt[MRT ? Lat::Q : 1];
+  if constexpr (MRT) {
+    if (tid < Lat::Q) {
+      constexpr MomentBasis<Lat> B = make_moment_basis<Lat>();
+      s_mrt[tid] = I.mrt ? I.mrt[tid] : T(double(p.inv_tau) / B.n2[tid]);
+    }
+  }
   if (tid == 0) {
     for (int s = 0; s < C::NSQ; s++) mbar_init(&bars[s], 1);
     mbar_fence_init();
@@ -316,7 +326,24 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     const unsigned o = (unsigned)(z * nxy + rowy[1] + x);
     const unsigned n32 = (unsigned)d.n;
     T rho, u[3];
-    if constexpr (kPacked) {
+    if constexpr (MRT) {
+      T g[Lat::Q];
+      if constexpr (kPacked) {
+        g[0] = gn.g0;
+#pragma unroll
+        for (int q = 0; q < NP; q++) {
+          g[pair_first<Lat>(q)] = gn.gp[q].x;
+          g[Lat::opp(pair_first<Lat>(q))] = gn.gp[q].y;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < Lat::Q; i++) g[i] = gn.g[i];
+      }
+      moments<Lat, T>(g, F, p, rho, u);
+      collide_mrt<Lat, T>(g, rho, u, F, p, s_mrt);
+#pragma unroll
+      for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = g[i];
+    } else if constexpr (kPacked) {
       float g0 = gn.g0, drho;
       float2 gp[NP];
 #pragma unroll
@@ -671,15 +698,24 @@ inline cudaError_t set_smem(K kernel, size_t bytes, unsigned long long* done_mas
   return e;
 }
 
+template <class Lat, class T, bool MRT>
+cudaError_t launch_fused_lb_as(const InstDev<T>* insts, const CUtensorMap* qmaps,
+                               const TileRef* tiles, int ntiles, int cur, unsigned* err,
+                               cudaStream_t st) {
+  static unsigned long long configured = 0;
+  cudaError_t e = set_smem(k_fused_lb<Lat, T, MRT>, LbCfg<Lat, T>::bytes, &configured);
+  if (e != cudaSuccess) return e;
+  k_fused_lb<Lat, T, MRT><<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(
+      insts, qmaps, tiles, cur, err);
+  return cudaGetLastError();
+}
+
 template <class Lat, class T>
 cudaError_t launch_fused_lb(const InstDev<T>* insts, const CUtensorMap* qmaps,
                             const TileRef* tiles, int ntiles, int cur, unsigned* err,
-                            cudaStream_t st) {
-  static unsigned long long configured = 0;
-  cudaError_t e = set_smem(k_fused_lb<Lat, T>, LbCfg<Lat, T>::bytes, &configured);
-  if (e != cudaSuccess) return e;
-  k_fused_lb<Lat, T><<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(insts, qmaps, tiles, cur, err);
-  return cudaGetLastError();
+                            cudaStream_t st, bool mrt) {
+  return mrt ? launch_fused_lb_as<Lat, T, true>(insts, qmaps, tiles, ntiles, cur, err, st)
+             : launch_fused_lb_as<Lat, T, false>(insts, qmaps, tiles, ntiles, cur, err, st);
 }
 
 template <class Lat, class T>

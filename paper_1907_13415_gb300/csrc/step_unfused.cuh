@@ -135,16 +135,21 @@ __device__ __forceinline__ void pull(const T* __restrict__ gin, const Dims& d,
   }
 }
 
+// mrt: the Q coefficients s_k / |v_k|^2 of the MRT collision, or nullptr
+// for BGK
 template <class Lat, class T>
 __device__ __forceinline__ void lb_at(const T* __restrict__ gin, T* __restrict__ gout,
                                       const T* __restrict__ Pi, const Field<T>& U,
-                                      const Dims& d, const Par<T>& p, int64_t idx, int x,
-                                      int y, int z) {
+                                      const Dims& d, const Par<T>& p, const T* mrt,
+                                      int64_t idx, int x, int y, int z) {
   T F[3], g[Lat::Q], rho, u[3];
   force_at<T, Lat::DIM>(Pi, d, x, y, z, F);
   pull<Lat, T>(gin, d, x, y, z, g);
   moments<Lat, T>(g, F, p, rho, u);
-  collide_bgk<Lat, T>(g, rho, u, F, p);
+  if (mrt)
+    collide_mrt<Lat, T>(g, rho, u, F, p, mrt);
+  else
+    collide_bgk<Lat, T>(g, rho, u, F, p);
 #pragma unroll
   for (int i = 0; i < Lat::Q; i++) gout[(int64_t)i * d.n + idx] = g[i];
   store_with_images<T, Lat::DIM, Lat::DIM>(U, d, x, y, z, u);
@@ -154,10 +159,11 @@ template <class Lat, class T>
 __global__ void __launch_bounds__(256) k_lb(const T* __restrict__ gin,
                                             T* __restrict__ gout,
                                             const T* __restrict__ Pi,
-                                            Field<T> U, Dims d, Par<T> p) {
+                                            Field<T> U, Dims d, Par<T> p,
+                                            const T* __restrict__ mrt) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (decode(d, idx, x, y, z)) lb_at<Lat, T>(gin, gout, Pi, U, d, p, idx, x, y, z);
+  if (decode(d, idx, x, y, z)) lb_at<Lat, T>(gin, gout, Pi, U, d, p, mrt, idx, x, y, z);
 }
 
 template <class Lat, class T>

@@ -95,6 +95,7 @@ def load(build_if_missing=True):
         "nlc_set_graph": ([P, I32], I32),
         "nlc_set_check": ([P, I32], I32),
         "nlc_set_params": ([P, I32, ctypes.POINTER(nlc_params)], I32),
+        "nlc_set_mrt": ([P, I32, P, I32], I32),
         "nlc_set_schedule": ([P, I32], I32),
         "nlc_set_fields": ([P, I32, P, P, P], I32),
         "nlc_get_fields": ([P, I32, P, P, P], I32),
@@ -124,7 +125,7 @@ def load(build_if_missing=True):
 
 def exported_symbols():
     return ["nlc_create", "nlc_create_batch", "nlc_count", "nlc_set_graph", "nlc_set_check",
-            "nlc_set_params",
+            "nlc_set_params", "nlc_set_mrt",
             "nlc_set_schedule", "nlc_set_fields",
             "nlc_get_fields", "nlc_get_populations", "nlc_step",
             "nlc_observables", "nlc_last_error", "nlc_destroy",
@@ -183,6 +184,16 @@ def nlc_count(ctx):
 def nlc_set_params(ctx, inst, params):
     P = params if isinstance(params, nlc_params) else _params(params)
     _check(ctx, load().nlc_set_params(ctx, inst, ctypes.byref(P)))
+
+
+def nlc_set_mrt(ctx, inst, rates=None):
+    """MRT collision with q rates in the library's moment order (nlc.h), or
+    BGK again with rates=None."""
+    if rates is None:
+        _check(ctx, load().nlc_set_mrt(ctx, inst, None, 0))
+        return
+    r = np.ascontiguousarray(rates, dtype=np.float64)
+    _check(ctx, load().nlc_set_mrt(ctx, inst, _ptr(r), int(r.size)))
 
 
 def nlc_set_check(ctx, every):
@@ -327,6 +338,9 @@ class Batch:
     def __len__(self):
         return len(self.shapes)
 
+    def set_mrt(self, i, rates=None):
+        nlc_set_mrt(self.ctx, i, rates)
+
     def set_fields(self, i, Q5, rho=None, u=None):
         sh = self.shapes[i]
         nlc_set_fields(self.ctx, i, _f64(Q5, (5,) + sh), _f64(rho, sh),
@@ -425,6 +439,9 @@ class Simulation:
 
     def load_state(self, data):
         nlc_load(self.ctx, data)
+
+    def set_mrt(self, rates=None):
+        nlc_set_mrt(self.ctx, 0, rates)
 
     def set_graph(self, steps):
         nlc_set_graph(self.ctx, steps)

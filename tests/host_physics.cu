@@ -52,6 +52,36 @@ int hp_collide(int lattice, double* g, double rho, const double* u, const double
   collide_bgk<LatD3Q19, double>(g, rho, uu, FF, pp);
   return 19;
 }
+// MRT collision with the source term on deviations g (rho0 = 1); a[k] are
+// the per-moment coefficients s_k / |v_k|^2 (filled here from rates s_k)
+int hp_collide_mrt(int lattice, double* g, double rho, const double* u, const double* F,
+                   const double* p, const double* rates) {
+  Par<double> pp = par(p);
+  double uu[3] = {u[0], u[1], u[2]}, FF[3] = {F[0], F[1], F[2]}, a[19];
+  if (lattice == 0) {
+    constexpr MomentBasis<LatD2Q9> B = make_moment_basis<LatD2Q9>();
+    for (int k = 0; k < 9; k++) a[k] = rates[k] / B.n2[k];
+    collide_mrt<LatD2Q9, double>(g, rho, uu, FF, pp, a);
+    return 9;
+  }
+  constexpr MomentBasis<LatD3Q19> B = make_moment_basis<LatD3Q19>();
+  for (int k = 0; k < 19; k++) a[k] = rates[k] / B.n2[k];
+  collide_mrt<LatD3Q19, double>(g, rho, uu, FF, pp, a);
+  return 19;
+}
+// the library's moment rows v[k * q + i] in its own velocity order
+int hp_moment_basis(int lattice, double* v) {
+  if (lattice == 0) {
+    constexpr MomentBasis<LatD2Q9> B = make_moment_basis<LatD2Q9>();
+    for (int k = 0; k < 9; k++)
+      for (int i = 0; i < 9; i++) v[k * 9 + i] = B.v[k][i];
+    return 9;
+  }
+  constexpr MomentBasis<LatD3Q19> B = make_moment_basis<LatD3Q19>();
+  for (int k = 0; k < 19; k++)
+    for (int i = 0; i < 19; i++) v[k * 19 + i] = B.v[k][i];
+  return 19;
+}
 void hp_lattice(int lattice, int* c, double* w) {
   const int q = lattice == 0 ? 9 : 19;
   for (int i = 0; i < q; i++) {

@@ -28,6 +28,9 @@ def hp(tmp_path_factory):
         getattr(lib, name).restype = None
     lib.hp_collide.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.hp_collide_mrt.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]
     lib.hp_corotation.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                   ctypes.c_void_p]
     return lib
@@ -140,6 +143,45 @@ def test_collision_with_source(hp, orc, lattice):
         S = orc.guo_point(lattice, p[5], u, F)
         ref = f - (f - feq) / p[5] + S
         assert np.allclose(g + w, ref[perm], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_mrt_collision_matches_oracle(hp, orc, lattice):
+    """The library's MRT collision (its own moment rows, its own velocity
+    order) against the oracle's, for random rates; the two moment bases are
+    the same rows up to the velocity order."""
+    q = 9 if lattice == 0 else 19
+    c = np.zeros((q, 3), dtype=np.int32)
+    w = np.zeros(q)
+    hp.hp_lattice(lattice, P(c), P(w))
+    co, wo = orc.lattice(lattice)
+    perm = [int(np.where((co == cv).all(axis=1))[0][0]) for cv in c]
+    rng = np.random.default_rng(12)
+    rates = rng.uniform(0.6, 1.9, size=q)
+    orc.set_mrt(lattice, rates)
+    try:
+        v = np.zeros(q * q)
+        hp.hp_moment_basis(lattice, P(v))
+        assert np.allclose(v.reshape(q, q), orc.mrt_basis(lattice)[:, perm], atol=1e-13)
+        d = 2 if lattice == 0 else 3
+        for _ in range(30):
+            p = params(rng)
+            rho = 1 + 0.05 * rng.normal()
+            u = np.zeros(3)
+            u[:d] = rng.normal(scale=0.05, size=d)
+            F = np.zeros(3)
+            F[:d] = rng.normal(scale=1e-3, size=d)
+            f = orc.equilibrium_point(lattice, rho, u) + rng.normal(scale=1e-3, size=q)
+            # rho and u of Eq. 6 from f itself: then the mass and momentum
+            # rows of f - feq + Ft/2 vanish, as in every step
+            rho = f.sum()
+            u = (co.T @ f + F / 2) / rho
+            g = f[perm] - w
+            hp.hp_collide_mrt(lattice, P(g), rho, P(u), P(F), P(p), P(rates))
+            ref = orc.mrt_point(lattice, f, rho, u, F)
+            assert np.allclose(g + w, ref[perm], rtol=0, atol=2e-15)
+    finally:
+        orc.set_mrt(lattice, None)
 
 
 # piece id: (inputs, outputs)
