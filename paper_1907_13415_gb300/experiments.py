@@ -135,6 +135,36 @@ def paper_circle(angle_deg=0.0, steps=35000, every=1000, gamma=2.707681,
             "max_abs_vorticity": float(np.abs(om).max())}
 
 
+def tanh_fit(profile, x_guess, lam=None, s_n=None, window=6.0):
+    """FP64 least-squares fit of Eq. 7, S = S_n/2 [1 - tanh((x - x_i)/(2 lambda))],
+    to a mean S(x) profile around one descending interface.  x_i is always
+    free; S_n and lambda are fitted unless given.  Returns (x_i, S_n, lambda,
+    rms residual)."""
+    from scipy.optimize import least_squares
+    prof = np.asarray(profile, dtype=np.float64)
+    x = np.arange(prof.size, dtype=np.float64)
+    lam0 = 2.0 if lam is None else lam
+    sel = np.abs(x - x_guess) < window * lam0
+    xs, ys = x[sel], prof[sel]
+
+    def unpack(v):
+        k = 1
+        sn = s_n if s_n is not None else v[k]
+        k += s_n is None
+        la = lam if lam is not None else v[k]
+        return v[0], sn, la
+
+    def resid(v):
+        xi, sn, la = unpack(v)
+        return sn / 2 * (1 - np.tanh((xs - xi) / (2 * la))) - ys
+
+    v0 = [x_guess] + ([] if s_n is not None else [max(ys.max(), 1e-6)]) + \
+         ([] if lam is not None else [lam0])
+    r = least_squares(resid, v0, method="lm", xtol=1e-15, ftol=1e-15)
+    xi, sn, la = unpack(r.x)
+    return float(xi), float(sn), float(la), float(np.sqrt(np.mean(r.fun ** 2)))
+
+
 def flat_paper(gamma=2.7, steps=350000, lx=200, ly=8, every=10000):
     """Sec. 2.1 / Fig. 1 with the paper's parameters: a nematic slab in the
     middle of an lx x ly lattice (director along y), run to t = 350000.
@@ -169,10 +199,12 @@ def flat_paper(gamma=2.7, steps=350000, lx=200, ly=8, every=10000):
     xs = np.array(xs)
     half = len(xs) // 2
     v = float(np.polyfit(np.arange(half, len(xs)) * every, xs[half:], 1)[0]) if len(xs) > 3 else 0.0
+    xf, snf, laf, rms = tanh_fit(prof, xr)
     return {"experiment": "flat interface (paper parameters)", "gamma": gamma,
             "lattice": [lx, ly], "steps": steps, "x_iface": float(xr),
             "velocity": v, "max_u": float(o["max_u"]),
-            "eq7_max_deviation": float(best[0]), "eq7_fit_x_iface": float(best[1])}
+            "eq7_max_deviation": float(best[0]), "eq7_fit_x_iface": float(best[1]),
+            "tanh_fit": {"x_i": xf, "S_n": snf, "lambda": laf, "rms": rms}}
 
 
 def sweep(steps=50000, every=2500, graph_steps=50):
@@ -201,7 +233,9 @@ def sweep(steps=50000, every=2500, graph_steps=50):
         v_est = 10 / 9 * w.params["Gamma"] * w.params["A0"] * lam * (g - 2.7)
         out.append({"gamma": g, "lattice": [w.shape[2], w.shape[1]],
                     "velocity": v, "allen_cahn_estimate": v_est,
-                    "interface_survives": ok})
+                    "interface_survives": ok,
+                    # below the spinodal 8/3 the bulk nematic is unstable
+                    "nematic_unstable": bool(g < 8.0 / 3.0)})
     b.close()
     return {"experiment": "temperature sweep", "steps": steps, "instances": out}
 
