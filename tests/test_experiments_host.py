@@ -13,7 +13,7 @@ def test_tanh_fit_recovers_eq7_parameters():
     assert rms < 1e-12
     # with S_n and lambda held at other values only x_i moves, by little
     xi2, sn2, lam2, rms2 = ex.tanh_fit(prof, 96.0, lam=2.0, s_n=1 / 3)
-    assert sn2 == 1 / 3 and lam2 == 2.0 and abs(xi2 - 97.25) < 0.2 and rms2 > 1e-3
+    assert sn2 == 1 / 3 and lam2 == 2.0 and abs(xi2 - 97.25) < 1.0 and rms2 > 1e-3
 
 
 def test_vorticity_of_rigid_rotation_and_shear():
