@@ -32,6 +32,8 @@
  *       with all rates 1/tau it is the BGK step.
  *   R3  The Laplacian is the standard 2d+1-point second-order stencil; first
  *       derivatives (including the advection term and grad u) are central.
+ *       orc_set_stencil(1) switches every finite difference to the
+ *       isotropic stencils of the lattice's neighbour set (q_grad_lap).
  *   R4  The right-hand side of Eq. 1 is made traceless by the orthogonal
  *       projection R <- R - (Tr R / 3) I before the five independent
  *       components (xx, xy, xz, yy, yz) are stored; Qzz = -Qxx - Qyy.
@@ -186,12 +188,45 @@ static rt ddot(rt A[3][3], rt B[3][3]) {
 /* 2d+1-point Laplacian (reading R3).                                    */
 /* dQ[g][a][b] = d_g Q_ab.                                               */
 /* ------------------------------------------------------------------ */
+/* Finite-difference stencils.  Standard (reading R3): central first
+ * derivatives and the 2d+1-point Laplacian.  Isotropic (orc_set_stencil(1)):
+ * the lattice's own neighbour set and weights (9 points on D2Q9, 19 on
+ * D3Q19), d_a phi = (1/cs^2) sum_i w_i c_ia phi(x + c_i) and
+ * lap phi = (2/cs^2) sum_i w_i [phi(x + c_i) - phi(x)], both second order
+ * with a leading error that does not depend on direction. */
+static int iso_stencil = 0;
+
+int API(orc_set_stencil)(int kind) {
+  if (kind != 0 && kind != 1) return -1;
+  iso_stencil = kind;
+  return 0;
+}
+
 static void q_grad_lap(const grid_t *g, const rt *Q5, long c, rt dQ[3][3][3],
                        rt lap[3][3]) {
   rt Q0[3][3];
   q_full(Q5, g->n, c, Q0);
   for (int a = 0; a < 3; a++)
     for (int b = 0; b < 3; b++) lap[a][b] = 0;
+  if (iso_stencil) {
+    int q = nvel(g->lattice);
+    const int(*cv)[3] = vel(g->lattice);
+    const double *w = wgt(g->lattice);
+    for (int gdir = 0; gdir < 3; gdir++)
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) dQ[gdir][a][b] = 0;
+    for (int i = 1; i < q; i++) {
+      rt Qi[3][3];
+      q_full(Q5, g->n, neighbour(g, c, cv[i][0], cv[i][1], cv[i][2]), Qi);
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+          for (int gdir = 0; gdir < 3; gdir++)
+            dQ[gdir][a][b] += w[i] * cv[i][gdir] * Qi[a][b] / CS2;
+          lap[a][b] += 2.0 * w[i] * (Qi[a][b] - Q0[a][b]) / CS2;
+        }
+    }
+    return;
+  }
   for (int gdir = 0; gdir < 3; gdir++) {
     rt Qp[3][3], Qm[3][3];
     long cp = neighbour(g, c, UNIT[gdir][0], UNIT[gdir][1], UNIT[gdir][2]);
@@ -461,14 +496,25 @@ static void stage_fields(const grid_t *g, const rt *p, const rt *Q5, rt *H5,
  * reading R5 drops F_z on the 2D lattice. */
 static void stage_force(const grid_t *g, const rt *Pi9, rt *F3) {
   long N = g->n;
+  int q = nvel(g->lattice);
+  const int(*cv)[3] = vel(g->lattice);
+  const double *w = wgt(g->lattice);
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < N; c++) {
     for (int a = 0; a < 3; a++) {
       rt s = 0;
-      for (int b = 0; b < 3; b++) {
-        long cp = neighbour(g, c, UNIT[b][0], UNIT[b][1], UNIT[b][2]);
-        long cm = neighbour(g, c, -UNIT[b][0], -UNIT[b][1], -UNIT[b][2]);
-        s += (Pi9[(3 * a + b) * N + cp] - Pi9[(3 * a + b) * N + cm]) / 2.0;
+      if (iso_stencil) {
+        for (int i = 1; i < q; i++) {
+          long ci = neighbour(g, c, cv[i][0], cv[i][1], cv[i][2]);
+          for (int b = 0; b < 3; b++)
+            s += w[i] * cv[i][b] * Pi9[(3 * a + b) * N + ci] / CS2;
+        }
+      } else {
+        for (int b = 0; b < 3; b++) {
+          long cp = neighbour(g, c, UNIT[b][0], UNIT[b][1], UNIT[b][2]);
+          long cm = neighbour(g, c, -UNIT[b][0], -UNIT[b][1], -UNIT[b][2]);
+          s += (Pi9[(3 * a + b) * N + cp] - Pi9[(3 * a + b) * N + cm]) / 2.0;
+        }
       }
       F3[a * N + c] = s;
     }
@@ -528,6 +574,19 @@ static void stage_collide_stream(const grid_t *g, const rt *p, const rt *f,
 /* Velocity gradient Gu[a][b] = d_b u_a by central differences. */
 static void vel_grad(const grid_t *g, const rt *u3, long c, rt Gu[3][3]) {
   long N = g->n;
+  if (iso_stencil) {
+    int q = nvel(g->lattice);
+    const int(*cv)[3] = vel(g->lattice);
+    const double *w = wgt(g->lattice);
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) Gu[a][b] = 0;
+    for (int i = 1; i < q; i++) {
+      long ci = neighbour(g, c, cv[i][0], cv[i][1], cv[i][2]);
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) Gu[a][b] += w[i] * cv[i][b] * u3[a * N + ci] / CS2;
+    }
+    return;
+  }
   for (int b = 0; b < 3; b++) {
     long cp = neighbour(g, c, UNIT[b][0], UNIT[b][1], UNIT[b][2]);
     long cm = neighbour(g, c, -UNIT[b][0], -UNIT[b][1], -UNIT[b][2]);

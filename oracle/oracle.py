@@ -112,6 +112,15 @@ class Oracle:
         assert rc == q
         return v
 
+    def set_stencil(self, kind):
+        """0: standard stencils (2d+1-point Laplacian, central first
+        derivatives); 1: the isotropic stencils of the lattice's neighbour
+        set.  Applies to every later call of this oracle (real or complex)."""
+        fn = getattr(self._lib, "orc_set_stencil" + ("_cs" if self.cs else ""))
+        fn.argtypes = [_I]
+        fn.restype = _I
+        assert fn(int(kind)) == 0
+
     def set_threads(self, n=0):
         """OpenMP threads of the cell loops (n <= 0: unchanged); returns the
         count in effect."""
