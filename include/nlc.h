@@ -157,6 +157,21 @@ NLC_API int32_t nlc_count(const nlc_ctx* ctx);
  * Not used while timing is enabled. */
 NLC_API nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps);
 
+/* Finite-difference stencils of the context (every lattice).
+ * NLC_STENCIL_STANDARD (default): central first derivatives and the
+ * 2d+1-point Laplacian (Sec. 1.2.2, second order).  NLC_STENCIL_ISOTROPIC:
+ * the lattice's own neighbour set and weights (9 points on D2Q9, 19 on
+ * D3Q19), d_a v = 3 sum_i w_i c_ia v(x + c_i) and
+ * lap v = 6 sum_i w_i [v(x + c_i) - v(x)], also second order but with a
+ * leading error that does not depend on direction -- the remedy Sec. 2.2
+ * names for the spurious currents.  Applies to every derivative of the
+ * step (grad Q, lap Q, grad u, div Pi) and to the force in the observables;
+ * nlc_observables_static keeps the standard stencils.  nlc_adjoint returns
+ * NLC_EUNSUPPORTED with the isotropic stencils.  Errors: NLC_EINVAL. */
+#define NLC_STENCIL_STANDARD 0
+#define NLC_STENCIL_ISOTROPIC 1
+NLC_API nlc_status nlc_set_stencil(nlc_ctx* ctx, int32_t kind);
+
 /* Collision operator of lattice inst.  The paper (Sec. 1.2.1) uses a
  * multiple-relaxation-time (MRT) collision but gives neither its moment
  * matrices nor its rates; the default is BGK with the single tau of

@@ -120,14 +120,14 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_record(SegArgs<T> a) {
   unsigned gen = 0;
   for (int j = 0; j < a.len; j++) {
     const Field<T> Q = S.q(j), U = S.u(j), QP = S.qp(j);
-    NLC_FOR_CELLS(d) stress_at<Lat, T>(Q, S.pi(j), d, p, idx, x, y, z);
+    NLC_FOR_CELLS(d) stress_at<Lat, T>(Q, S.pi(j), d, p, false, idx, x, y, z);
     if (!grid_sync(a.bar, gen, a.err)) return;
     NLC_FOR_CELLS(d)
-    lb_at<Lat, T>(S.g(j), S.g(j + 1), S.pi(j), U, d, p, nullptr, idx, x, y, z);
+    lb_at<Lat, T>(S.g(j), S.g(j + 1), S.pi(j), U, d, p, nullptr, false, idx, x, y, z);
     if (!grid_sync(a.bar, gen, a.err)) return;
-    NLC_FOR_CELLS(d) predict_at<Lat, T>(Q, U, QP, a.r1, d, p, idx, x, y, z);
+    NLC_FOR_CELLS(d) predict_at<Lat, T>(Q, U, QP, a.r1, d, p, false, idx, x, y, z);
     if (!grid_sync(a.bar, gen, a.err)) return;
-    NLC_FOR_CELLS(d) correct_at<Lat, T>(Q, QP, a.r1, U, S.q(j + 1), d, p, idx, x, y, z);
+    NLC_FOR_CELLS(d) correct_at<Lat, T>(Q, QP, a.r1, U, S.q(j + 1), d, p, false, idx, x, y, z);
     if (!grid_sync(a.bar, gen, a.err)) return;
   }
 }

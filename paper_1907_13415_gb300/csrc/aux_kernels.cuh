@@ -56,12 +56,15 @@ __global__ void __launch_bounds__(256) k_set_fields(
 template <class Lat, class T>
 __global__ void __launch_bounds__(256) k_moments_out(
     const T* __restrict__ gin, const T* __restrict__ Pi, Dims d, Par<T> p,
-    double* __restrict__ rho_out, double* __restrict__ u_out) {
+    double* __restrict__ rho_out, double* __restrict__ u_out, bool iso) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (!decode(d, idx, x, y, z)) return;
   T F[3], g[Lat::Q], rho, u[3];
-  force_at<T, Lat::DIM>(Pi, d, x, y, z, F);
+  if (iso)
+    force_at_iso<Lat, T>(Pi, d, x, y, z, F);
+  else
+    force_at<T, Lat::DIM>(Pi, d, x, y, z, F);
   pull<Lat, T>(gin, d, x, y, z, g);
   moments<Lat, T>(g, F, p, rho, u);
   rho_out[idx] = (double)rho;

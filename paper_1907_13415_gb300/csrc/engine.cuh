@@ -219,6 +219,13 @@ class Engine final : public EngineBase {
     sweep_graphs_.clear();
   }
 
+  // stencils of every lattice: standard (false) or isotropic (true)
+  nlc_status set_stencil(bool iso) override {
+    if (iso != iso_) drop_graphs();
+    iso_ = iso;
+    return NLC_OK;
+  }
+
   nlc_status set_params(int i, const nlc_params& q) override {
     InstHost<T>& I = inst_[i];
     I.p.A0 = (T)q.A0;
@@ -395,8 +402,8 @@ class Engine final : public EngineBase {
       err = "the adjoint needs cooperative launches of its segment kernels";
       return NLC_EUNSUPPORTED;
     }
-    if (any_mrt_) {
-      err = "the adjoint covers the BGK collision only";
+    if (any_mrt_ || iso_) {
+      err = "the adjoint covers the BGK collision with the standard stencils only";
       return NLC_EUNSUPPORTED;
     }
     if (!maps_ok_) {
@@ -427,7 +434,7 @@ class Engine final : public EngineBase {
     int lc = 0;  // lQ[lc], lG[lc] hold the adjoint of the current state
     {
       const unsigned gb = grid1(n);
-      k_stress<Lat, T><<<gb, 256, 0, st>>>(I.q[cur_], I.pi, I.d, I.p);
+      k_stress<Lat, T><<<gb, 256, 0, st>>>(I.q[cur_], I.pi, I.d, I.p, false);
       k_adj_seed_q<T><<<gb, 256, 0, st>>>(I.q[cur_], (T)cR, I.lQ[lc], I.d);
       k_adj_lb<Lat, T><<<gb, 256, 0, st>>>(I.g[cur_], I.pi, nullptr, nullptr, nullptr,
                                            I.lG[lc], I.lF, I.d, I.p, (T)cu);
@@ -762,10 +769,10 @@ class Engine final : public EngineBase {
   nlc_status moments_to_stage(InstHost<T>& I) {
     const int64_t n = I.d.n;
     cudaStream_t st = args_.stream;
-    k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[cur_], I.pi, I.d, I.p);
+    k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[cur_], I.pi, I.d, I.p, iso_);
     NLC_CK_LAUNCH("k_stress");
     k_moments_out<Lat, T><<<grid1(n), 256, 0, st>>>(I.g[cur_], I.pi, I.d, I.p, I.stage + 5 * n,
-                                                     I.stage + 6 * n);
+                                                     I.stage + 6 * n, iso_);
     NLC_CK_LAUNCH("k_moments_out");
     return NLC_OK;
   }
@@ -778,17 +785,18 @@ class Engine final : public EngineBase {
     for (auto& I : inst_) {
       const int64_t n = I.d.n;
       const int e0 = mark();
-      k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.pi, I.d, I.p);
+      k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.pi, I.d, I.p, iso_);
       NLC_CK_LAUNCH("k_stress");
       const int e1 = mark();
       k_lb<Lat, T><<<grid1(n), 256, 0, st>>>(I.g[a], I.g[b], I.pi, I.u, I.d, I.p,
-                                             mrt_on_[&I - inst_.data()] ? I.mrt : nullptr);
+                                             mrt_on_[&I - inst_.data()] ? I.mrt : nullptr, iso_);
       NLC_CK_LAUNCH("k_lb");
       const int e2 = mark();
-      k_predict<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.u, I.qp, I.r1, I.d, I.p);
+      k_predict<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.u, I.qp, I.r1, I.d, I.p, iso_);
       NLC_CK_LAUNCH("k_predict");
       const int e3 = mark();
-      k_correct<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.qp, I.r1, I.u, I.q[b], I.d, I.p);
+      k_correct<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[a], I.qp, I.r1, I.u, I.q[b], I.d, I.p,
+                                                  iso_);
       NLC_CK_LAUNCH("k_correct");
       const int e4 = mark();
       if (timer.on) {
@@ -807,14 +815,14 @@ class Engine final : public EngineBase {
     const int a = cur_;
     const int e0 = mark();
     cudaError_t e = launch_fused_lb<Lat, T>(insts_dev_, qmaps_dev_, tiles_dev_, ntiles_, a,
-                                            derr_, st, any_mrt_);
+                                            derr_, st, any_mrt_, iso_);
     if (e != cudaSuccess) {
       err = std::string("fused lb kernel: ") + cudaGetErrorString(e);
       return NLC_ECUDA;
     }
     const int e1 = mark();
     e = launch_fused_be<Lat, T>(insts_dev_, qmaps_dev_, umaps_dev_, tiles_dev_, ntiles_, a,
-                                derr_, st);
+                                derr_, st, iso_);
     if (e != cudaSuccess) {
       err = std::string("fused Beris-Edwards kernel: ") + cudaGetErrorString(e);
       return NLC_ECUDA;
@@ -916,6 +924,7 @@ class Engine final : public EngineBase {
   cudaStream_t side_stream_ = nullptr;    // adjoint segment records
   std::vector<bool> mrt_on_;              // per lattice: MRT collision
   bool any_mrt_ = false;
+  bool iso_ = false;                      // isotropic stencils
   cudaEvent_t seg_ev_[5] = {};
   int graph_len_[2] = {0, 0};
 };

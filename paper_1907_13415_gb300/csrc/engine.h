@@ -78,6 +78,7 @@ struct EngineBase {
   virtual nlc_status check_finite(int* bad) = 0;
   virtual nlc_status set_params(int inst, const nlc_params& p) = 0;
   virtual nlc_status set_mrt(int inst, const double* rates) = 0;
+  virtual nlc_status set_stencil(bool isotropic) = 0;
   virtual nlc_status step(int64_t n, int schedule) = 0;
   virtual nlc_status set_fields(int inst, const double* Q5, const double* rho,
                                 const double* u) = 0;

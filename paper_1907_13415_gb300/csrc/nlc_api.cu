@@ -175,6 +175,15 @@ nlc_status nlc_set_mrt(nlc_ctx* ctx, int32_t inst, const double* rates, int32_t 
   return NLC_OK;
 }
 
+nlc_status nlc_set_stencil(nlc_ctx* ctx, int32_t kind) {
+  if (!ctx) return NLC_EINVAL;
+  if (kind != NLC_STENCIL_STANDARD && kind != NLC_STENCIL_ISOTROPIC)
+    return fail(ctx, NLC_EINVAL, "unknown stencil");
+  nlc_status st = ctx->eng->set_stencil(kind == NLC_STENCIL_ISOTROPIC);
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  return NLC_OK;
+}
+
 nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps) {
   if (!ctx) return NLC_EINVAL;
   if (steps < 0) return fail(ctx, NLC_EINVAL, "negative graph length");

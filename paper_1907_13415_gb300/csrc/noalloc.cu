@@ -85,7 +85,7 @@ nlc_status run(const Dims& d, const Par<double>& p, const double* f, const doubl
   double* prof = scratch + kOffProf;
   const unsigned gb = (unsigned)((n + 255) / 256);
   k_field_raw_in<double, DIM><<<gb, 256, 0, st>>>(Q5, d, Qf);
-  k_stress<Lat, double><<<gb, 256, 0, st>>>(Qf, Pi, d, p);
+  k_stress<Lat, double><<<gb, 256, 0, st>>>(Qf, Pi, d, p, false);
   k_moments_pre<Lat><<<gb, 256, 0, st>>>(f, Pi, d, p, rho, u);
   const int blocks = (int)(gb < (unsigned)kObsBlocks ? gb : (unsigned)kObsBlocks);
   const double s_ref = 1.0 / 3.0;

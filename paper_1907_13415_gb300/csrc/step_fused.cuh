@@ -138,23 +138,60 @@ __device__ __forceinline__ T lap_points(T v, T xp, T xm, T yp, T ym, T zp, T zm)
   }
 }
 
+// Isotropic stencils on the lattice's neighbour set (the remedy the paper
+// points to for spurious currents, Sec. 2.2): twice the gradient,
+// 2 d_a phi = 6 sum_i w_i c_ia phi(x + c_i), and the Laplacian,
+// lap phi = 6 sum_i w_i [phi(x + c_i) - phi(x)], from at(cx, cy, cz), the
+// value at neighbour offset c_i, and v = phi(x).
+template <class Lat, class T, class At>
+__device__ __forceinline__ void lattice_stencil(const At& at, T v, T d2[3], T& lap) {
+  d2[0] = d2[1] = d2[2] = T(0);
+  T s = T(0);
+#pragma unroll
+  for (int i = 1; i < Lat::Q; i++) {
+    const T vi = at(Lat::c(i, 0), Lat::c(i, 1), Lat::c(i, 2));
+    const T w = T(Lat::w(i));
+    s = fma_(w, vi, s);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+      if (Lat::c(i, a) != 0) d2[a] = fma_(T(Lat::c(i, a)) * w, vi, d2[a]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++) d2[a] = d2[a] * T(6);
+  lap = T(6) * fma_(T(-(1.0 - Lat::w(0))), v, s);
+}
+
 // stress on the ring-region cell of ring-phase thread t of a plane whose Q
 // box is in sq (z neighbours in sqm, sqp), into the Pi slot sp.  The first
 // derivatives are kept as plain differences (twice the central difference);
 // the stress sees them with K/4, which gives K dQ:dQ exactly (scalings by
 // powers of two are exact).
-template <class T, int DIM>
+template <class Lat, class T, bool ISO>
 __device__ __forceinline__ void stress_ring_cell(int t, const T* __restrict__ sq,
                                                  const T* __restrict__ sqm,
                                                  const T* __restrict__ sqp,
-                                                 T* __restrict__ sp,
-                                                 const Par<T>& p) {
+                                                 T* __restrict__ sp, const Par<T>& p) {
+  constexpr int DIM = Lat::DIM;
   int cx, cy, c;
   ring_cell(t, cx, cy, c);
   const int o = box_at(cx, cy);
   T q[5], dq2[3][5], lap[5], h[5], P[3][3];
 #pragma unroll
   for (int k = 0; k < 5; k++) {
+    if constexpr (ISO) {
+      const int ok = k * BA + o;
+      auto at = [&](int dx, int dy, int dz) {
+        const T* pl = dz == 0 ? sq : (dz > 0 ? sqp : sqm);
+        return pl[ok + dx + dy * BXW];
+      };
+      T d2[3];
+      q[k] = sq[ok];
+      lattice_stencil<Lat, T>(at, q[k], d2, lap[k]);
+      dq2[0][k] = d2[0];
+      dq2[1][k] = d2[1];
+      dq2[2][k] = d2[2];
+      continue;
+    }
     const T* F = sq + k * BA;
     const T v = F[o], xp = F[o + 1], xm = F[o - 1];
     const T yp = F[o + BXW], ym = F[o - BXW];
@@ -194,7 +231,7 @@ struct CellPops<Lat, float> {
 
 // MRT: the multiple-relaxation-time collision (physics.cuh: collide_mrt);
 // a lattice of the launch without its own rates gets the BGK rates 1/tau
-template <class Lat, class T, bool MRT>
+template <class Lat, class T, bool MRT, bool ISO>
 __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     k_fused_lb(const InstDev<T>* __restrict__ insts,
                const CUtensorMap* __restrict__ qmaps,
@@ -315,13 +352,31 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     T F[3] = {T(0), T(0), T(0)};
     const T* Pm = DIM == 3 ? sP(pslot(z - 1)) : Pc;
     const T* Pp = DIM == 3 ? sP(pslot(z + 1)) : Pc;
+    if constexpr (ISO) {
+      // F_a = 3 sum_i w_i sum_b c_ib Pi_ab(x + c_i)
 #pragma unroll
-    for (int a = 0; a < DIM; a++) {
-      // F_a = sum_b [Pi_ab(x + e_b) - Pi_ab(x - e_b)] / 2
-      T s = Pc[(a * DIM + 0) * A1 + ic + 1] - Pc[(a * DIM + 0) * A1 + ic - 1];
-      s += Pc[(a * DIM + 1) * A1 + ic + RX1] - Pc[(a * DIM + 1) * A1 + ic - RX1];
-      if (DIM == 3) s += Pp[(a * DIM + 2) * A1 + ic] - Pm[(a * DIM + 2) * A1 + ic];
-      F[a] = s * T(0.5);
+      for (int i = 1; i < Lat::Q; i++) {
+        const T* Pi = Lat::c(i, 2) == 0 ? Pc : (Lat::c(i, 2) > 0 ? Pp : Pm);
+        const int oi = ic + Lat::c(i, 0) + Lat::c(i, 1) * RX1;
+        const T w3 = T(3.0 * Lat::w(i));
+#pragma unroll
+        for (int a = 0; a < DIM; a++) {
+          T sb = T(0);
+#pragma unroll
+          for (int b = 0; b < DIM; b++)
+            if (Lat::c(i, b) != 0) sb = fma_(T(Lat::c(i, b)), Pi[(a * DIM + b) * A1 + oi], sb);
+          F[a] = fma_(w3, sb, F[a]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < DIM; a++) {
+        // F_a = sum_b [Pi_ab(x + e_b) - Pi_ab(x - e_b)] / 2
+        T s = Pc[(a * DIM + 0) * A1 + ic + 1] - Pc[(a * DIM + 0) * A1 + ic - 1];
+        s += Pc[(a * DIM + 1) * A1 + ic + RX1] - Pc[(a * DIM + 1) * A1 + ic - RX1];
+        if (DIM == 3) s += Pp[(a * DIM + 2) * A1 + ic] - Pm[(a * DIM + 2) * A1 + ic];
+        F[a] = s * T(0.5);
+      }
     }
     const unsigned o = (unsigned)(z * nxy + rowy[1] + x);
     const unsigned n32 = (unsigned)d.n;
@@ -374,7 +429,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     if (tid == 0) issue(0);
     pull_next(0);
     wait(0);
-    if (tid < C::RING_T) stress_ring_cell<T, DIM>(tid, sQ(0), sQ(0), sQ(0), sP(0), p);
+    if (tid < C::RING_T) stress_ring_cell<Lat, T, ISO>(tid, sQ(0), sQ(0), sQ(0), sP(0), p);
     if (__syncthreads_or(late)) {
       abort_block();
       return;
@@ -388,7 +443,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     wait(z0 - 1);
     wait(z0);
     if (tid < C::RING_T)
-      stress_ring_cell<T, DIM>(tid, sQ(qslot(z0 - 1)), sQ(qslot(z0 - 2)), sQ(qslot(z0)),
+      stress_ring_cell<Lat, T, ISO>(tid, sQ(qslot(z0 - 1)), sQ(qslot(z0 - 2)), sQ(qslot(z0)),
                                sP(pslot(z0 - 1)), p);
     if (__syncthreads_or(late)) {
       abort_block();
@@ -397,7 +452,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     if (tid == 0) issue(z0 + 2);
     wait(z0 + 1);
     if (tid < C::RING_T)
-      stress_ring_cell<T, DIM>(tid, sQ(qslot(z0)), sQ(qslot(z0 - 1)), sQ(qslot(z0 + 1)),
+      stress_ring_cell<Lat, T, ISO>(tid, sQ(qslot(z0)), sQ(qslot(z0 - 1)), sQ(qslot(z0 + 1)),
                                sP(pslot(z0)), p);
     for (int z = z0; z < z1; z++) {
       // Q(z+3) reuses the slot of Q(z-1), last read by the ring phase of
@@ -405,7 +460,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
       if (tid == 0 && z + 3 <= z1 + 1) issue(z + 3);
       wait(z + 2);
       if (tid < C::RING_T)
-        stress_ring_cell<T, DIM>(tid, sQ(qslot(z + 1)), sQ(qslot(z)), sQ(qslot(z + 2)),
+        stress_ring_cell<Lat, T, ISO>(tid, sQ(qslot(z + 1)), sQ(qslot(z)), sQ(qslot(z + 2)),
                                  sP(pslot(z + 1)), p);
       if (__syncthreads_or(late)) {
         abort_block();
@@ -451,15 +506,28 @@ struct BeCfg {
 
 // u and G[a][b] = d_b u_a at box offset o (z neighbours from
 // the planes above and below)
-template <class T, int DIM>
+template <class Lat, class T, bool ISO>
 __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
                                           const T* __restrict__ m,
                                           const T* __restrict__ pp, int o,
                                           T u[3], T G[3][3]) {
+  constexpr int DIM = Lat::DIM;
   const T half = T(0.5);
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    if (a < DIM) {
+    if (ISO && a < DIM) {
+      const int oa = a * BA + o;
+      auto at = [&](int dx, int dy, int dz) {
+        const T* pl = dz == 0 ? c : (dz > 0 ? pp : m);
+        return pl[oa + dx + dy * BXW];
+      };
+      T d2[3], unused;
+      u[a] = c[oa];
+      lattice_stencil<Lat, T>(at, u[a], d2, unused);
+      G[a][0] = d2[0] * half;
+      G[a][1] = d2[1] * half;
+      G[a][2] = d2[2] * half;
+    } else if (a < DIM) {
       const T* F = c + a * BA;
       u[a] = F[o];
       G[a][0] = (F[o + 1] - F[o - 1]) * half;
@@ -477,13 +545,28 @@ __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
 // of a plane array c (row stride row, component stride comp; z neighbours in
 // m and pp).  The differences are kept plain (twice the central difference)
 // and meet u/2: (u/2).(2 dQ) = u.dQ exactly.
-template <class T, int DIM>
+template <class Lat, class T, bool ISO>
 __device__ __forceinline__ void stencil_adv(const T* __restrict__ c, const T* __restrict__ m,
                                             const T* __restrict__ pp, int o, int row, int comp,
                                             const T u[3], T q[5], T adv[5], T lap[5]) {
+  constexpr int DIM = Lat::DIM;
   const T uh0 = u[0] * T(0.5), uh1 = u[1] * T(0.5), uh2 = u[2] * T(0.5);
 #pragma unroll
   for (int k = 0; k < 5; k++) {
+    if constexpr (ISO) {
+      const int ok = k * comp + o;
+      auto at = [&](int dx, int dy, int dz) {
+        const T* pl = dz == 0 ? c : (dz > 0 ? pp : m);
+        return pl[ok + dx + dy * row];
+      };
+      T d2[3];
+      q[k] = c[ok];
+      lattice_stencil<Lat, T>(at, q[k], d2, lap[k]);
+      T a = fma_(uh0, d2[0], uh1 * d2[1]);
+      if (DIM == 3) a = fma_(uh2, d2[2], a);
+      adv[k] = a;
+      continue;
+    }
     const T* F = c + k * comp;
     const T v = F[o], xp = F[o + 1],
             xm = F[o - 1];
@@ -501,7 +584,7 @@ __device__ __forceinline__ void stencil_adv(const T* __restrict__ c, const T* __
   }
 }
 
-template <class Lat, class T>
+template <class Lat, class T, bool ISO>
 __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     k_fused_be(const InstDev<T>* __restrict__ insts,
                const CUtensorMap* __restrict__ qmaps,
@@ -577,8 +660,8 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     const T* um = DIM == 3 ? sU(us(z - 1)) : uc;
     const T* up = DIM == 3 ? sU(us(z + 1)) : uc;
     T q[5], adv[5], lap[5], u[3], G[3][3], r[5];
-    box_ugrad<T, DIM>(uc, um, up, o, u, G);
-    stencil_adv<T, DIM>(qc, qm, qp, o, BXW, BA, u, q, adv, lap);
+    box_ugrad<Lat, T, ISO>(uc, um, up, o, u, G);
+    stencil_adv<Lat, T, ISO>(qc, qm, qp, o, BXW, BA, u, q, adv, lap);
     be_rhs_adv<T>(q, adv, lap, G, p, r);
     T* qpo = sQP(ps(z));
 #pragma unroll
@@ -600,9 +683,9 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     const T* pm = DIM == 3 ? sQP(ps(z - 1)) : pc;
     const T* pp = DIM == 3 ? sQP(ps(z + 1)) : pc;
     T qp[5], adv[5], lap[5], u[3], G[3][3], r2[5];
-    box_ugrad<T, DIM>(sU(us(z)), DIM == 3 ? sU(us(z - 1)) : sU(us(z)),
+    box_ugrad<Lat, T, ISO>(sU(us(z)), DIM == 3 ? sU(us(z - 1)) : sU(us(z)),
                          DIM == 3 ? sU(us(z + 1)) : sU(us(z)), o2, u, G);
-    stencil_adv<T, DIM>(pc, pm, pp, ic, RX1, A1, u, qp, adv, lap);
+    stencil_adv<Lat, T, ISO>(pc, pm, pp, ic, RX1, A1, u, qp, adv, lap);
     be_rhs_adv<T>(qp, adv, lap, G, p, r2);
     // Q^{n+1} = Q^n + [R(Q^n) + R(Q^P)]/2 = [Q^n + Q^P + R(Q^P)]/2, since
     // Q^P = Q^n + R(Q^n)
@@ -698,36 +781,48 @@ inline cudaError_t set_smem(K kernel, size_t bytes, unsigned long long* done_mas
   return e;
 }
 
-template <class Lat, class T, bool MRT>
+template <class Lat, class T, bool MRT, bool ISO>
 cudaError_t launch_fused_lb_as(const InstDev<T>* insts, const CUtensorMap* qmaps,
                                const TileRef* tiles, int ntiles, int cur, unsigned* err,
                                cudaStream_t st) {
   static unsigned long long configured = 0;
-  cudaError_t e = set_smem(k_fused_lb<Lat, T, MRT>, LbCfg<Lat, T>::bytes, &configured);
+  cudaError_t e = set_smem(k_fused_lb<Lat, T, MRT, ISO>, LbCfg<Lat, T>::bytes, &configured);
   if (e != cudaSuccess) return e;
-  k_fused_lb<Lat, T, MRT><<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(
+  k_fused_lb<Lat, T, MRT, ISO><<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(
       insts, qmaps, tiles, cur, err);
   return cudaGetLastError();
 }
 
+// mrt: MRT collision; iso: isotropic stencils
 template <class Lat, class T>
 cudaError_t launch_fused_lb(const InstDev<T>* insts, const CUtensorMap* qmaps,
                             const TileRef* tiles, int ntiles, int cur, unsigned* err,
-                            cudaStream_t st, bool mrt) {
-  return mrt ? launch_fused_lb_as<Lat, T, true>(insts, qmaps, tiles, ntiles, cur, err, st)
-             : launch_fused_lb_as<Lat, T, false>(insts, qmaps, tiles, ntiles, cur, err, st);
+                            cudaStream_t st, bool mrt, bool iso) {
+  if (iso)
+    return mrt ? launch_fused_lb_as<Lat, T, true, true>(insts, qmaps, tiles, ntiles, cur, err, st)
+               : launch_fused_lb_as<Lat, T, false, true>(insts, qmaps, tiles, ntiles, cur, err, st);
+  return mrt ? launch_fused_lb_as<Lat, T, true, false>(insts, qmaps, tiles, ntiles, cur, err, st)
+             : launch_fused_lb_as<Lat, T, false, false>(insts, qmaps, tiles, ntiles, cur, err, st);
+}
+
+template <class Lat, class T, bool ISO>
+cudaError_t launch_fused_be_as(const InstDev<T>* insts, const CUtensorMap* qmaps,
+                               const CUtensorMap* umaps, const TileRef* tiles, int ntiles,
+                               int cur, unsigned* err, cudaStream_t st) {
+  static unsigned long long configured = 0;
+  cudaError_t e = set_smem(k_fused_be<Lat, T, ISO>, BeCfg<Lat, T>::bytes, &configured);
+  if (e != cudaSuccess) return e;
+  k_fused_be<Lat, T, ISO><<<ntiles, BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::bytes, st>>>(
+      insts, qmaps, umaps, tiles, cur, err);
+  return cudaGetLastError();
 }
 
 template <class Lat, class T>
 cudaError_t launch_fused_be(const InstDev<T>* insts, const CUtensorMap* qmaps,
                             const CUtensorMap* umaps, const TileRef* tiles, int ntiles,
-                            int cur, unsigned* err, cudaStream_t st) {
-  static unsigned long long configured = 0;
-  cudaError_t e = set_smem(k_fused_be<Lat, T>, BeCfg<Lat, T>::bytes, &configured);
-  if (e != cudaSuccess) return e;
-  k_fused_be<Lat, T><<<ntiles, BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::bytes, st>>>(insts, qmaps, umaps, tiles,
-                                                                 cur, err);
-  return cudaGetLastError();
+                            int cur, unsigned* err, cudaStream_t st, bool iso) {
+  return iso ? launch_fused_be_as<Lat, T, true>(insts, qmaps, umaps, tiles, ntiles, cur, err, st)
+             : launch_fused_be_as<Lat, T, false>(insts, qmaps, umaps, tiles, ntiles, cur, err, st);
 }
 
 }  // namespace nlc

@@ -64,6 +64,48 @@ __device__ __forceinline__ void u_stencil(const Field<T>& U, int x, int y,
   }
 }
 
+// The same three from the isotropic stencils of the lattice's neighbour set:
+// d_a v = (1/cs^2) sum_i w_i c_ia v(x + c_i),
+// lap v = (2/cs^2) sum_i w_i [v(x + c_i) - v(x)].
+template <class Lat, class T>
+__device__ __forceinline__ void q_stencil_iso(const Field<T>& Q, int x, int y, int z, T q[5],
+                                              T dq[3][5], T lap[5]) {
+#pragma unroll
+  for (int k = 0; k < 5; k++) {
+    const T v = Q.at(k, x, y, z);
+    T s = T(0), d[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 1; i < Lat::Q; i++) {
+      const T vi = Q.at(k, x + Lat::c(i, 0), y + Lat::c(i, 1), z + Lat::c(i, 2));
+      const T w = T(Lat::w(i));
+      s += w * (vi - v);
+#pragma unroll
+      for (int a = 0; a < 3; a++) d[a] += w * T(Lat::c(i, a)) * vi;
+    }
+    q[k] = v;
+    lap[k] = T(6) * s;
+#pragma unroll
+    for (int a = 0; a < 3; a++) dq[a][k] = T(3) * d[a];
+  }
+}
+
+template <class Lat, class T>
+__device__ __forceinline__ void u_stencil_iso(const Field<T>& U, int x, int y, int z, T u[3],
+                                              T G[3][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    u[a] = a < Lat::DIM ? U.at(a, x, y, z) : T(0);
+    G[a][0] = G[a][1] = G[a][2] = T(0);
+    if (a >= Lat::DIM) continue;
+#pragma unroll
+    for (int i = 1; i < Lat::Q; i++) {
+      const T vi = U.at(a, x + Lat::c(i, 0), y + Lat::c(i, 1), z + Lat::c(i, 2));
+#pragma unroll
+      for (int b = 0; b < 3; b++) G[a][b] += T(3.0 * Lat::w(i) * Lat::c(i, b)) * vi;
+    }
+  }
+}
+
 __device__ __forceinline__ bool decode(const Dims& d, int64_t idx, int& x,
                                        int& y, int& z) {
   if (idx >= d.n) return false;
@@ -77,12 +119,17 @@ __device__ __forceinline__ bool decode(const Dims& d, int64_t idx, int& x,
 // The four stages at one cell (x, y, z) = decode(idx); the kernels below run
 // one cell per thread, the adjoint's segment kernels (adjoint_segment.cuh)
 // loop over cells with the same functions.
+// iso: isotropic stencils (q_stencil_iso, u_stencil_iso, force_at_iso)
 template <class Lat, class T>
 __device__ __forceinline__ void stress_at(const Field<T>& Q, T* __restrict__ Pi, const Dims& d,
-                                          const Par<T>& p, int64_t idx, int x, int y, int z) {
+                                          const Par<T>& p, bool iso, int64_t idx, int x,
+                                          int y, int z) {
   constexpr int DIM = Lat::DIM;
   T q[5], dq[3][5], lap[5], h[5], P[3][3];
-  q_stencil<T, DIM>(Q, x, y, z, q, dq, lap);
+  if (iso)
+    q_stencil_iso<Lat, T>(Q, x, y, z, q, dq, lap);
+  else
+    q_stencil<T, DIM>(Q, x, y, z, q, dq, lap);
   molecular_field(q, lap, p, h);
   stress<T, DIM>(q, h, dq, p, P);
 #pragma unroll
@@ -93,10 +140,10 @@ __device__ __forceinline__ void stress_at(const Field<T>& Q, T* __restrict__ Pi,
 
 template <class Lat, class T>
 __global__ void __launch_bounds__(256) k_stress(Field<T> Q, T* __restrict__ Pi,
-                                                Dims d, Par<T> p) {
+                                                Dims d, Par<T> p, bool iso) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (decode(d, idx, x, y, z)) stress_at<Lat, T>(Q, Pi, d, p, idx, x, y, z);
+  if (decode(d, idx, x, y, z)) stress_at<Lat, T>(Q, Pi, d, p, iso, idx, x, y, z);
 }
 
 // F_a = sum_b [Pi_ab(x + e_b) - Pi_ab(x - e_b)] / 2  (Pi unpadded: wrap)
@@ -122,6 +169,26 @@ __device__ __forceinline__ void force_at(const T* __restrict__ Pi,
   }
 }
 
+// F_a = (1/cs^2) sum_i w_i sum_b c_ib Pi_ab(x + c_i)  (isotropic; wrap)
+template <class Lat, class T>
+__device__ __forceinline__ void force_at_iso(const T* __restrict__ Pi, const Dims& d, int x,
+                                             int y, int z, T F[3]) {
+  constexpr int DIM = Lat::DIM;
+  F[0] = F[1] = F[2] = T(0);
+#pragma unroll
+  for (int i = 1; i < Lat::Q; i++) {
+    const int64_t ci = cell_of(d, wrap_add(x, Lat::c(i, 0), d.nx),
+                               wrap_add(y, Lat::c(i, 1), d.ny),
+                               DIM == 3 ? wrap_add(z, Lat::c(i, 2), d.nz) : z);
+#pragma unroll
+    for (int a = 0; a < DIM; a++)
+#pragma unroll
+      for (int b = 0; b < DIM; b++)
+        if (Lat::c(i, b) != 0)
+          F[a] += T(3.0 * Lat::w(i) * Lat::c(i, b)) * Pi[(a * DIM + b) * d.n + ci];
+  }
+}
+
 // pre-collision deviations g_i(x, t) = g*_i(x - c_i) (pull, periodic)
 template <class Lat, class T>
 __device__ __forceinline__ void pull(const T* __restrict__ gin, const Dims& d,
@@ -140,10 +207,13 @@ __device__ __forceinline__ void pull(const T* __restrict__ gin, const Dims& d,
 template <class Lat, class T>
 __device__ __forceinline__ void lb_at(const T* __restrict__ gin, T* __restrict__ gout,
                                       const T* __restrict__ Pi, const Field<T>& U,
-                                      const Dims& d, const Par<T>& p, const T* mrt,
+                                      const Dims& d, const Par<T>& p, const T* mrt, bool iso,
                                       int64_t idx, int x, int y, int z) {
   T F[3], g[Lat::Q], rho, u[3];
-  force_at<T, Lat::DIM>(Pi, d, x, y, z, F);
+  if (iso)
+    force_at_iso<Lat, T>(Pi, d, x, y, z, F);
+  else
+    force_at<T, Lat::DIM>(Pi, d, x, y, z, F);
   pull<Lat, T>(gin, d, x, y, z, g);
   moments<Lat, T>(g, F, p, rho, u);
   if (mrt)
@@ -160,21 +230,27 @@ __global__ void __launch_bounds__(256) k_lb(const T* __restrict__ gin,
                                             T* __restrict__ gout,
                                             const T* __restrict__ Pi,
                                             Field<T> U, Dims d, Par<T> p,
-                                            const T* __restrict__ mrt) {
+                                            const T* __restrict__ mrt, bool iso) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (decode(d, idx, x, y, z)) lb_at<Lat, T>(gin, gout, Pi, U, d, p, mrt, idx, x, y, z);
+  if (decode(d, idx, x, y, z))
+    lb_at<Lat, T>(gin, gout, Pi, U, d, p, mrt, iso, idx, x, y, z);
 }
 
 template <class Lat, class T>
 __device__ __forceinline__ void predict_at(const Field<T>& Q, const Field<T>& U,
                                            const Field<T>& QP, T* __restrict__ R1,
-                                           const Dims& d, const Par<T>& p, int64_t idx,
-                                           int x, int y, int z) {
+                                           const Dims& d, const Par<T>& p, bool iso,
+                                           int64_t idx, int x, int y, int z) {
   constexpr int DIM = Lat::DIM;
   T q[5], dq[3][5], lap[5], u[3], G[3][3], r[5], qp[5];
-  q_stencil<T, DIM>(Q, x, y, z, q, dq, lap);
-  u_stencil<T, DIM>(U, x, y, z, u, G);
+  if (iso) {
+    q_stencil_iso<Lat, T>(Q, x, y, z, q, dq, lap);
+    u_stencil_iso<Lat, T>(U, x, y, z, u, G);
+  } else {
+    q_stencil<T, DIM>(Q, x, y, z, q, dq, lap);
+    u_stencil<T, DIM>(U, x, y, z, u, G);
+  }
   be_rhs<T, DIM>(q, dq, lap, u, G, p, r);
 #pragma unroll
   for (int k = 0; k < 5; k++) {
@@ -188,22 +264,27 @@ template <class Lat, class T>
 __global__ void __launch_bounds__(256) k_predict(Field<T> Q, Field<T> U,
                                                  Field<T> QP,
                                                  T* __restrict__ R1, Dims d,
-                                                 Par<T> p) {
+                                                 Par<T> p, bool iso) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (decode(d, idx, x, y, z)) predict_at<Lat, T>(Q, U, QP, R1, d, p, idx, x, y, z);
+  if (decode(d, idx, x, y, z)) predict_at<Lat, T>(Q, U, QP, R1, d, p, iso, idx, x, y, z);
 }
 
 template <class Lat, class T>
 __device__ __forceinline__ void correct_at(const Field<T>& Q, const Field<T>& QP,
                                            const T* __restrict__ R1, const Field<T>& U,
                                            const Field<T>& Qout, const Dims& d,
-                                           const Par<T>& p, int64_t idx, int x, int y,
-                                           int z) {
+                                           const Par<T>& p, bool iso, int64_t idx, int x,
+                                           int y, int z) {
   constexpr int DIM = Lat::DIM;
   T qp[5], dq[3][5], lap[5], u[3], G[3][3], r2[5], out[5];
-  q_stencil<T, DIM>(QP, x, y, z, qp, dq, lap);
-  u_stencil<T, DIM>(U, x, y, z, u, G);
+  if (iso) {
+    q_stencil_iso<Lat, T>(QP, x, y, z, qp, dq, lap);
+    u_stencil_iso<Lat, T>(U, x, y, z, u, G);
+  } else {
+    q_stencil<T, DIM>(QP, x, y, z, qp, dq, lap);
+    u_stencil<T, DIM>(U, x, y, z, u, G);
+  }
   be_rhs<T, DIM>(qp, dq, lap, u, G, p, r2);
 #pragma unroll
   for (int k = 0; k < 5; k++)
@@ -215,10 +296,11 @@ template <class Lat, class T>
 __global__ void __launch_bounds__(256) k_correct(Field<T> Q, Field<T> QP,
                                                  const T* __restrict__ R1,
                                                  Field<T> U, Field<T> Qout,
-                                                 Dims d, Par<T> p) {
+                                                 Dims d, Par<T> p, bool iso) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (decode(d, idx, x, y, z)) correct_at<Lat, T>(Q, QP, R1, U, Qout, d, p, idx, x, y, z);
+  if (decode(d, idx, x, y, z))
+    correct_at<Lat, T>(Q, QP, R1, U, Qout, d, p, iso, idx, x, y, z);
 }
 
 }  // namespace nlc

@@ -96,6 +96,7 @@ def load(build_if_missing=True):
         "nlc_set_check": ([P, I32], I32),
         "nlc_set_params": ([P, I32, ctypes.POINTER(nlc_params)], I32),
         "nlc_set_mrt": ([P, I32, P, I32], I32),
+        "nlc_set_stencil": ([P, I32], I32),
         "nlc_set_schedule": ([P, I32], I32),
         "nlc_set_fields": ([P, I32, P, P, P], I32),
         "nlc_get_fields": ([P, I32, P, P, P], I32),
@@ -125,7 +126,7 @@ def load(build_if_missing=True):
 
 def exported_symbols():
     return ["nlc_create", "nlc_create_batch", "nlc_count", "nlc_set_graph", "nlc_set_check",
-            "nlc_set_params", "nlc_set_mrt",
+            "nlc_set_params", "nlc_set_mrt", "nlc_set_stencil",
             "nlc_set_schedule", "nlc_set_fields",
             "nlc_get_fields", "nlc_get_populations", "nlc_step",
             "nlc_observables", "nlc_last_error", "nlc_destroy",
@@ -194,6 +195,14 @@ def nlc_set_mrt(ctx, inst, rates=None):
         return
     r = np.ascontiguousarray(rates, dtype=np.float64)
     _check(ctx, load().nlc_set_mrt(ctx, inst, _ptr(r), int(r.size)))
+
+
+NLC_STENCIL_STANDARD = 0
+NLC_STENCIL_ISOTROPIC = 1
+
+
+def nlc_set_stencil(ctx, kind):
+    _check(ctx, load().nlc_set_stencil(ctx, int(kind)))
 
 
 def nlc_set_check(ctx, every):
@@ -341,6 +350,9 @@ class Batch:
     def set_mrt(self, i, rates=None):
         nlc_set_mrt(self.ctx, i, rates)
 
+    def set_stencil(self, kind):
+        nlc_set_stencil(self.ctx, kind)
+
     def set_fields(self, i, Q5, rho=None, u=None):
         sh = self.shapes[i]
         nlc_set_fields(self.ctx, i, _f64(Q5, (5,) + sh), _f64(rho, sh),
@@ -442,6 +454,9 @@ class Simulation:
 
     def set_mrt(self, rates=None):
         nlc_set_mrt(self.ctx, 0, rates)
+
+    def set_stencil(self, kind):
+        nlc_set_stencil(self.ctx, kind)
 
     def set_graph(self, steps):
         nlc_set_graph(self.ctx, steps)
