@@ -35,10 +35,11 @@ def _stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def _run(w, precision, steps, every):
+def _run(w, precision, steps, every, stencil=0):
     """Runs w, returning observables every `every` steps and the final Q."""
     s = nlc.Simulation(w.lattice, w.shape, w.params, precision=precision,
                        stream=_stream())
+    s.set_stencil(stencil)
     s.set_fields(w.initial_q5())
     trace = [s.observables()]
     done = 0
@@ -74,14 +75,15 @@ def flat(gamma=2.7, steps=2000, lx=128, ly=8, every=100):
             "fp32_vs_fp64": _drift("x_iface", t32, t64, Q32, Q64)}
 
 
-def disc(delta=0.0, steps=20000, n=256, radius=32, every=500):
+def disc(delta=0.0, steps=20000, n=256, radius=32, every=500, stencil=0):
     w = wl.disc_256(delta).with_(shape=(1, n, n), size=radius)
-    t64, Q64 = _run(w, nlc.NLC_FP64, steps, every)
-    t32, Q32 = _run(w, nlc.NLC_FP32, steps, every)
+    t64, Q64 = _run(w, nlc.NLC_FP64, steps, every, stencil)
+    t32, Q32 = _run(w, nlc.NLC_FP32, steps, every, stencil)
     R = np.array([o["radius"] for o in t64])
     tail = max(2, len(R) // 4)
     dRdt = float((R[-1] - R[-tail]) / ((tail - 1) * every))
     return {"experiment": "circular droplet", "delta": delta,
+            "stencil": "isotropic" if stencil else "standard",
             "gamma": w.params["gamma"], "lattice": [n, n], "radius0": radius,
             "steps": steps, "radius_fp64": [float(r) for r in R[:: max(1, len(R) // 10)]],
             "dRdt_fp64": dRdt,
@@ -98,7 +100,7 @@ def vorticity(u):
 
 
 def paper_circle(angle_deg=0.0, steps=35000, every=1000, gamma=2.707681,
-                 lattice=wl.D2Q9, dump=None):
+                 lattice=wl.D2Q9, dump=None, stencil=0):
     """Sec. 2.2 / Fig. 2 with the paper's parameters (tau = 1.5, K = 0.04,
     Gamma = 0.34, xi = 0.7, A0 = 0.1): a 100 x 100 lattice, disc of radius 25,
     director at angle_deg from y, gamma = 2.707681.  Reports the interface
@@ -112,6 +114,7 @@ def paper_circle(angle_deg=0.0, steps=35000, every=1000, gamma=2.707681,
                     (math.sin(a), math.cos(a), 0.0), 0.0, 0)
     s = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP64,
                        stream=_stream())
+    s.set_stencil(stencil)
     s.set_fields(w.initial_q5())
     trace = [s.observables()]
     done = 0
@@ -129,6 +132,7 @@ def paper_circle(angle_deg=0.0, steps=35000, every=1000, gamma=2.707681,
     tail = max(2, len(R) // 4)
     return {"experiment": "paper circle", "angle_deg": angle_deg, "gamma": gamma,
             "lattice": "D2Q9" if lattice == wl.D2Q9 else "D3Q19 (nz = 1)",
+            "stencil": "isotropic" if stencil else "standard",
             "steps": steps, "radius_final": float(R[-1]),
             "dRdt_final": float((R[-1] - R[-tail]) / ((tail - 1) * every)),
             "max_u_final": float(trace[-1]["max_u"]),
@@ -246,6 +250,8 @@ def main(argv=None):
     ap.add_argument("--angle", type=float, default=0.0)
     ap.add_argument("--lattice", choices=["d2q9", "d3q19"], default="d2q9")
     ap.add_argument("--dump", default=None, help="paper_circle: .npz of the final fields")
+    ap.add_argument("--isotropic", action="store_true",
+                    help="disc, paper_circle: isotropic finite-difference stencils")
     ap.add_argument("--gamma", type=float, default=2.7)
     ap.add_argument("--delta", type=float, default=0.0)
     ap.add_argument("--steps", type=int, default=None)
@@ -255,11 +261,11 @@ def main(argv=None):
     if args.which == "flat":
         r = flat(args.gamma, args.steps or 2000)
     elif args.which == "disc":
-        r = disc(args.delta, args.steps or 20000)
+        r = disc(args.delta, args.steps or 20000, stencil=int(args.isotropic))
     elif args.which == "paper_circle":
         r = paper_circle(args.angle, args.steps or 35000,
                          lattice=wl.D3Q19 if args.lattice == "d3q19" else wl.D2Q9,
-                         dump=args.dump)
+                         dump=args.dump, stencil=int(args.isotropic))
     elif args.which == "flat_paper":
         r = flat_paper(args.gamma, args.steps or 350000)
     else:
