@@ -67,9 +67,13 @@ enum { NLC_D2Q9 = 0, NLC_D3Q19 = 1 };
 /* Arithmetic and storage precision of the step.  Observables are always
  * accumulated in FP64. */
 enum {
-  NLC_FP64 = 0, /* everything in double                                     */
-  NLC_FP32 = 1  /* populations (as deviations from w_i rho0) and Q stored
-                   and computed in float                                    */
+  NLC_FP64 = 0,     /* everything in double                                 */
+  NLC_FP32 = 1,     /* populations (as deviations from w_i rho0) and Q stored
+                       and computed in float                                */
+  NLC_FP32_QF64 = 2 /* populations stored in float (as deviations), Q, u and
+                       all arithmetic in double: halves the population
+                       traffic of FP64 while Q keeps double precision.
+                       nlc_adjoint returns NLC_EUNSUPPORTED.               */
 };
 
 /* Kernel schedule of one step.  Both compute the same step. */
@@ -81,7 +85,7 @@ enum {
 typedef struct {
   int32_t nx, ny, nz; /* lattice extent; nz = 1 for D2Q9                    */
   int32_t lattice;    /* NLC_D2Q9 | NLC_D3Q19                               */
-  int32_t precision;  /* NLC_FP64 | NLC_FP32                                */
+  int32_t precision;  /* NLC_FP64 | NLC_FP32 | NLC_FP32_QF64                */
 } nlc_grid;
 
 /* Eq. 2 (A0, K, gamma), Eq. 1 (Gamma, xi), Sec. 1.2.1 (tau), reference

@@ -144,8 +144,8 @@ __device__ __forceinline__ void adj_be1_at(const Field<T>& Q, const Field<T>& U,
 //    the pre-collision adjoint is stored pulled back: lG_i(x - c_i).
 //    Writes the force adjoint lF for the stress adjoint.
 //    lGn == nullptr: seed mode (no collision; only u of the final state).
-template <class Lat, class T>
-__device__ __forceinline__ void adj_lb_at(const T* __restrict__ gin, const T* __restrict__ Pi,
+template <class Lat, class T, class G>
+__device__ __forceinline__ void adj_lb_at(const G* __restrict__ gin, const T* __restrict__ Pi,
                                           const T* __restrict__ lGn,
                                           const T* __restrict__ lUa,
                                           const T* __restrict__ lGv, T* __restrict__ lG,
@@ -190,8 +190,8 @@ __device__ __forceinline__ void adj_lb_at(const T* __restrict__ gin, const T* __
   for (int a = 0; a < DIM; a++) lF[a * d.n + idx] = Fb[a];
 }
 
-template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_adj_lb(const T* __restrict__ gin,
+template <class Lat, class T, class G>
+__global__ void __launch_bounds__(256) k_adj_lb(const G* __restrict__ gin,
                                                 const T* __restrict__ Pi,
                                                 const T* __restrict__ lGn,
                                                 const T* __restrict__ lUa,

@@ -10,10 +10,10 @@ namespace nlc {
 // Q from float64 input; populations to the pull-layout image of f^eq(rho, u):
 // the deviation stored at y for direction i is g^eq_i evaluated at y + c_i,
 // so that pulling reproduces f^eq at every cell.  Counts non-finite inputs.
-template <class Lat, class T>
+template <class Lat, class T, class G>
 __global__ void __launch_bounds__(256) k_set_fields(
     const double* __restrict__ q_in, const double* __restrict__ rho_in,
-    const double* __restrict__ u_in, Field<T> Q, T* __restrict__ g,
+    const double* __restrict__ u_in, Field<T> Q, G* __restrict__ g,
     Dims d, double rho0, unsigned long long* __restrict__ bad) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -47,15 +47,15 @@ __global__ void __launch_bounds__(256) k_set_fields(
     }
     const double w = Lat::w(i);
     const double geq = w * ((rho - rho0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
-    g[(int64_t)i * d.n + idx] = (T)geq;
+    g[(int64_t)i * d.n + idx] = (G)geq;
   }
   if (nbad) atomicAdd(bad, (unsigned long long)nbad);
 }
 
 // rho and u of Eq. 6 (with F/2) at the current time, into float64 arrays
-template <class Lat, class T>
+template <class Lat, class T, class G>
 __global__ void __launch_bounds__(256) k_moments_out(
-    const T* __restrict__ gin, const T* __restrict__ Pi, Dims d, Par<T> p,
+    const G* __restrict__ gin, const T* __restrict__ Pi, Dims d, Par<T> p,
     double* __restrict__ rho_out, double* __restrict__ u_out, bool iso) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -73,9 +73,9 @@ __global__ void __launch_bounds__(256) k_moments_out(
 }
 
 // pre-collision populations f_i = w_i rho0 + g*_i(x - c_i) as float64
-template <class Lat, class T>
+template <class Lat, class T, class G>
 __global__ void __launch_bounds__(256) k_populations_out(
-    const T* __restrict__ gin, Dims d, double rho0, double* __restrict__ f) {
+    const G* __restrict__ gin, Dims d, double rho0, double* __restrict__ f) {
   int x, y, z;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (!decode(d, idx, x, y, z)) return;
@@ -97,8 +97,8 @@ __global__ void __launch_bounds__(256) k_field_out(Field<T> F, int nc, Dims d,
 }
 
 // counts non-finite populations and Q components
-template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_count_nonfinite(const T* __restrict__ g, Field<T> Q,
+template <class Lat, class T, class G>
+__global__ void __launch_bounds__(256) k_count_nonfinite(const G* __restrict__ g, Field<T> Q,
                                                          Dims d,
                                                          unsigned long long* __restrict__ bad) {
   int x, y, z;
@@ -140,9 +140,9 @@ __global__ void __launch_bounds__(256) k_field_raw_in(const T* __restrict__ in, 
 // non-finite count, sum |u|^2, max |u| (last).
 constexpr int OBS_SLOTS = 9;
 
-template <class Lat, class T>
+template <class Lat, class T, class G>
 __global__ void __launch_bounds__(256) k_obs_partial(
-    Field<T> Q, const T* __restrict__ gpost,
+    Field<T> Q, const G* __restrict__ gpost,
     const double* __restrict__ rho, const double* __restrict__ u, Dims d,
     Par<T> p, double s_ref, double* __restrict__ partial) {
   __shared__ double sh[32];

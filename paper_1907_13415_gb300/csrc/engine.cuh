@@ -34,13 +34,13 @@ namespace nlc {
     }                                                                      \
   } while (0)
 
-// host-side record of one lattice
-template <class T>
+// host-side record of one lattice (T: arithmetic, Q and u; G: populations)
+template <class T, class G = T>
 struct InstHost {
   Dims d;
   Layout L;
   Par<T> p;
-  T* g[2] = {nullptr, nullptr};
+  G* g[2] = {nullptr, nullptr};
   Field<T> q[2];
   Field<T> u;
   int tz = 1;
@@ -73,7 +73,9 @@ struct InstHost {
   int seg_grid = 0;            // blocks of the cooperative launches (0: not available)
 };
 
-template <class Lat, class T>
+// T: arithmetic and the Q, u fields; G: storage of the populations (float
+// with T = double is the FP32-population, FP64-Q mode)
+template <class Lat, class T, class G = T>
 class Engine final : public EngineBase {
  public:
   static constexpr int Q = Lat::Q;
@@ -96,7 +98,7 @@ class Engine final : public EngineBase {
     const int n = args_.n;
     inst_.resize(n);
     mrt_on_.assign(n, false);
-    std::vector<InstDev<T>> dev(n);
+    std::vector<InstDev<T, G>> dev(n);
     std::vector<CUtensorMap> qmaps(2 * n), umaps(n);
     std::vector<TileRef> tiles;
     int64_t tiles_so_far = 0;
@@ -104,7 +106,7 @@ class Engine final : public EngineBase {
     cudaStream_t st = args_.stream;
     nlc_status s;
     for (int i = 0; i < n; i++) {
-      InstHost<T>& I = inst_[i];
+      InstHost<T, G>& I = inst_[i];
       const nlc_grid& g = args_.grids[i];
       const nlc_params& q = args_.params[i];
       I.d = Dims{g.nx, g.ny, g.nz, (int64_t)g.nx * g.ny * g.nz};
@@ -126,8 +128,8 @@ class Engine final : public EngineBase {
       I.q[0] = Field<T>{q0, I.L};
       I.q[1] = Field<T>{q1, I.L};
       I.u = Field<T>{u, I.L};
-      NLC_CK(cudaMemsetAsync(I.g[0], 0, sizeof(T) * Q * I.d.n, st));
-      NLC_CK(cudaMemsetAsync(I.g[1], 0, sizeof(T) * Q * I.d.n, st));
+      NLC_CK(cudaMemsetAsync(I.g[0], 0, sizeof(G) * Q * I.d.n, st));
+      NLC_CK(cudaMemsetAsync(I.g[1], 0, sizeof(G) * Q * I.d.n, st));
       NLC_CK(cudaMemsetAsync(q0, 0, sizeof(T) * 5 * I.L.comp, st));
       NLC_CK(cudaMemsetAsync(q1, 0, sizeof(T) * 5 * I.L.comp, st));
       NLC_CK(cudaMemsetAsync(u, 0, sizeof(T) * DIM * I.L.comp, st));
@@ -154,7 +156,7 @@ class Engine final : public EngineBase {
       return s;
     ntiles_ = (int)tiles.size();
     NLC_CK(cudaMemsetAsync(derr_, 0, sizeof(unsigned), st));
-    NLC_CK(cudaMemcpyAsync(insts_dev_, dev.data(), sizeof(InstDev<T>) * n, cudaMemcpyHostToDevice, st));
+    NLC_CK(cudaMemcpyAsync(insts_dev_, dev.data(), sizeof(InstDev<T, G>) * n, cudaMemcpyHostToDevice, st));
     NLC_CK(cudaMemcpyAsync(qmaps_dev_, qmaps.data(), sizeof(CUtensorMap) * 2 * n, cudaMemcpyHostToDevice, st));
     NLC_CK(cudaMemcpyAsync(umaps_dev_, umaps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, st));
     NLC_CK(cudaMemcpyAsync(tiles_dev_, tiles.data(), sizeof(TileRef) * tiles.size(), cudaMemcpyHostToDevice, st));
@@ -168,7 +170,7 @@ class Engine final : public EngineBase {
     cudaStream_t st = args_.stream;
     *bad = -1;
     for (size_t i = 0; i < inst_.size(); i++) {
-      InstHost<T>& I = inst_[i];
+      InstHost<T, G>& I = inst_[i];
       NLC_CK(cudaMemsetAsync(bad_, 0, sizeof(unsigned long long), st));
       k_count_nonfinite<Lat, T><<<grid1(I.d.n), 256, 0, st>>>(I.g[cur_], I.q[cur_], I.d, bad_);
       NLC_CK_LAUNCH("k_count_nonfinite");
@@ -188,7 +190,7 @@ class Engine final : public EngineBase {
   // lattice.cuh, or BGK again (rates == nullptr).  Captured step graphs hold
   // the kernel variant, so they are dropped.
   nlc_status set_mrt(int i, const double* rates) override {
-    InstHost<T>& I = inst_[i];
+    InstHost<T, G>& I = inst_[i];
     cudaStream_t st = args_.stream;
     nlc_status s;
     if (rates) {
@@ -227,7 +229,7 @@ class Engine final : public EngineBase {
   }
 
   nlc_status set_params(int i, const nlc_params& q) override {
-    InstHost<T>& I = inst_[i];
+    InstHost<T, G>& I = inst_[i];
     I.p.A0 = (T)q.A0;
     I.p.K = (T)q.K;
     I.p.gamma = (T)q.gamma;
@@ -278,7 +280,7 @@ class Engine final : public EngineBase {
   // ---------------------------------------------------------------- I/O
   nlc_status set_fields(int i, const double* Q5, const double* rho,
                         const double* u) override {
-    InstHost<T>& I = inst_[i];
+    InstHost<T, G>& I = inst_[i];
     nlc_status s;
     if ((s = ensure_staging(I))) return s;
     const int64_t n = I.d.n;
@@ -305,7 +307,7 @@ class Engine final : public EngineBase {
   }
 
   nlc_status get_fields(int i, double* Q5, double* rho, double* u) override {
-    InstHost<T>& I = inst_[i];
+    InstHost<T, G>& I = inst_[i];
     nlc_status s;
     if ((s = ensure_staging(I))) return s;
     const int64_t n = I.d.n;
@@ -327,7 +329,7 @@ class Engine final : public EngineBase {
   }
 
   nlc_status get_populations(int i, double* f) override {
-    InstHost<T>& I = inst_[i];
+    InstHost<T, G>& I = inst_[i];
     if (!I.fstage) {
       nlc_status s = alloc(&I.fstage, (size_t)Q * I.d.n);
       if (s) return s;
@@ -344,7 +346,7 @@ class Engine final : public EngineBase {
 
   size_t state_bytes() const override {
     size_t b = 0;
-    for (const auto& I : inst_) b += sizeof(T) * (size_t)(Q + 5) * (size_t)I.d.n;
+    for (const auto& I : inst_) b += (sizeof(G) * Q + sizeof(T) * 5) * (size_t)I.d.n;
     return b;
   }
 
@@ -357,8 +359,8 @@ class Engine final : public EngineBase {
       const int64_t n = I.d.n;
       k_field_raw_out<T><<<grid1(n), 256, 0, st>>>(I.q[cur_], 5, I.d, I.raw);
       NLC_CK_LAUNCH("k_field_raw_out");
-      NLC_CK(cudaMemcpyAsync(out, I.g[cur_], sizeof(T) * Q * n, cudaMemcpyDeviceToHost, st));
-      out += sizeof(T) * Q * n;
+      NLC_CK(cudaMemcpyAsync(out, I.g[cur_], sizeof(G) * Q * n, cudaMemcpyDeviceToHost, st));
+      out += sizeof(G) * Q * n;
       NLC_CK(cudaMemcpyAsync(out, I.raw, sizeof(T) * 5 * n, cudaMemcpyDeviceToHost, st));
       out += sizeof(T) * 5 * n;
     }
@@ -373,8 +375,8 @@ class Engine final : public EngineBase {
       nlc_status s;
       if (!I.raw && (s = alloc(&I.raw, (size_t)5 * I.d.n))) return s;
       const int64_t n = I.d.n;
-      NLC_CK(cudaMemcpyAsync(I.g[0], in, sizeof(T) * Q * n, cudaMemcpyHostToDevice, st));
-      in += sizeof(T) * Q * n;
+      NLC_CK(cudaMemcpyAsync(I.g[0], in, sizeof(G) * Q * n, cudaMemcpyHostToDevice, st));
+      in += sizeof(G) * Q * n;
       NLC_CK(cudaMemcpyAsync(I.raw, in, sizeof(T) * 5 * n, cudaMemcpyHostToDevice, st));
       in += sizeof(T) * 5 * n;
       k_field_raw_in<T, DIM><<<grid1(n), 256, 0, st>>>(I.raw, I.d, I.q[0]);
@@ -389,7 +391,11 @@ class Engine final : public EngineBase {
   // ------------------------------------------------------------- adjoint
   nlc_status adjoint(const nlc_loss* loss, int64_t nsteps, int ckpt_every, nlc_grad* out,
                      double* dQ0) override {
-    InstHost<T>& I = inst_[0];
+    if constexpr (!std::is_same<T, G>::value) {
+      err = "the adjoint needs the populations in the arithmetic precision";
+      return NLC_EUNSUPPORTED;
+    }
+    InstHost<T, G>& I = inst_[0];
     const int64_t n = I.d.n;
     const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
     const int64_t S = (int64_t)(Q + 5) * n;  // one state
@@ -468,7 +474,7 @@ class Engine final : public EngineBase {
   }
 
   nlc_status observables(int i, nlc_obs* out, double* s_profile) override {
-    InstHost<T>& I = inst_[i];
+    InstHost<T, G>& I = inst_[i];
     nlc_status s;
     if ((s = ensure_staging(I))) return s;
     const int64_t n = I.d.n;
@@ -553,7 +559,7 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
-  nlc_status ensure_unfused(InstHost<T>& I) {
+  nlc_status ensure_unfused(InstHost<T, G>& I) {
     if (I.pi) return NLC_OK;
     nlc_status s;
     const int64_t n = I.d.n;
@@ -565,7 +571,7 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
-  nlc_status ensure_staging(InstHost<T>& I) {
+  nlc_status ensure_staging(InstHost<T, G>& I) {
     if (I.stage) return NLC_OK;
     nlc_status s;
     const int64_t n = I.d.n;
@@ -585,7 +591,7 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
-  nlc_status ensure_adjoint(InstHost<T>& I, int64_t ck_count) {
+  nlc_status ensure_adjoint(InstHost<T, G>& I, int64_t ck_count) {
     nlc_status s;
     const int64_t n = I.d.n;
     const int64_t S = (int64_t)(Q + 5) * n;
@@ -624,7 +630,7 @@ class Engine final : public EngineBase {
   }
 
   // record slots (two sets) for segments of up to len steps
-  nlc_status ensure_segment(InstHost<T>& I, int64_t len) {
+  nlc_status ensure_segment(InstHost<T, G>& I, int64_t len) {
     nlc_status s;
     if (!I.bar) {
       if ((s = alloc(&I.bar, 3))) return s;
@@ -650,7 +656,7 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
-  SegArgs<T> seg_args(InstHost<T>& I, int b, int len, int lc) {
+  SegArgs<T> seg_args(InstHost<T, G>& I, int b, int len, int lc) {
     SegArgs<T> a;
     a.d = I.d;
     a.p = I.p;
@@ -680,7 +686,7 @@ class Engine final : public EngineBase {
 
   // record of a segment of len steps from the checkpoint at ck into set b,
   // on stream ss
-  nlc_status segment_record(InstHost<T>& I, int b, const T* ck, int len, cudaStream_t ss) {
+  nlc_status segment_record(InstHost<T, G>& I, int b, const T* ck, int len, cudaStream_t ss) {
     const int64_t n = I.d.n;
     NLC_CK(cudaMemcpyAsync(I.rec_g[b], ck, sizeof(T) * Q * n, cudaMemcpyDeviceToDevice, ss));
     k_field_raw_in<T, DIM><<<grid1(n), 256, 0, ss>>>(ck + (int64_t)Q * n, I.d,
@@ -697,7 +703,7 @@ class Engine final : public EngineBase {
 
   // reverse of the segment recorded in set b; the adjoint of its end state
   // is in (lQ[lc], lG[lc])
-  nlc_status segment_reverse(InstHost<T>& I, int b, int len, int lc, cudaStream_t st) {
+  nlc_status segment_reverse(InstHost<T, G>& I, int b, int len, int lc, cudaStream_t st) {
     SegArgs<T> a = seg_args(I, b, len, lc);
     a.bar = I.bar + 2;
     void* args[] = {&a};
@@ -710,7 +716,7 @@ class Engine final : public EngineBase {
   // All segments, last to first: the record of segment k-1 runs on the side
   // stream while segment k reverses on the main stream.  Record set k % 2
   // is rewritten only after the reverse that read it (segment k+2) is done.
-  nlc_status segments_backward(InstHost<T>& I, int64_t nsteps, int ckpt_every, int64_t nseg,
+  nlc_status segments_backward(InstHost<T, G>& I, int64_t nsteps, int ckpt_every, int64_t nseg,
                                int64_t S, int& lc) {
     cudaStream_t st = args_.stream, ss = side_stream_;
     cudaEvent_t ev_main = seg_ev_[0], ev_rec[2] = {seg_ev_[1], seg_ev_[2]},
@@ -747,7 +753,7 @@ class Engine final : public EngineBase {
   }
 
   // current state of instance I <-> a dense (g, Q) record
-  nlc_status state_out(InstHost<T>& I, T* dst) {
+  nlc_status state_out(InstHost<T, G>& I, T* dst) {
     const int64_t n = I.d.n;
     cudaStream_t st = args_.stream;
     NLC_CK(cudaMemcpyAsync(dst, I.g[cur_], sizeof(T) * Q * n, cudaMemcpyDeviceToDevice, st));
@@ -756,7 +762,7 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
-  nlc_status state_in(InstHost<T>& I, const T* src) {
+  nlc_status state_in(InstHost<T, G>& I, const T* src) {
     const int64_t n = I.d.n;
     cudaStream_t st = args_.stream;
     NLC_CK(cudaMemcpyAsync(I.g[cur_], src, sizeof(T) * Q * n, cudaMemcpyDeviceToDevice, st));
@@ -766,7 +772,7 @@ class Engine final : public EngineBase {
   }
 
   // rho, u of Eq. 6 at the current state into stage[5n..9n)
-  nlc_status moments_to_stage(InstHost<T>& I) {
+  nlc_status moments_to_stage(InstHost<T, G>& I) {
     const int64_t n = I.d.n;
     cudaStream_t st = args_.stream;
     k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[cur_], I.pi, I.d, I.p, iso_);
@@ -902,9 +908,9 @@ class Engine final : public EngineBase {
   }
 
   EngineArgs args_;
-  std::vector<InstHost<T>> inst_;
+  std::vector<InstHost<T, G>> inst_;
   std::vector<void*> allocs_;
-  InstDev<T>* insts_dev_ = nullptr;
+  InstDev<T, G>* insts_dev_ = nullptr;
   CUtensorMap* qmaps_dev_ = nullptr;
   CUtensorMap* umaps_dev_ = nullptr;
   TileRef* tiles_dev_ = nullptr;
@@ -929,10 +935,10 @@ class Engine final : public EngineBase {
   int graph_len_[2] = {0, 0};
 };
 
-template <class Lat, class T>
+template <class Lat, class T, class G = T>
 std::unique_ptr<EngineBase> make_engine(const EngineArgs& a, nlc_status* st,
                                         std::string* msg) {
-  auto e = std::make_unique<Engine<Lat, T>>(a);
+  auto e = std::make_unique<Engine<Lat, T, G>>(a);
   *st = e->init();
   if (*st != NLC_OK) {
     *msg = e->err;

@@ -106,5 +106,7 @@ std::unique_ptr<EngineBase> make_engine_d2q9_f64(const EngineArgs&, nlc_status*,
 std::unique_ptr<EngineBase> make_engine_d2q9_f32(const EngineArgs&, nlc_status*, std::string*);
 std::unique_ptr<EngineBase> make_engine_d3q19_f64(const EngineArgs&, nlc_status*, std::string*);
 std::unique_ptr<EngineBase> make_engine_d3q19_f32(const EngineArgs&, nlc_status*, std::string*);
+std::unique_ptr<EngineBase> make_engine_d2q9_f64f32(const EngineArgs&, nlc_status*, std::string*);
+std::unique_ptr<EngineBase> make_engine_d3q19_f64f32(const EngineArgs&, nlc_status*, std::string*);
 
 }  // namespace nlc

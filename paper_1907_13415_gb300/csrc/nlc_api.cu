@@ -48,7 +48,7 @@ nlc_status check_grid(const nlc_grid* g, std::string* msg) {
     *msg = "unknown lattice " + std::to_string(g->lattice);
     return NLC_EINVAL;
   }
-  if (g->precision != NLC_FP64 && g->precision != NLC_FP32) {
+  if (g->precision != NLC_FP64 && g->precision != NLC_FP32 && g->precision != NLC_FP32_QF64) {
     *msg = "unknown precision " + std::to_string(g->precision);
     return NLC_EINVAL;
   }
@@ -125,14 +125,16 @@ nlc_status nlc_create_batch(int32_t n, const nlc_grid* grids,
   }
   nlc::EngineArgs a{n, ctx->grids, ctx->params, ctx->stream};
   const bool d3 = grids[0].lattice == NLC_D3Q19;
-  const bool f64 = grids[0].precision == NLC_FP64;
+  const int32_t prec = grids[0].precision;
   nlc_status st = NLC_OK;
   if (d3)
-    ctx->eng = f64 ? nlc::make_engine_d3q19_f64(a, &st, &msg)
-                   : nlc::make_engine_d3q19_f32(a, &st, &msg);
+    ctx->eng = prec == NLC_FP64   ? nlc::make_engine_d3q19_f64(a, &st, &msg)
+               : prec == NLC_FP32 ? nlc::make_engine_d3q19_f32(a, &st, &msg)
+                                  : nlc::make_engine_d3q19_f64f32(a, &st, &msg);
   else
-    ctx->eng = f64 ? nlc::make_engine_d2q9_f64(a, &st, &msg)
-                   : nlc::make_engine_d2q9_f32(a, &st, &msg);
+    ctx->eng = prec == NLC_FP64   ? nlc::make_engine_d2q9_f64(a, &st, &msg)
+               : prec == NLC_FP32 ? nlc::make_engine_d2q9_f32(a, &st, &msg)
+                                  : nlc::make_engine_d2q9_f64f32(a, &st, &msg);
   if (!ctx->eng) {
     delete ctx;
     return st != NLC_OK ? st : NLC_ECUDA;

@@ -79,11 +79,12 @@ constexpr size_t align128(size_t bytes) {
 }
 
 // One lattice of a (possibly batched) context, as the step kernels see it.
-template <class T>
+// T: arithmetic and the Q and u fields; G: storage of the populations.
+template <class T, class G = T>
 struct InstDev {
   Dims d;
   Par<T> p;
-  T* g[2];         // populations, ping-pong
+  G* g[2];         // populations (deviations), ping-pong
   Field<T> q[2];   // Q, ping-pong
   Field<T> u;      // u^n handed from the lb to the Beris-Edwards kernel
   const T* mrt;    // Q coefficients s_k / |v_k|^2 of the MRT collision, or nullptr
@@ -231,9 +232,9 @@ struct CellPops<Lat, float> {
 
 // MRT: the multiple-relaxation-time collision (physics.cuh: collide_mrt);
 // a lattice of the launch without its own rates gets the BGK rates 1/tau
-template <class Lat, class T, bool MRT, bool ISO>
+template <class Lat, class T, class G, bool MRT, bool ISO>
 __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
-    k_fused_lb(const InstDev<T>* __restrict__ insts,
+    k_fused_lb(const InstDev<T, G>* __restrict__ insts,
                const CUtensorMap* __restrict__ qmaps,
                const TileRef* __restrict__ tiles, int cur,
                unsigned* __restrict__ err) {
@@ -246,11 +247,11 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
   auto sP = [&](int slot) { return reinterpret_cast<T*>(smem + C::off_p + slot * C::p_slot); };
 
   const TileRef tile = tiles[blockIdx.x];
-  const InstDev<T>& I = insts[tile.inst];
+  const InstDev<T, G>& I = insts[tile.inst];
   const Dims d = I.d;
   const Par<T> p = I.p;
-  const T* __restrict__ gin = I.g[cur];
-  T* __restrict__ gout = I.g[cur ^ 1];
+  const G* __restrict__ gin = I.g[cur];
+  G* __restrict__ gout = I.g[cur ^ 1];
   const Field<T> U = I.u;
   const int zoff = U.L.zoff;
   const CUtensorMap* qmap = &qmaps[2 * tile.inst + cur];
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     auto ld = [&](int i) {
       const unsigned off = (unsigned)(plane[Lat::c(i, 2) + 1] + rowy[Lat::c(i, 1) + 1] +
                                       colx[Lat::c(i, 0) + 1]);
-      return __ldg(gin + (size_t)i * n32 + off);
+      return T(__ldg(gin + (size_t)i * n32 + off));
     };
     if constexpr (kPacked) {
       gn.g0 = ld(0);
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
       moments<Lat, T>(g, F, p, rho, u);
       collide_mrt<Lat, T>(g, rho, u, F, p, s_mrt);
 #pragma unroll
-      for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = g[i];
+      for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = G(g[i]);
     } else if constexpr (kPacked) {
       float g0 = gn.g0, drho;
       float2 gp[NP];
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
       moments<Lat, T>(g, F, p, rho, u);
       collide_bgk<Lat, T>(g, rho, u, F, p);
 #pragma unroll
-      for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = g[i];
+      for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = G(g[i]);
     }
     store_with_images<T, DIM, DIM>(U, d, x, y, z, u);
     if (z + 1 < z1) pull_next(z + 1);
@@ -584,9 +585,9 @@ __device__ __forceinline__ void stencil_adv(const T* __restrict__ c, const T* __
   }
 }
 
-template <class Lat, class T, bool ISO>
+template <class Lat, class T, class G, bool ISO>
 __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
-    k_fused_be(const InstDev<T>* __restrict__ insts,
+    k_fused_be(const InstDev<T, G>* __restrict__ insts,
                const CUtensorMap* __restrict__ qmaps,
                const CUtensorMap* __restrict__ umaps,
                const TileRef* __restrict__ tiles, int cur,
@@ -601,7 +602,7 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
   auto sQP = [&](int s) { return reinterpret_cast<T*>(smem + C::off_p + s * C::p_slot); };
 
   const TileRef tile = tiles[blockIdx.x];
-  const InstDev<T>& I = insts[tile.inst];
+  const InstDev<T, G>& I = insts[tile.inst];
   const Dims d = I.d;
   const Par<T> p = I.p;
   const Field<T> Qout = I.q[cur ^ 1];
@@ -781,48 +782,48 @@ inline cudaError_t set_smem(K kernel, size_t bytes, unsigned long long* done_mas
   return e;
 }
 
-template <class Lat, class T, bool MRT, bool ISO>
-cudaError_t launch_fused_lb_as(const InstDev<T>* insts, const CUtensorMap* qmaps,
+template <class Lat, class T, class G, bool MRT, bool ISO>
+cudaError_t launch_fused_lb_as(const InstDev<T, G>* insts, const CUtensorMap* qmaps,
                                const TileRef* tiles, int ntiles, int cur, unsigned* err,
                                cudaStream_t st) {
   static unsigned long long configured = 0;
-  cudaError_t e = set_smem(k_fused_lb<Lat, T, MRT, ISO>, LbCfg<Lat, T>::bytes, &configured);
+  cudaError_t e = set_smem(k_fused_lb<Lat, T, G, MRT, ISO>, LbCfg<Lat, T>::bytes, &configured);
   if (e != cudaSuccess) return e;
-  k_fused_lb<Lat, T, MRT, ISO><<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(
+  k_fused_lb<Lat, T, G, MRT, ISO><<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(
       insts, qmaps, tiles, cur, err);
   return cudaGetLastError();
 }
 
 // mrt: MRT collision; iso: isotropic stencils
-template <class Lat, class T>
-cudaError_t launch_fused_lb(const InstDev<T>* insts, const CUtensorMap* qmaps,
+template <class Lat, class T, class G>
+cudaError_t launch_fused_lb(const InstDev<T, G>* insts, const CUtensorMap* qmaps,
                             const TileRef* tiles, int ntiles, int cur, unsigned* err,
                             cudaStream_t st, bool mrt, bool iso) {
   if (iso)
-    return mrt ? launch_fused_lb_as<Lat, T, true, true>(insts, qmaps, tiles, ntiles, cur, err, st)
-               : launch_fused_lb_as<Lat, T, false, true>(insts, qmaps, tiles, ntiles, cur, err, st);
-  return mrt ? launch_fused_lb_as<Lat, T, true, false>(insts, qmaps, tiles, ntiles, cur, err, st)
-             : launch_fused_lb_as<Lat, T, false, false>(insts, qmaps, tiles, ntiles, cur, err, st);
+    return mrt ? launch_fused_lb_as<Lat, T, G, true, true>(insts, qmaps, tiles, ntiles, cur, err, st)
+               : launch_fused_lb_as<Lat, T, G, false, true>(insts, qmaps, tiles, ntiles, cur, err, st);
+  return mrt ? launch_fused_lb_as<Lat, T, G, true, false>(insts, qmaps, tiles, ntiles, cur, err, st)
+             : launch_fused_lb_as<Lat, T, G, false, false>(insts, qmaps, tiles, ntiles, cur, err, st);
 }
 
-template <class Lat, class T, bool ISO>
-cudaError_t launch_fused_be_as(const InstDev<T>* insts, const CUtensorMap* qmaps,
+template <class Lat, class T, class G, bool ISO>
+cudaError_t launch_fused_be_as(const InstDev<T, G>* insts, const CUtensorMap* qmaps,
                                const CUtensorMap* umaps, const TileRef* tiles, int ntiles,
                                int cur, unsigned* err, cudaStream_t st) {
   static unsigned long long configured = 0;
-  cudaError_t e = set_smem(k_fused_be<Lat, T, ISO>, BeCfg<Lat, T>::bytes, &configured);
+  cudaError_t e = set_smem(k_fused_be<Lat, T, G, ISO>, BeCfg<Lat, T>::bytes, &configured);
   if (e != cudaSuccess) return e;
-  k_fused_be<Lat, T, ISO><<<ntiles, BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::bytes, st>>>(
+  k_fused_be<Lat, T, G, ISO><<<ntiles, BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::bytes, st>>>(
       insts, qmaps, umaps, tiles, cur, err);
   return cudaGetLastError();
 }
 
-template <class Lat, class T>
-cudaError_t launch_fused_be(const InstDev<T>* insts, const CUtensorMap* qmaps,
+template <class Lat, class T, class G>
+cudaError_t launch_fused_be(const InstDev<T, G>* insts, const CUtensorMap* qmaps,
                             const CUtensorMap* umaps, const TileRef* tiles, int ntiles,
                             int cur, unsigned* err, cudaStream_t st, bool iso) {
-  return iso ? launch_fused_be_as<Lat, T, true>(insts, qmaps, umaps, tiles, ntiles, cur, err, st)
-             : launch_fused_be_as<Lat, T, false>(insts, qmaps, umaps, tiles, ntiles, cur, err, st);
+  return iso ? launch_fused_be_as<Lat, T, G, true>(insts, qmaps, umaps, tiles, ntiles, cur, err, st)
+             : launch_fused_be_as<Lat, T, G, false>(insts, qmaps, umaps, tiles, ntiles, cur, err, st);
 }
 
 }  // namespace nlc

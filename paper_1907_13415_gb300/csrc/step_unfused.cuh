@@ -190,22 +190,22 @@ __device__ __forceinline__ void force_at_iso(const T* __restrict__ Pi, const Dim
 }
 
 // pre-collision deviations g_i(x, t) = g*_i(x - c_i) (pull, periodic)
-template <class Lat, class T>
-__device__ __forceinline__ void pull(const T* __restrict__ gin, const Dims& d,
+template <class Lat, class T, class G>
+__device__ __forceinline__ void pull(const G* __restrict__ gin, const Dims& d,
                                      int x, int y, int z, T g[Lat::Q]) {
 #pragma unroll
   for (int i = 0; i < Lat::Q; i++) {
     const int xs = wrap_add(x, -Lat::c(i, 0), d.nx);
     const int ys = wrap_add(y, -Lat::c(i, 1), d.ny);
     const int zs = Lat::DIM == 3 ? wrap_add(z, -Lat::c(i, 2), d.nz) : z;
-    g[i] = gin[(int64_t)i * d.n + cell_of(d, xs, ys, zs)];
+    g[i] = T(gin[(int64_t)i * d.n + cell_of(d, xs, ys, zs)]);
   }
 }
 
 // mrt: the Q coefficients s_k / |v_k|^2 of the MRT collision, or nullptr
 // for BGK
-template <class Lat, class T>
-__device__ __forceinline__ void lb_at(const T* __restrict__ gin, T* __restrict__ gout,
+template <class Lat, class T, class G>
+__device__ __forceinline__ void lb_at(const G* __restrict__ gin, G* __restrict__ gout,
                                       const T* __restrict__ Pi, const Field<T>& U,
                                       const Dims& d, const Par<T>& p, const T* mrt, bool iso,
                                       int64_t idx, int x, int y, int z) {
@@ -221,13 +221,13 @@ __device__ __forceinline__ void lb_at(const T* __restrict__ gin, T* __restrict__
   else
     collide_bgk<Lat, T>(g, rho, u, F, p);
 #pragma unroll
-  for (int i = 0; i < Lat::Q; i++) gout[(int64_t)i * d.n + idx] = g[i];
+  for (int i = 0; i < Lat::Q; i++) gout[(int64_t)i * d.n + idx] = G(g[i]);
   store_with_images<T, Lat::DIM, Lat::DIM>(U, d, x, y, z, u);
 }
 
-template <class Lat, class T>
-__global__ void __launch_bounds__(256) k_lb(const T* __restrict__ gin,
-                                            T* __restrict__ gout,
+template <class Lat, class T, class G>
+__global__ void __launch_bounds__(256) k_lb(const G* __restrict__ gin,
+                                            G* __restrict__ gout,
                                             const T* __restrict__ Pi,
                                             Field<T> U, Dims d, Par<T> p,
                                             const T* __restrict__ mrt, bool iso) {

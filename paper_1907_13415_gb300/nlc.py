@@ -17,7 +17,7 @@ STATUS = {0: "NLC_OK", -1: "NLC_EINVAL", -2: "NLC_ENOMEM", -3: "NLC_ECUDA",
           -4: "NLC_EUNSTABLE", -5: "NLC_ETIMEOUT", -6: "NLC_ECORRUPT",
           -7: "NLC_EUNSUPPORTED"}
 NLC_D2Q9, NLC_D3Q19 = 0, 1
-NLC_FP64, NLC_FP32 = 0, 1
+NLC_FP64, NLC_FP32, NLC_FP32_QF64 = 0, 1, 2
 NLC_SCHED_FUSED, NLC_SCHED_UNFUSED = 0, 1
 NLC_STATIC_MAX_CELLS, NLC_STATIC_MAX_NX = 65536, 4096
 
