@@ -42,6 +42,19 @@ ALG_BYTES_STEP = 2 * (Q3 + 5) * WORD          # 192 B
 ALG_BYTES = {"fused_lb": (2 * Q3 + 5) * WORD,  # 172 B
              "fused_be": 2 * 5 * WORD}         # 40 B
 
+# precision option: (library constant name, bytes of a population word,
+# bytes of a Q word, arithmetic dtype)
+PRECISIONS = {"fp32": ("NLC_FP32", 4, 4, "f32"),
+              "fp64": ("NLC_FP64", 8, 8, "f64"),
+              "fp32_qf64": ("NLC_FP32_QF64", 4, 8, "f64")}
+
+
+def alg_bytes(precision):
+    """(step, per-kernel) algorithmic bytes per LUP for a precision."""
+    _, gw, qw, _ = PRECISIONS[precision]
+    return (2 * (Q3 * gw + 5 * qw),
+            {"fused_lb": 2 * Q3 * gw + 5 * qw, "fused_be": 2 * 5 * qw})
+
 # DRAM traffic per LUP of each kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, divided by the cells of the
 # captured launch), keyed by the SHA-256 of the kernel sources it was taken
@@ -300,7 +313,8 @@ def run_ours(args, w):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
-    sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+    prec_name, _, _, dtype = PRECISIONS[args.precision]
+    sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=getattr(nlc, prec_name),
                          stream=stream.cuda_stream,
                          schedule=(nlc.NLC_SCHED_FUSED if args.schedule == "fused"
                                    else nlc.NLC_SCHED_UNFUSED))
@@ -342,18 +356,21 @@ def run_ours(args, w):
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms, dom_n = kt[dom]
     per_launch_s = dom_ms / max(dom_n, 1) * 1e-3
-    alg = ALG_BYTES.get(dom, ALG_BYTES_STEP) * cells
+    step_bytes, kern_bytes = alg_bytes(args.precision)
+    alg = kern_bytes.get(dom, step_bytes) * cells
     achieved = alg / per_launch_s / 1e9
     tr = NCU_TRAFFIC.get(dom)
-    traffic = (tr[0] * cells if tr and tr[1] == source_hash() else None)
+    # the ncu figures were taken on the FP32 default configuration
+    traffic = (tr[0] * cells if tr and tr[1] == source_hash() and args.precision == "fp32"
+               and not args.mrt else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "kernel": dom, "peak_source": peak_src,
-                "alg_bytes_per_lup": ALG_BYTES.get(dom, ALG_BYTES_STEP)}
+                "alg_bytes_per_lup": kern_bytes.get(dom, step_bytes)}
     step_s = t_max / args.steps * 1e-3
-    step_roofline = {"alg_bytes_per_lup": ALG_BYTES_STEP,
-                     "achieved": ALG_BYTES_STEP * cells / step_s / 1e9,
-                     "frac": ALG_BYTES_STEP * cells / step_s / 1e9 / peak}
+    step_roofline = {"alg_bytes_per_lup": step_bytes,
+                     "achieved": step_bytes * cells / step_s / 1e9,
+                     "frac": step_bytes * cells / step_s / 1e9 / peak}
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
                    "share": v[0] / max(sum(x[0] for x in kt.values()), 1e-30)}
                for k, v in kt.items() if v[1]}
@@ -402,9 +419,10 @@ def run_ours(args, w):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic",
             "config": {"workload": w.name, "lattice": "D3Q19",
+                       "precision": args.precision,
                        "shape": [nx, ny, nz], "radius": w.size,
                        "gamma": w.params["gamma"],
                        "parallelism": f"replicas{ws}",
@@ -553,6 +571,9 @@ def main():
                          "(profiling captures); the reported workload is "
                          "the default 256^3")
     ap.add_argument("--schedule", default="fused", choices=["fused", "unfused"])
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
+                    help="fp32 (default), fp64, or fp32_qf64 (float populations, "
+                         "double Q and arithmetic)")
     ap.add_argument("--mrt", action="store_true",
                     help="time the MRT collision instead of BGK")
     ap.add_argument("--workload", default="sphere256",
