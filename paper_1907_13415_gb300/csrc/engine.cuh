@@ -16,6 +16,42 @@
 
 namespace nlc {
 
+// parameters of one lattice in the arithmetic type T; the derived factors
+// are formed in float64 and rounded once
+template <class T>
+inline Par<T> make_par(const nlc_params& q) {
+  Par<double> d;
+  d.A0 = q.A0;
+  d.K = q.K;
+  d.gamma = q.gamma;
+  d.Gamma = q.Gamma;
+  d.xi = q.xi;
+  d.tau = q.tau;
+  d.rho0 = q.rho0;
+  derive(d);
+  Par<T> p;
+  p.A0 = (T)d.A0;
+  p.K = (T)d.K;
+  p.gamma = (T)d.gamma;
+  p.Gamma = (T)d.Gamma;
+  p.xi = (T)d.xi;
+  p.tau = (T)d.tau;
+  p.rho0 = (T)d.rho0;
+  p.inv_tau = (T)d.inv_tau;
+  p.guo = (T)d.guo;
+  p.Ag = (T)d.Ag;
+  p.A1 = (T)d.A1;
+  p.Ag3 = (T)d.Ag3;
+  p.xm1 = (T)d.xm1;
+  p.xp1 = (T)d.xp1;
+  p.x23 = (T)d.x23;
+  p.x2 = (T)d.x2;
+  p.hp = (T)d.hp;
+  p.hm = (T)d.hm;
+  p.x29 = (T)d.x29;
+  return p;
+}
+
 #define NLC_CK(call)                                                       \
   do {                                                                     \
     cudaError_t e_ = (call);                                               \
@@ -111,15 +147,7 @@ class Engine final : public EngineBase {
       const nlc_params& q = args_.params[i];
       I.d = Dims{g.nx, g.ny, g.nz, (int64_t)g.nx * g.ny * g.nz};
       I.L = make_layout(I.d, DIM == 3);
-      I.p.A0 = (T)q.A0;
-      I.p.K = (T)q.K;
-      I.p.gamma = (T)q.gamma;
-      I.p.Gamma = (T)q.Gamma;
-      I.p.xi = (T)q.xi;
-      I.p.tau = (T)q.tau;
-      I.p.rho0 = (T)q.rho0;
-      I.p.inv_tau = (T)(1.0 / q.tau);
-      I.p.guo = (T)(1.0 - 1.0 / (2.0 * q.tau));
+      I.p = make_par<T>(q);
       T *q0, *q1, *u;
       if ((s = alloc(&I.g[0], (size_t)Q * I.d.n)) || (s = alloc(&I.g[1], (size_t)Q * I.d.n)) ||
           (s = alloc(&q0, (size_t)5 * I.L.comp)) || (s = alloc(&q1, (size_t)5 * I.L.comp)) ||
@@ -230,15 +258,7 @@ class Engine final : public EngineBase {
 
   nlc_status set_params(int i, const nlc_params& q) override {
     InstHost<T, G>& I = inst_[i];
-    I.p.A0 = (T)q.A0;
-    I.p.K = (T)q.K;
-    I.p.gamma = (T)q.gamma;
-    I.p.Gamma = (T)q.Gamma;
-    I.p.xi = (T)q.xi;
-    I.p.tau = (T)q.tau;
-    I.p.rho0 = (T)q.rho0;
-    I.p.inv_tau = (T)(1.0 / q.tau);
-    I.p.guo = (T)(1.0 - 1.0 / (2.0 * q.tau));
+    I.p = make_par<T>(q);
     args_.params[i] = q;
     // the device descriptor holds the parameters: update it in place
     NLC_CK(cudaMemcpyAsync(&insts_dev_[i].p, &I.p, sizeof(Par<T>), cudaMemcpyHostToDevice,

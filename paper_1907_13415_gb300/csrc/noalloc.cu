@@ -165,8 +165,7 @@ extern "C" NLC_API nlc_status nlc_observables_static(const nlc_grid* grid,
   p.xi = params->xi;
   p.tau = params->tau;
   p.rho0 = params->rho0;
-  p.inv_tau = 1.0 / params->tau;
-  p.guo = 1.0 - 1.0 / (2.0 * params->tau);
+  derive(p);
   cudaStream_t st = (cudaStream_t)stream;
   return grid->lattice == NLC_D2Q9
              ? run<LatD2Q9>(d, p, f, Q5, st, g_scratch_ptr[dev], out)

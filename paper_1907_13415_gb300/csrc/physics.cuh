@@ -24,7 +24,34 @@ struct Par {
   T A0, K, gamma, Gamma, xi, tau, rho0;
   T inv_tau;  // 1/tau
   T guo;      // 1 - 1/(2 tau), the prefactor of the source term
+  // parameter factors of Eq. 3, Eq. 5 and Eq. 1, formed once by derive() so
+  // that no cell divides or recombines parameters
+  T Ag;       // A0 gamma
+  T A1;       // -A0 (1 - gamma/3)
+  T Ag3;      // -A0 gamma/3
+  T xm1, xp1; // xi - 1, xi + 1
+  T x23;      // 2 xi/3
+  T x2;       // 2 xi
+  T hp, hm;   // (xi + 1)/2, (xi - 1)/2
+  T x29;      // 2 xi/9
 };
+
+// inv_tau, guo and the factors above from A0, K, gamma, Gamma, xi, tau
+template <class T>
+__host__ __device__ inline void derive(Par<T>& p) {
+  p.inv_tau = T(1) / p.tau;
+  p.guo = T(1) - T(1) / (T(2) * p.tau);
+  p.Ag = p.A0 * p.gamma;
+  p.A1 = -p.A0 * (T(1) - p.gamma / T(3));
+  p.Ag3 = -p.Ag / T(3);
+  p.xm1 = p.xi - T(1);
+  p.xp1 = p.xi + T(1);
+  p.x23 = T(2) * p.xi / T(3);
+  p.x2 = T(2) * p.xi;
+  p.hp = (p.xi + T(1)) * T(0.5);
+  p.hm = (p.xi - T(1)) * T(0.5);
+  p.x29 = T(2) * p.xi / T(9);
+}
 
 // five stored components -> full symmetric traceless 3x3
 template <class T>
@@ -56,9 +83,9 @@ __host__ __device__ __forceinline__ void molecular_field(const T q[5], const T l
   const T qq3 = b * b + d * d + e * e;
   const T qq4 = b * c + d * e + e * f;
   const T tr2 = a * a + d * d + f * f + T(2) * (b * b + c * c + e * e);
-  const T Ag = p.A0 * p.gamma;
-  const T c1 = -p.A0 * (T(1) - p.gamma / T(3)) - Ag * tr2;
-  const T c3 = (-Ag / T(3)) * tr2;  // parameter factor, no division per cell
+  const T Ag = p.Ag;
+  const T c1 = p.A1 - Ag * tr2;
+  const T c3 = p.Ag3 * tr2;
   h[0] = c1 * a + Ag * qq0 + c3 + p.K * lap[0];
   h[1] = c1 * b + Ag * qq1 + p.K * lap[1];
   h[2] = c1 * c + Ag * qq2 + p.K * lap[2];
@@ -82,8 +109,8 @@ __host__ __device__ __forceinline__ void stress(const T q[5], const T h[5],
   // Q:H over all nine entries
   const T qh = fma_(Q[0][0], H[0][0], fma_(Q[1][1], H[1][1], Q[2][2] * H[2][2])) +
                T(2) * fma_(q[1], h[1], fma_(q[2], h[2], q[4] * h[4]));
-  const T xm1 = p.xi - T(1), xp1 = p.xi + T(1), x23 = T(2) * p.xi / T(3);
-  const T xqh = T(2) * p.xi * qh;
+  const T xm1 = p.xm1, xp1 = p.xp1, x23 = p.x23;
+  const T xqh = p.x2 * qh;
   T X[3][3];  // X = Q H
 #pragma unroll
   for (int a = 0; a < DIM; a++)
@@ -112,14 +139,14 @@ __host__ __device__ __forceinline__ void stress(const T q[5], const T h[5],
 // G[a][b] = d_b u_a.  With M = xi D + W = ((xi+1) G + (xi-1) G^T)/2 one has
 // xi D - W = M^T, so S = P + P^T - 2 xi Qt (Q:G^T) with P = M Qt.
 // Writes the five stored components of S.
+// hp = (xi + 1)/2, hm = (xi - 1)/2, x2 = 2 xi.
 template <class T>
 __host__ __device__ __forceinline__ void corotation(const T G[3][3], const T q[5],
-                                           T xi, T s[5]) {
+                                                    T hp, T hm, T x2, T s[5]) {
   const T third = T(1) / T(3);
   const T Qt[3][3] = {{q[0] + third, q[1], q[2]},
                       {q[1], q[3] + third, q[4]},
                       {q[2], q[4], third - q[0] - q[3]}};
-  const T hp = (xi + T(1)) * T(0.5), hm = (xi - T(1)) * T(0.5);
   T M[3][3];
 #pragma unroll
   for (int a = 0; a < 3; a++)
@@ -132,12 +159,18 @@ __host__ __device__ __forceinline__ void corotation(const T G[3][3], const T q[5
   auto P = [&](int a, int b) {
     return fma_(M[a][0], Qt[0][b], fma_(M[a][1], Qt[1][b], M[a][2] * Qt[2][b]));
   };
-  const T t = T(2) * xi * qg;
+  const T t = x2 * qg;
   s[0] = fma_(-t, Qt[0][0], T(2) * P(0, 0));
   s[1] = fma_(-t, Qt[0][1], P(0, 1) + P(1, 0));
   s[2] = fma_(-t, Qt[0][2], P(0, 2) + P(2, 0));
   s[3] = fma_(-t, Qt[1][1], T(2) * P(1, 1));
   s[4] = fma_(-t, Qt[1][2], P(1, 2) + P(2, 1));
+}
+
+template <class T>
+__host__ __device__ __forceinline__ void corotation(const T G[3][3], const T q[5], T xi,
+                                                    T s[5]) {
+  corotation(G, q, (xi + T(1)) * T(0.5), (xi - T(1)) * T(0.5), T(2) * xi, s);
 }
 
 // Right-hand side of Eq. 1 at one cell,
@@ -154,9 +187,8 @@ __host__ __device__ __forceinline__ void be_rhs_adv(const T q[5], const T adv[5]
                                            const Par<T>& p, T r[5]) {
   T h[5], s[5];
   molecular_field(q, lap, p, h);
-  corotation(G, q, p.xi, s);
-  // parameter factor first: no division per cell
-  const T tr3 = (T(2) * p.xi / T(9)) * (G[0][0] + G[1][1] + G[2][2]);
+  corotation(G, q, p.hp, p.hm, p.x2, s);
+  const T tr3 = p.x29 * (G[0][0] + G[1][1] + G[2][2]);
   r[0] = fma_(p.Gamma, h[0], s[0] - adv[0]) - tr3;
   r[1] = fma_(p.Gamma, h[1], s[1] - adv[1]);
   r[2] = fma_(p.Gamma, h[2], s[2] - adv[2]);

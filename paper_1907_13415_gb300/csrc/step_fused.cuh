@@ -53,6 +53,13 @@ constexpr int BA = BXW * BYH;            // box plane area (480)
 // box index of lattice offset (dx, dy) from the tile origin (x0, y0)
 __host__ __device__ constexpr int box_at(int dx, int dy) { return (dy + 2) * BXW + dx + 4; }
 
+// slot s + k of a ring of N plane slots, 0 <= s < N, 0 <= k < N
+template <int N>
+__device__ __forceinline__ int slot_add(int s, int k) {
+  const int r = s + k;
+  return r >= N ? r - N : r;
+}
+
 // Ring-phase thread t -> cell (cx, cy) of the tile plus its one-cell ring,
 // cx in [-1, FTX], cy in [-1, FTY], and its index ri = (cy + 1) RX1 + cx + 1
 // in the ring-region arrays.  The first FTX (FTY + 2) threads take whole rows
@@ -262,9 +269,13 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
   const int z1 = DIM == 3 ? min(z0 + I.tz, d.nz) : 1;
   const int zq0 = DIM == 3 ? z0 - 2 : 0;  // first Q plane loaded
   const int zp0 = DIM == 3 ? z0 - 1 : 0;  // first Pi plane computed
-  auto qslot = [&](int z) { return (z - zq0) % C::NSQ; };
-  auto qpar = [&](int z) { return (uint32_t)(((z - zq0) / C::NSQ) & 1); };
-  auto pslot = [&](int z) { return (z - zp0) % C::NSP; };
+  // z - zq0 and z - zp0 are never negative: unsigned arithmetic lets the
+  // power-of-two slot counts reduce to masks and shifts
+  static_assert((C::NSQ & (C::NSQ - 1)) == 0 && (C::NSP & (C::NSP - 1)) == 0,
+                "power-of-two slot counts");
+  auto qslot = [&](int z) { return (int)((unsigned)(z - zq0) % C::NSQ); };
+  auto qpar = [&](int z) { return ((unsigned)(z - zq0) / C::NSQ) & 1u; };
+  auto pslot = [&](int z) { return (int)((unsigned)(z - zp0) % C::NSP); };
 
   __shared__ T s_mrt[MRT ? Lat::Q : 1];
   if constexpr (MRT) {
@@ -614,32 +625,32 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
   const int x0 = tile.x0, y0 = tile.y0;
   const int z0 = tile.z0;
   const int z1 = DIM == 3 ? min(z0 + I.tz, d.nz) : 1;
-  const int zl0 = DIM == 3 ? z0 - 2 : 0;  // first loaded plane
-  const int zr0 = DIM == 3 ? z0 - 1 : 0;  // first predicted plane
-  auto qs = [&](int z) { return (z - zl0) % C::NSQ; };
-  auto qpar = [&](int z) { return (uint32_t)(((z - zl0) / C::NSQ) & 1); };
-  auto us = [&](int z) { return (z - zl0) % C::NSU; };
-  auto upar = [&](int z) { return (uint32_t)(((z - zl0) / C::NSU) & 1); };
-  auto ps = [&](int z) { return (z - zr0) % C::NSP; };
+  // Plane z of Q^n and u lives in slot (z - z0 + 2) mod NSQ (NSU), Q^P of
+  // plane z in slot (z - z0 + 1) mod NSP.  The loop carries the slots of its
+  // current plane and steps them with slot_add; every plane's copy is waited
+  // on once, in z order, so one phase bit per slot (flipped at each wait)
+  // gives the parity to wait for.
 
   if (tid == 0) {
     for (int s = 0; s < C::NSQ + C::NSU; s++) mbar_init(&qbar[s], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  auto issue_q = [&](int z) {
-    const int s = qs(z);
+  // copies of plane z into Q slot s and u slot t (thread 0)
+  auto issue = [&](int z, int s, int t) {
     mbar_expect_tx(&qbar[s], C::q_tx);
     tma_load_4d(sQ(s), qmap, x0, y0, z + zoff, 0, &qbar[s]);
-  };
-  auto issue_u = [&](int z) {
-    const int s = us(z);
-    mbar_expect_tx(&ubar[s], C::u_tx);
-    tma_load_4d(sU(s), umap, x0, y0, z + zoff, 0, &ubar[s]);
+    mbar_expect_tx(&ubar[t], C::u_tx);
+    tma_load_4d(sU(t), umap, x0, y0, z + zoff, 0, &ubar[t]);
   };
   bool late = false;
-  auto wait_q = [&](int z) { late |= !mbar_wait(&qbar[qs(z)], qpar(z)); };
-  auto wait_u = [&](int z) { late |= !mbar_wait(&ubar[us(z)], upar(z)); };
+  uint32_t qph = 0, uph = 0;  // phase bit per slot
+  auto wait = [&](int s, int t) {
+    late |= !mbar_wait(&qbar[s], (qph >> s) & 1u);
+    late |= !mbar_wait(&ubar[t], (uph >> t) & 1u);
+    qph ^= 1u << s;
+    uph ^= 1u << t;
+  };
   auto abort_block = [&]() {
     if (tid == 0) {
       atomicExch(err, DEV_ERR_TMA_TIMEOUT);
@@ -648,23 +659,18 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     }
   };
 
-  // predictor on the ring cell of ring-phase thread t of plane z: R(Q^n)
-  // and Q^P = Q^n + R
-  auto predict = [&](int z, int t) {
+  // predictor on the ring cell of ring-phase thread t of a plane whose Q^n
+  // and u slots are sq, su (the planes below and above in sqm, sqp, sum,
+  // sup): R(Q^n) and Q^P = Q^n + R into Q^P slot spo
+  auto predict = [&](int t, int sq, int sqm, int sqp, int su, int sum, int sup, int spo) {
     int cx, cy, c;
     ring_cell(t, cx, cy, c);
     const int o = box_at(cx, cy);
-    const T* qc = sQ(qs(z));
-    const T* qm = DIM == 3 ? sQ(qs(z - 1)) : qc;
-    const T* qp = DIM == 3 ? sQ(qs(z + 1)) : qc;
-    const T* uc = sU(us(z));
-    const T* um = DIM == 3 ? sU(us(z - 1)) : uc;
-    const T* up = DIM == 3 ? sU(us(z + 1)) : uc;
     T q[5], adv[5], lap[5], u[3], G[3][3], r[5];
-    box_ugrad<Lat, T, ISO>(uc, um, up, o, u, G);
-    stencil_adv<Lat, T, ISO>(qc, qm, qp, o, BXW, BA, u, q, adv, lap);
+    box_ugrad<Lat, T, ISO>(sU(su), sU(sum), sU(sup), o, u, G);
+    stencil_adv<Lat, T, ISO>(sQ(sq), sQ(sqm), sQ(sqp), o, BXW, BA, u, q, adv, lap);
     be_rhs_adv<T>(q, adv, lap, G, p, r);
-    T* qpo = sQP(ps(z));
+    T* qpo = sQP(spo);
 #pragma unroll
     for (int k = 0; k < 5; k++) qpo[k * A1 + c] = q[k] + r[k];
   };
@@ -677,20 +683,17 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
   const int ic = (ty + 1) * RX1 + (tx + 1);
   const int o2 = box_at(tx, ty);
 
-  // corrector at the tile cell of this thread on plane z
-  auto correct = [&](int z) {
+  // corrector at the tile cell of this thread on plane z, whose Q^n, u and
+  // Q^P slots are sq, su, sp (neighbouring planes in sum, sup, spm, spp)
+  auto correct = [&](int z, int sq, int su, int sum, int sup, int sp, int spm, int spp) {
     if (!cell) return;
-    const T* pc = sQP(ps(z));
-    const T* pm = DIM == 3 ? sQP(ps(z - 1)) : pc;
-    const T* pp = DIM == 3 ? sQP(ps(z + 1)) : pc;
     T qp[5], adv[5], lap[5], u[3], G[3][3], r2[5];
-    box_ugrad<Lat, T, ISO>(sU(us(z)), DIM == 3 ? sU(us(z - 1)) : sU(us(z)),
-                         DIM == 3 ? sU(us(z + 1)) : sU(us(z)), o2, u, G);
-    stencil_adv<Lat, T, ISO>(pc, pm, pp, ic, RX1, A1, u, qp, adv, lap);
+    box_ugrad<Lat, T, ISO>(sU(su), sU(sum), sU(sup), o2, u, G);
+    stencil_adv<Lat, T, ISO>(sQP(sp), sQP(spm), sQP(spp), ic, RX1, A1, u, qp, adv, lap);
     be_rhs_adv<T>(qp, adv, lap, G, p, r2);
     // Q^{n+1} = Q^n + [R(Q^n) + R(Q^P)]/2 = [Q^n + Q^P + R(Q^P)]/2, since
     // Q^P = Q^n + R(Q^n)
-    const T* qn = sQ(qs(z));
+    const T* qn = sQ(sq);
     T out[5];
 #pragma unroll
     for (int k = 0; k < 5; k++) out[k] = (qn[k * BA + o2] + qp[k] + r2[k]) * T(0.5);
@@ -698,49 +701,46 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
   };
 
   if constexpr (DIM == 2) {
-    if (tid == 0) {
-      issue_q(0);
-      issue_u(0);
-    }
-    wait_q(0);
-    wait_u(0);
-    if (tid < C::RING_T) predict(0, tid);
+    if (tid == 0) issue(0, 0, 0);
+    wait(0, 0);
+    if (tid < C::RING_T) predict(tid, 0, 0, 0, 0, 0, 0, 0);
     if (__syncthreads_or(late)) {
       abort_block();
       return;
     }
-    correct(0);
+    correct(0, 0, 0, 0, 0, 0, 0, 0);
   } else {
+    constexpr int NQ = C::NSQ, NU = C::NSU, NP = C::NSP;
+    // planes z0-2 .. z0+2 go to Q and u slots 0..4
     if (tid == 0)
-      for (int z = z0 - 2; z <= z0 + 2; z++) {
-        issue_q(z);
-        issue_u(z);
-      }
-    for (int z = z0 - 2; z <= z0; z++) {
-      wait_q(z);
-      wait_u(z);
-    }
-    if (tid < C::RING_T) predict(z0 - 1, tid);
+      for (int k = 0; k <= 4; k++) issue(z0 - 2 + k, k, k);
+    wait(0, 0);
+    wait(1, 1);
+    wait(2, 2);
+    if (tid < C::RING_T) predict(tid, 1, 0, 2, 1, 0, 2, 0);  // plane z0-1
     if (__syncthreads_or(late)) {
       abort_block();
       return;
     }
-    wait_q(z0 + 1);
-    wait_u(z0 + 1);
-    if (tid < C::RING_T) predict(z0, tid);
+    wait(3, 3);
+    if (tid < C::RING_T) predict(tid, 2, 1, 3, 2, 1, 3, 1);  // plane z0
+    // slots of plane z: Q^n sq, u su, Q^P sp
+    int sq = 2, su = 2, sp = 1;
     for (int z = z0; z < z1; z++) {
-      if (tid == 0 && z + 3 <= z1 + 1) {
-        issue_q(z + 3);
-        issue_u(z + 3);
-      }
-      wait_q(z + 2);
-      wait_u(z + 2);
-      if (tid < C::RING_T) predict(z + 1, tid);
+      const int sq1 = slot_add<NQ>(sq, 1), sq2 = slot_add<NQ>(sq, 2);
+      const int su1 = slot_add<NU>(su, 1), su2 = slot_add<NU>(su, 2);
+      const int sp1 = slot_add<NP>(sp, 1);
+      if (tid == 0 && z + 3 <= z1 + 1) issue(z + 3, slot_add<NQ>(sq, 3), slot_add<NU>(su, 3));
+      wait(sq2, su2);
+      if (tid < C::RING_T) predict(tid, sq1, sq, sq2, su1, su, su2, sp1);  // plane z+1
       if (__syncthreads_or(late)) {
         abort_block();
         return;
       }
-      correct(z);
+      correct(z, sq, su, slot_add<NU>(su, NU - 1), su1, sp, slot_add<NP>(sp, NP - 1), sp1);
+      sq = sq1;
+      su = su1;
+      sp = sp1;
     }
   }
 }

@@ -41,7 +41,8 @@ using namespace nlc;
 int main() {
   Par<OC> p;
   p.A0 = 0.1; p.K = 0.02; p.gamma = 2.7; p.Gamma = 0.3; p.xi = 0.7; p.tau = 1.0;
-  p.rho0 = 1.0; p.inv_tau = 1.0; p.guo = 0.5;
+  p.rho0 = 1.0;
+  derive(p);
   OC q[5] = {0.1, 0.02, 0.01, -0.05, 0.03}, lap[5] = {1e-3, 2e-3, 3e-3, 4e-3, 5e-3};
   OC dq[3][5], G[3][3], u[3] = {1e-3, 2e-3, 3e-3}, F[3] = {1e-5, 2e-5, 3e-5}, h[5], s[5],
      r[5], P[3][3], adv[5];
@@ -54,7 +55,7 @@ int main() {
   g_ops = 0; molecular_field(q, lap, p, h); printf("\"H\": %ld", g_ops);
   g_ops = 0; stress<OC, 3>(q, h, dq, p, P); printf(", \"Pi_3d\": %ld", g_ops);
   g_ops = 0; stress<OC, 2>(q, h, dq, p, P); printf(", \"Pi_2d\": %ld", g_ops);
-  g_ops = 0; corotation(G, q, p.xi, s); printf(", \"S\": %ld", g_ops);
+  g_ops = 0; corotation(G, q, p.hp, p.hm, p.x2, s); printf(", \"S\": %ld", g_ops);
   g_ops = 0; be_rhs_adv(q, adv, lap, G, p, r); printf(", \"R_from_adv\": %ld", g_ops);
   OC g19[19], g9[9], rho;
   for (int i = 0; i < 19; i++) g19[i] = 1e-3 * i;

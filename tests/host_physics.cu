@@ -19,7 +19,8 @@ using namespace nlc;
 static Par<double> par(const double* p) {
   Par<double> r;
   r.A0 = p[0]; r.K = p[1]; r.gamma = p[2]; r.Gamma = p[3]; r.xi = p[4]; r.tau = p[5];
-  r.rho0 = 1.0; r.inv_tau = 1.0 / p[5]; r.guo = 1.0 - 0.5 / p[5];
+  r.rho0 = 1.0;
+  derive(r);
   return r;
 }
 
@@ -114,7 +115,8 @@ template <class T>
 static Par<T> parT(const T* p) {
   Par<T> r;
   r.A0 = p[0]; r.K = p[1]; r.gamma = p[2]; r.Gamma = p[3]; r.xi = p[4]; r.tau = p[5];
-  r.rho0 = T(1.0); r.inv_tau = T(1.0) / p[5]; r.guo = T(1.0) - T(0.5) / p[5];
+  r.rho0 = T(1.0);
+  derive(r);
   return r;
 }
 

@@ -44,7 +44,7 @@ def test_operation_counts(tmp_path):
     assert 200 <= c["Pi_3d"] <= 260 and c["Pi_2d"] < c["Pi_3d"]
     assert 90 <= c["S"] <= 130
     # R from the advection term = H + S + the assembly with the projection
-    assert c["R_from_adv"] == c["H"] + c["S"] + 22
+    assert c["R_from_adv"] == c["H"] + c["S"] + 20
     # MRT costs two transforms of the non-conserved moments on top of BGK
     assert c["mrt_d3q19"] > 2.5 * c["bgk_d3q19"]
     lb, be = step_flops(c)
