@@ -327,6 +327,14 @@ def run_ours(args, w):
     sim.set_fields(Q0)
     cells = w.n_cells
 
+    # chunk depth of the fused kernels: autotuned on this state (the state is
+    # restored afterwards), the library default, or fixed
+    tune = None
+    if args.chunk < 0:
+        tune = sim.autotune(args.tune_steps)
+    else:
+        sim.set_chunk(args.chunk)
+
     # warm-up
     sim.step(args.warmup)
     torch.cuda.synchronize()
@@ -401,6 +409,7 @@ def run_ours(args, w):
                "steps": args.e2e_steps,
                "what": "nlc_set_fields(Q from pinned host) + nlc_step(1) + "
                        "nlc_observables() per step"}
+    nlc_chunk = sim.chunk()
     sim.close()
 
     cpu = None
@@ -427,7 +436,9 @@ def run_ours(args, w):
                        "gamma": w.params["gamma"],
                        "parallelism": f"replicas{ws}",
                        "collision": "mrt" if args.mrt else "bgk",
+                       "chunk": nlc_chunk,
                        "l2": "inputs larger than L2 (3.2 GB of state)"},
+            "autotune": tune,
             "roofline": roofline, "step_roofline": step_roofline,
             "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
@@ -582,6 +593,11 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=0,
                     help="steps of the adjoint workload (default: its own 2000)")
     ap.add_argument("--graph-steps", type=int, default=50)
+    ap.add_argument("--chunk", type=int, default=-1,
+                    help="z planes per block of the fused kernels: -1 autotune "
+                         "(default), 0 the library default, N fixed")
+    ap.add_argument("--tune-steps", type=int, default=8,
+                    help="steps timed per candidate chunk depth by the autotuner")
     args = ap.parse_args()
     # at least three untimed warm-up steps (reported as the count used)
     args.warmup = max(args.warmup, 3)

@@ -129,6 +129,16 @@ typedef struct {
   double dgamma, dK, dGamma;
 } nlc_grad;
 
+/* Result of nlc_autotune. */
+typedef struct {
+  int32_t chunk;         /* z planes per block chosen for the fused kernels */
+  int32_t from_cache;    /* 1: taken from the cache file, nothing was timed */
+  int32_t candidates;    /* chunk depths timed                              */
+  int32_t trial_steps;   /* steps timed per candidate                       */
+  double best_ms;        /* time per step of the chosen depth (0 if cached) */
+  double default_ms;     /* time per step of the default depth (0 if cached)*/
+} nlc_tune;
+
 typedef struct nlc_ctx nlc_ctx;
 
 /* Creates a context for one lattice on the current CUDA device and
@@ -211,6 +221,35 @@ NLC_API nlc_status nlc_set_check(nlc_ctx* ctx, int32_t every);
 
 /* Selects the kernel schedule (NLC_SCHED_*) for later nlc_step calls. */
 NLC_API nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule);
+
+/* Depth of the z-chunks of the fused schedule on D3Q19 lattices: each
+ * thread block of the two step kernels marches through `chunk` planes of one
+ * 32 x 8 column of the lattice (capped at nz), so the chunk depth trades the
+ * two extra planes every chunk recomputes against the number of blocks the
+ * GPU spreads over its SMs.  It changes no result: every depth computes the
+ * same step bit for bit.  chunk = 0 restores the library's default choice.
+ * A runtime choice of this library; the paper has no counterpart.  No-op on
+ * D2Q9.  Synchronises the stream.  Errors: NLC_EINVAL (chunk < 0). */
+NLC_API nlc_status nlc_set_chunk(nlc_ctx* ctx, int32_t chunk);
+
+/* Chunk depth in use for lattice inst (1 on D2Q9). */
+NLC_API int32_t nlc_get_chunk(const nlc_ctx* ctx, int32_t inst);
+
+/* Autotuner of the fused schedule (a runtime choice of this library; the
+ * paper has no counterpart).  Times trial_steps fused steps of the context's
+ * own state for each candidate chunk depth (see nlc_set_chunk) with CUDA
+ * events, restores the state bit for bit afterwards (populations and Q of
+ * every lattice, buffer parity; the step counters are not touched) and keeps
+ * the fastest depth.  If the environment variable NLC_TUNE_CACHE names a
+ * file, results are cached there as a flat JSON object keyed by lattice,
+ * precision, extents, collision, stencils and GPU (name, SM count): a key
+ * found there is applied without timing (out->from_cache = 1), a new result
+ * is added.  Needs two extra copies of the populations and Q of the whole
+ * context in device memory while it runs (freed before it returns).  No-op
+ * on D2Q9 (out->chunk = 1).  out may be NULL.  Synchronises the stream.
+ * Errors: NLC_EINVAL (trial_steps < 1), NLC_ENOMEM, NLC_ECUDA,
+ * NLC_ETIMEOUT. */
+NLC_API nlc_status nlc_autotune(nlc_ctx* ctx, int32_t trial_steps, nlc_tune* out);
 
 /* Replaces the state of lattice inst with Q5, rho and u (host float64,
  * layouts above).  The populations are set to the equilibrium

@@ -136,8 +136,6 @@ class Engine final : public EngineBase {
     mrt_on_.assign(n, false);
     std::vector<InstDev<T, G>> dev(n);
     std::vector<CUtensorMap> qmaps(2 * n), umaps(n);
-    std::vector<TileRef> tiles;
-    int64_t tiles_so_far = 0;
     maps_ok_ = true;
     cudaStream_t st = args_.stream;
     nlc_status s;
@@ -165,9 +163,6 @@ class Engine final : public EngineBase {
                  encode_field_map<T>(&qmaps[2 * i], q0, I.L.nxp, I.L.nyp, I.L.nzp, 5, BXW, BYH) &&
                  encode_field_map<T>(&qmaps[2 * i + 1], q1, I.L.nxp, I.L.nyp, I.L.nzp, 5, BXW, BYH) &&
                  encode_field_map<T>(&umaps[i], u, I.L.nxp, I.L.nyp, I.L.nzp, DIM, BXW, BYH);
-      I.tz = fused_tz<Lat>(I.d, tiles_so_far);
-      append_tiles<Lat>(i, I.d, I.tz, &tiles);
-      tiles_so_far = (int64_t)tiles.size();
       dev[i].d = I.d;
       dev[i].p = I.p;
       dev[i].g[0] = I.g[0];
@@ -176,19 +171,157 @@ class Engine final : public EngineBase {
       dev[i].q[1] = I.q[1];
       dev[i].u = I.u;
       dev[i].mrt = nullptr;
-      dev[i].tz = I.tz;
+      dev[i].tz = 1;
     }
     if ((s = alloc(&bad_, 1)) || (s = alloc(&derr_, 1)) || (s = alloc(&insts_dev_, (size_t)n)) ||
-        (s = alloc(&qmaps_dev_, (size_t)2 * n)) || (s = alloc(&umaps_dev_, (size_t)n)) ||
-        (s = alloc(&tiles_dev_, tiles.size())))
+        (s = alloc(&qmaps_dev_, (size_t)2 * n)) || (s = alloc(&umaps_dev_, (size_t)n)))
       return s;
-    ntiles_ = (int)tiles.size();
     NLC_CK(cudaMemsetAsync(derr_, 0, sizeof(unsigned), st));
     NLC_CK(cudaMemcpyAsync(insts_dev_, dev.data(), sizeof(InstDev<T, G>) * n, cudaMemcpyHostToDevice, st));
     NLC_CK(cudaMemcpyAsync(qmaps_dev_, qmaps.data(), sizeof(CUtensorMap) * 2 * n, cudaMemcpyHostToDevice, st));
     NLC_CK(cudaMemcpyAsync(umaps_dev_, umaps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, st));
-    NLC_CK(cudaMemcpyAsync(tiles_dev_, tiles.data(), sizeof(TileRef) * tiles.size(), cudaMemcpyHostToDevice, st));
+    return set_chunk(0);
+  }
+
+  // ---------------------------------------------------------------- chunks
+  // Rebuilds the joint tile list with chunk depth tz (0: the default per
+  // lattice), updates the per-lattice depth on the device and drops captured
+  // step graphs (they hold the old list).  Synchronises the stream.
+  nlc_status set_chunk(int tz) override {
+    cudaStream_t st = args_.stream;
+    std::vector<TileRef> tiles;
+    for (size_t i = 0; i < inst_.size(); i++) {
+      InstHost<T, G>& I = inst_[i];
+      if (DIM == 2)
+        I.tz = 1;
+      else
+        I.tz = tz > 0 ? std::min(tz, I.d.nz) : fused_tz<Lat>(I.d, (int64_t)tiles.size());
+      append_tiles<Lat>((int)i, I.d, I.tz, &tiles);
+    }
+    NLC_CK(cudaStreamSynchronize(st));  // no step may still read the old list
+    if (tiles.size() > tiles_cap_) {
+      if (tiles_dev_) {
+        cudaFree(tiles_dev_);
+        allocs_.erase(std::remove(allocs_.begin(), allocs_.end(), (void*)tiles_dev_),
+                      allocs_.end());
+        tiles_dev_ = nullptr;
+      }
+      nlc_status s = alloc(&tiles_dev_, tiles.size());
+      if (s) return s;
+      tiles_cap_ = tiles.size();
+    }
+    ntiles_ = (int)tiles.size();
+    NLC_CK(cudaMemcpyAsync(tiles_dev_, tiles.data(), sizeof(TileRef) * tiles.size(),
+                           cudaMemcpyHostToDevice, st));
+    for (size_t i = 0; i < inst_.size(); i++)
+      NLC_CK(cudaMemcpyAsync(&insts_dev_[i].tz, &inst_[i].tz, sizeof(int), cudaMemcpyHostToDevice,
+                             st));
     NLC_CK(cudaStreamSynchronize(st));
+    drop_graphs();
+    return NLC_OK;
+  }
+
+  int chunk(int i) const override { return inst_[i].tz; }
+
+  // Candidate depths are timed on the current state, which is saved first
+  // and restored afterwards (the populations and Q of buffer parity cur_;
+  // the other buffers are rewritten by every step before they are read).
+  nlc_status autotune(int trial_steps, nlc_tune* out) override {
+    cudaStream_t st = args_.stream;
+    *out = nlc_tune{};
+    out->trial_steps = trial_steps;
+    if (DIM == 2) {
+      out->chunk = 1;
+      return NLC_OK;
+    }
+    if (!maps_ok_) {
+      err = "TMA tensor maps unavailable: the fused schedule cannot run";
+      return NLC_EUNSUPPORTED;
+    }
+    int maxz = 1;
+    for (const auto& I : inst_) maxz = std::max(maxz, I.d.nz);
+    std::vector<int> cand = {0};  // 0: the default choice
+    for (int c : {4, 6, 8, 12, 16, 24, 32, 48, 64})
+      if (c <= maxz) cand.push_back(c);
+    // saved state
+    const int cur0 = cur_;
+    std::vector<G*> gsave(inst_.size(), nullptr);
+    std::vector<T*> qsave(inst_.size(), nullptr);
+    auto release = [&]() {
+      for (G* p : gsave) cudaFree(p);
+      for (T* p : qsave) cudaFree(p);
+    };
+    for (size_t i = 0; i < inst_.size(); i++) {
+      InstHost<T, G>& I = inst_[i];
+      const size_t gb = sizeof(G) * Q * I.d.n, qb = sizeof(T) * 5 * I.L.comp;
+      if (cudaMalloc(&gsave[i], gb) != cudaSuccess || cudaMalloc(&qsave[i], qb) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        err = "nlc_autotune: no device memory for the saved state";
+        return NLC_ENOMEM;
+      }
+      cudaMemcpyAsync(gsave[i], I.g[cur0], gb, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(qsave[i], I.q[cur0].base, qb, cudaMemcpyDeviceToDevice, st);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    nlc_status s = NLC_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      err = "nlc_autotune: cudaEventCreate failed";
+      s = NLC_ECUDA;
+    }
+    const bool timing = timer.on;
+    timer.on = false;
+    double best = 0.0;
+    int best_c = -1;
+    std::vector<std::vector<int>> timed;  // per-lattice depths already timed
+    for (size_t k = 0; k < cand.size() && s == NLC_OK; k++) {
+      if ((s = set_chunk(cand[k]))) break;
+      std::vector<int> depths;
+      for (const auto& I : inst_) depths.push_back(I.tz);
+      if (std::find(timed.begin(), timed.end(), depths) != timed.end()) continue;
+      timed.push_back(depths);
+      if ((s = step_fused(st))) break;  // warm-up
+      float ms = 0.f;
+      if (cudaEventRecord(e0, st) != cudaSuccess) s = NLC_ECUDA;
+      for (int j = 0; j < trial_steps && s == NLC_OK; j++) s = step_fused(st);
+      if (s) break;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        err = "nlc_autotune: event timing failed";
+        s = NLC_ECUDA;
+        break;
+      }
+      const double per = ms / trial_steps;
+      out->candidates++;
+      if (cand[k] == 0) out->default_ms = per;
+      if (best_c < 0 || per < best) {
+        best = per;
+        best_c = cand[k];
+      }
+    }
+    timer.on = timing;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    // restore the state whatever happened above
+    cur_ = cur0;
+    for (size_t i = 0; i < inst_.size(); i++) {
+      InstHost<T, G>& I = inst_[i];
+      cudaMemcpyAsync(I.g[cur0], gsave[i], sizeof(G) * Q * I.d.n, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(I.q[cur0].base, qsave[i], sizeof(T) * 5 * I.L.comp,
+                      cudaMemcpyDeviceToDevice, st);
+    }
+    const cudaError_t ce = cudaStreamSynchronize(st);
+    release();
+    if (s) return s;
+    if (ce != cudaSuccess) {
+      err = std::string("nlc_autotune: ") + cudaGetErrorString(ce);
+      return NLC_ECUDA;
+    }
+    if ((s = device_error())) return s;
+    if ((s = set_chunk(best_c))) return s;
+    out->best_ms = best;
+    out->chunk = 1;
+    for (const auto& I : inst_) out->chunk = std::max(out->chunk, I.tz);
     return NLC_OK;
   }
 
@@ -934,6 +1067,7 @@ class Engine final : public EngineBase {
   CUtensorMap* qmaps_dev_ = nullptr;
   CUtensorMap* umaps_dev_ = nullptr;
   TileRef* tiles_dev_ = nullptr;
+  size_t tiles_cap_ = 0;
   int ntiles_ = 0;
   bool maps_ok_ = false;
   unsigned long long* bad_ = nullptr;

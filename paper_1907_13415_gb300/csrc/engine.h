@@ -79,6 +79,13 @@ struct EngineBase {
   virtual nlc_status set_params(int inst, const nlc_params& p) = 0;
   virtual nlc_status set_mrt(int inst, const double* rates) = 0;
   virtual nlc_status set_stencil(bool isotropic) = 0;
+  // z planes per block of the fused kernels on three-dimensional lattices:
+  // tz > 0 for every lattice (capped at its nz), 0 for the default choice
+  virtual nlc_status set_chunk(int tz) = 0;
+  virtual int chunk(int inst) const = 0;
+  // times `trial_steps` fused steps for each candidate chunk depth on the
+  // current state, restores the state and keeps the fastest depth
+  virtual nlc_status autotune(int trial_steps, nlc_tune* out) = 0;
   virtual nlc_status step(int64_t n, int schedule) = 0;
   virtual nlc_status set_fields(int inst, const double* Q5, const double* rho,
                                 const double* u) = 0;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <algorithm>
 #include <cstring>
 #include <memory>
@@ -15,6 +16,7 @@
 #include "../../include/nlc.h"
 #include "engine.h"
 #include "lattice.cuh"
+#include "tune_cache.h"
 
 static_assert(nlc::KID_COUNT == NLC_N_KERNELS, "kernel id table out of sync");
 
@@ -26,6 +28,8 @@ struct nlc_ctx {
   int schedule = NLC_SCHED_FUSED;
   int check_every = 0;
   std::vector<int64_t> steps;  // per lattice, since its last nlc_set_fields
+  std::vector<char> mrt;       // per lattice: MRT collision on
+  bool iso = false;            // isotropic stencils
   std::unique_ptr<nlc::EngineBase> eng;
   std::string err;
 };
@@ -117,6 +121,7 @@ nlc_status nlc_create_batch(int32_t n, const nlc_grid* grids,
   ctx->grids.assign(grids, grids + n);
   ctx->params.assign(params, params + n);
   ctx->steps.assign(n, 0);
+  ctx->mrt.assign(n, 0);
   ctx->stream = (cudaStream_t)stream;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
     cudaGetLastError();
@@ -174,6 +179,7 @@ nlc_status nlc_set_mrt(nlc_ctx* ctx, int32_t inst, const double* rates, int32_t 
   }
   nlc_status st = ctx->eng->set_mrt(inst, rates);
   if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  ctx->mrt[inst] = rates != nullptr;
   return NLC_OK;
 }
 
@@ -183,6 +189,7 @@ nlc_status nlc_set_stencil(nlc_ctx* ctx, int32_t kind) {
     return fail(ctx, NLC_EINVAL, "unknown stencil");
   nlc_status st = ctx->eng->set_stencil(kind == NLC_STENCIL_ISOTROPIC);
   if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  ctx->iso = kind == NLC_STENCIL_ISOTROPIC;
   return NLC_OK;
 }
 
@@ -200,6 +207,67 @@ nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule) {
   if (schedule != NLC_SCHED_FUSED && schedule != NLC_SCHED_UNFUSED)
     return fail(ctx, NLC_EINVAL, "unknown schedule");
   ctx->schedule = schedule;
+  return NLC_OK;
+}
+
+nlc_status nlc_set_chunk(nlc_ctx* ctx, int32_t chunk) {
+  if (!ctx) return NLC_EINVAL;
+  if (chunk < 0) return fail(ctx, NLC_EINVAL, "negative chunk depth");
+  nlc_status st = ctx->eng->set_chunk(chunk);
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  return NLC_OK;
+}
+
+int32_t nlc_get_chunk(const nlc_ctx* ctx, int32_t inst) {
+  if (!ctx || inst < 0 || inst >= (int32_t)ctx->grids.size()) return -1;
+  return ctx->eng->chunk(inst);
+}
+
+// Cache key of the autotuner: what the timing depends on (lattice type,
+// precision, extents, collision and stencils of every lattice, the GPU).
+static std::string tune_key(const nlc_ctx* ctx) {
+  const nlc_grid& g0 = ctx->grids[0];
+  std::string k = g0.lattice == NLC_D2Q9 ? "D2Q9" : "D3Q19";
+  k += g0.precision == NLC_FP64 ? "/fp64" : (g0.precision == NLC_FP32 ? "/fp32" : "/fp32_qf64");
+  k += "/n" + std::to_string(ctx->grids.size()) + "/";
+  for (size_t i = 0; i < ctx->grids.size(); i++) {
+    const nlc_grid& g = ctx->grids[i];
+    if (i) k += ",";
+    k += std::to_string(g.nx) + "x" + std::to_string(g.ny) + "x" + std::to_string(g.nz);
+    if (ctx->mrt[i]) k += "m";
+  }
+  k += ctx->iso ? "/iso" : "/std";
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess)
+    k += std::string("/") + prop.name + "/" + std::to_string(prop.multiProcessorCount);
+  else
+    cudaGetLastError();
+  return k;
+}
+
+nlc_status nlc_autotune(nlc_ctx* ctx, int32_t trial_steps, nlc_tune* out) {
+  if (!ctx) return NLC_EINVAL;
+  if (trial_steps < 1) return fail(ctx, NLC_EINVAL, "trial_steps must be at least 1");
+  nlc_tune res{};
+  res.trial_steps = trial_steps;
+  const char* env = std::getenv("NLC_TUNE_CACHE");
+  const std::string path = env ? env : "";
+  const std::string key = tune_key(ctx);
+  long cached = 0;
+  nlc_status st;
+  if (!path.empty() && nlc::tune_cache_get(path, key, &cached) && cached >= 0) {
+    if ((st = ctx->eng->set_chunk((int)cached)) != NLC_OK) return fail(ctx, st, ctx->eng->err);
+    res.from_cache = 1;
+    res.chunk = 1;
+    for (size_t i = 0; i < ctx->grids.size(); i++)
+      res.chunk = std::max(res.chunk, (int32_t)ctx->eng->chunk((int)i));
+  } else {
+    if ((st = ctx->eng->autotune(trial_steps, &res)) != NLC_OK)
+      return fail(ctx, st, ctx->eng->err);
+    if (!path.empty() && !nlc::tune_cache_put(path, key, res.chunk))
+      return fail(ctx, NLC_EINVAL, "nlc_autotune: cannot write the cache file " + path);
+  }
+  if (out) *out = res;
   return NLC_OK;
 }
 

@@ -184,8 +184,36 @@ __device__ __forceinline__ void stress_ring_cell(int t, const T* __restrict__ sq
   ring_cell(t, cx, cy, c);
   const int o = box_at(cx, cy);
   T q[5], dq2[3][5], lap[5], h[5], P[3][3];
+  // FP32: components (0, 1) and (2, 3) as packed pairs (same operations in
+  // the same order as the scalar form, lane by lane)
+  constexpr int KP = (std::is_same<T, float>::value && !ISO) ? 4 : 0;
+  if constexpr (KP == 4) {
 #pragma unroll
-  for (int k = 0; k < 5; k++) {
+    for (int k = 0; k < 4; k += 2) {
+      const float* F0 = sq + k * BA;
+      const float* F1 = F0 + BA;
+      const float2 v = pk(F0[o], F1[o]);
+      const float2 xp = pk(F0[o + 1], F1[o + 1]), xm = pk(F0[o - 1], F1[o - 1]);
+      const float2 yp = pk(F0[o + BXW], F1[o + BXW]), ym = pk(F0[o - BXW], F1[o - BXW]);
+      float2 sum = padd(padd(xp, xm), padd(yp, ym));
+      float2 dz = bc(0.0f);
+      if (DIM == 3) {
+        const float2 zp = pk(sqp[k * BA + o], sqp[(k + 1) * BA + o]);
+        const float2 zm = pk(sqm[k * BA + o], sqm[(k + 1) * BA + o]);
+        sum = padd(sum, padd(zp, zm));
+        dz = psub(zp, zm);
+      }
+      const float2 dx = psub(xp, xm), dy = psub(yp, ym);
+      const float2 l = pfma(bc(-2.0f * DIM), v, sum);
+      q[k] = v.x, q[k + 1] = v.y;
+      dq2[0][k] = dx.x, dq2[0][k + 1] = dx.y;
+      dq2[1][k] = dy.x, dq2[1][k + 1] = dy.y;
+      dq2[2][k] = dz.x, dq2[2][k + 1] = dz.y;
+      lap[k] = l.x, lap[k + 1] = l.y;
+    }
+  }
+#pragma unroll
+  for (int k = KP; k < 5; k++) {
     if constexpr (ISO) {
       const int ok = k * BA + o;
       auto at = [&](int dx, int dy, int dz) {
@@ -466,6 +494,9 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     if (tid < C::RING_T)
       stress_ring_cell<Lat, T, ISO>(tid, sQ(qslot(z0)), sQ(qslot(z0 - 1)), sQ(qslot(z0 + 1)),
                                sP(pslot(z0)), p);
+    // the first copy of the loop (plane z0 + 3) goes to the slot of Q(z0 - 1),
+    // which the ring phase of plane z0 just above still reads
+    __syncthreads();
     for (int z = z0; z < z1; z++) {
       // Q(z+3) reuses the slot of Q(z-1), last read by the ring phase of
       // plane z, which every thread finished before the previous barrier
@@ -525,8 +556,26 @@ __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
                                           T u[3], T G[3][3]) {
   constexpr int DIM = Lat::DIM;
   const T half = T(0.5);
+  // FP32: u_x and u_y as a packed pair
+  constexpr int AP = (std::is_same<T, float>::value && !ISO) ? 2 : 0;
+  if constexpr (AP == 2) {
+    const float* F0 = c;
+    const float* F1 = c + BA;
+    const float2 h2 = bc(0.5f);
+    const float2 gx = pmul(psub(pk(F0[o + 1], F1[o + 1]), pk(F0[o - 1], F1[o - 1])), h2);
+    const float2 gy = pmul(psub(pk(F0[o + BXW], F1[o + BXW]), pk(F0[o - BXW], F1[o - BXW])), h2);
+    u[0] = F0[o], u[1] = F1[o];
+    G[0][0] = gx.x, G[1][0] = gx.y;
+    G[0][1] = gy.x, G[1][1] = gy.y;
+    if (DIM == 3) {
+      const float2 gz = pmul(psub(pk(pp[o], pp[BA + o]), pk(m[o], m[BA + o])), h2);
+      G[0][2] = gz.x, G[1][2] = gz.y;
+    } else {
+      G[0][2] = G[1][2] = 0.0f;
+    }
+  }
 #pragma unroll
-  for (int a = 0; a < 3; a++) {
+  for (int a = AP; a < 3; a++) {
     if (ISO && a < DIM) {
       const int oa = a * BA + o;
       auto at = [&](int dx, int dy, int dz) {
@@ -563,8 +612,34 @@ __device__ __forceinline__ void stencil_adv(const T* __restrict__ c, const T* __
                                             const T u[3], T q[5], T adv[5], T lap[5]) {
   constexpr int DIM = Lat::DIM;
   const T uh0 = u[0] * T(0.5), uh1 = u[1] * T(0.5), uh2 = u[2] * T(0.5);
+  // FP32: components (0, 1) and (2, 3) as packed pairs (same operations in
+  // the same order as the scalar form, lane by lane)
+  constexpr int KP = (std::is_same<T, float>::value && !ISO) ? 4 : 0;
+  if constexpr (KP == 4) {
+    const float2 a0 = bc(uh0), a1 = bc(uh1), a2 = bc(uh2);
 #pragma unroll
-  for (int k = 0; k < 5; k++) {
+    for (int k = 0; k < 4; k += 2) {
+      const float* F0 = c + k * comp;
+      const float* F1 = F0 + comp;
+      const float2 v = pk(F0[o], F1[o]);
+      const float2 xp = pk(F0[o + 1], F1[o + 1]), xm = pk(F0[o - 1], F1[o - 1]);
+      const float2 yp = pk(F0[o + row], F1[o + row]), ym = pk(F0[o - row], F1[o - row]);
+      float2 a = pfma(a0, psub(xp, xm), pmul(a1, psub(yp, ym)));
+      float2 sum = padd(padd(xp, xm), padd(yp, ym));
+      if (DIM == 3) {
+        const float2 zp = pk(pp[k * comp + o], pp[(k + 1) * comp + o]);
+        const float2 zm = pk(m[k * comp + o], m[(k + 1) * comp + o]);
+        a = pfma(a2, psub(zp, zm), a);
+        sum = padd(sum, padd(zp, zm));
+      }
+      const float2 l = pfma(bc(-2.0f * DIM), v, sum);
+      q[k] = v.x, q[k + 1] = v.y;
+      adv[k] = a.x, adv[k + 1] = a.y;
+      lap[k] = l.x, lap[k + 1] = l.y;
+    }
+  }
+#pragma unroll
+  for (int k = KP; k < 5; k++) {
     if constexpr (ISO) {
       const int ok = k * comp + o;
       auto at = [&](int dx, int dy, int dz) {

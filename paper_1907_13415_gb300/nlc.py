@@ -59,6 +59,15 @@ class nlc_loss(ctypes.Structure):
                 ("w_velocity", ctypes.c_double)]
 
 
+class nlc_tune(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("trial_steps", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class nlc_grad(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("loss", "radius", "u_l2", "dgamma", "dK", "dGamma")]
@@ -98,6 +107,9 @@ def load(build_if_missing=True):
         "nlc_set_mrt": ([P, I32, P, I32], I32),
         "nlc_set_stencil": ([P, I32], I32),
         "nlc_set_schedule": ([P, I32], I32),
+        "nlc_set_chunk": ([P, I32], I32),
+        "nlc_get_chunk": ([P, I32], I32),
+        "nlc_autotune": ([P, I32, ctypes.POINTER(nlc_tune)], I32),
         "nlc_set_fields": ([P, I32, P, P, P], I32),
         "nlc_get_fields": ([P, I32, P, P, P], I32),
         "nlc_get_populations": ([P, I32, P], I32),
@@ -132,7 +144,8 @@ def exported_symbols():
             "nlc_observables", "nlc_last_error", "nlc_destroy",
             "nlc_lattice_velocities", "nlc_version", "nlc_set_timing",
             "nlc_get_timing", "nlc_timing_name", "nlc_save", "nlc_load",
-            "nlc_adjoint", "nlc_observables_static"]
+            "nlc_adjoint", "nlc_observables_static", "nlc_set_chunk",
+            "nlc_get_chunk", "nlc_autotune"]
 
 
 def _check(ctx, status):
@@ -215,6 +228,20 @@ def nlc_set_graph(ctx, steps):
 
 def nlc_set_schedule(ctx, schedule):
     _check(ctx, load().nlc_set_schedule(ctx, schedule))
+
+
+def nlc_set_chunk(ctx, chunk):
+    _check(ctx, load().nlc_set_chunk(ctx, int(chunk)))
+
+
+def nlc_get_chunk(ctx, inst=0):
+    return int(load().nlc_get_chunk(ctx, int(inst)))
+
+
+def nlc_autotune(ctx, trial_steps):
+    out = nlc_tune()
+    _check(ctx, load().nlc_autotune(ctx, int(trial_steps), ctypes.byref(out)))
+    return out.as_dict()
 
 
 def nlc_set_fields(ctx, inst, Q5, rho=None, u=None):
@@ -372,6 +399,15 @@ class Batch:
     def step(self, n=1):
         nlc_step(self.ctx, n)
 
+    def set_chunk(self, chunk):
+        nlc_set_chunk(self.ctx, chunk)
+
+    def chunk(self, i=0):
+        return nlc_get_chunk(self.ctx, i)
+
+    def autotune(self, trial_steps=10):
+        return nlc_autotune(self.ctx, trial_steps)
+
     def observables(self, i, profile=False):
         prof = np.empty(self.shapes[i][2]) if profile else None
         d = nlc_observables(self.ctx, i, prof).as_dict()
@@ -438,6 +474,15 @@ class Simulation:
 
     def step(self, n=1):
         nlc_step(self.ctx, n)
+
+    def set_chunk(self, chunk):
+        nlc_set_chunk(self.ctx, chunk)
+
+    def chunk(self):
+        return nlc_get_chunk(self.ctx, 0)
+
+    def autotune(self, trial_steps=10):
+        return nlc_autotune(self.ctx, trial_steps)
 
     def observables(self, profile=False):
         prof = np.empty(self.shape[2]) if profile else None

@@ -1,0 +1,149 @@
+"""Chunk depth of the fused kernels (nlc_set_chunk) and the autotuner
+(nlc_autotune).  The depth only changes how the lattice is split among
+thread blocks, so every depth must give the same step bit for bit; the
+autotuner must leave the state exactly as it found it, and its cache file
+must be written once and then read back."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_1907_13415_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def droplet(shape=(23, 20, 40), seed=31):
+    base = wl.sphere_256()
+    return base.with_(shape=shape, size=0.3 * min(shape), noise=1e-3, seed=seed)
+
+
+def state(sim):
+    Q, rho, u = sim.get_fields()
+    return Q, sim.get_populations(), rho, u
+
+
+@pytest.mark.parametrize("precision", ["NLC_FP32", "NLC_FP64"])
+def test_every_chunk_depth_gives_the_same_step(precision):
+    from paper_1907_13415_gb300 import nlc
+    prec = getattr(nlc, precision)
+    w = droplet()
+    ref = None
+    for chunk in (0, 1, 2, 3, 4, 7, 23, 64):
+        sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=prec,
+                             stream=stream())
+        sim.set_chunk(chunk)
+        assert sim.chunk() == (min(chunk, w.shape[0]) if chunk else sim.chunk())
+        sim.set_fields(w.initial_q5())
+        sim.step(7)
+        got = state(sim)
+        sim.close()
+        if ref is None:
+            ref = got
+            continue
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), chunk
+
+
+def test_chunk_change_between_steps_and_graphs():
+    """A new depth applies to the next step, also with graph replay."""
+    from paper_1907_13415_gb300 import nlc
+    w = droplet(seed=32)
+    sims = []
+    for chunks in ((0, 0), (5, 2)):
+        sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                             stream=stream())
+        sim.set_graph(3)
+        sim.set_fields(w.initial_q5())
+        sim.set_chunk(chunks[0])
+        sim.step(7)
+        sim.set_chunk(chunks[1])
+        sim.step(6)
+        sims.append(state(sim))
+        sim.close()
+    for a, b in zip(*sims):
+        assert np.array_equal(a, b)
+
+
+def test_autotune_keeps_the_state_and_the_trajectory(tmp_path, monkeypatch):
+    from paper_1907_13415_gb300 import nlc
+    monkeypatch.delenv("NLC_TUNE_CACHE", raising=False)
+    w = droplet(shape=(40, 24, 64), seed=33)
+    tuned = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                           stream=stream())
+    plain = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                           stream=stream())
+    for s in (tuned, plain):
+        s.set_fields(w.initial_q5())
+        s.step(3)   # an odd number: the state sits in the second buffer
+    before = state(tuned)
+    r = tuned.autotune(trial_steps=3)
+    assert r["from_cache"] == 0 and r["candidates"] >= 2 and r["trial_steps"] == 3
+    assert r["best_ms"] > 0 and r["default_ms"] >= r["best_ms"]
+    assert tuned.chunk() == r["chunk"] and 1 <= r["chunk"] <= w.shape[0]
+    after = state(tuned)
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    assert tuned.observables()["step"] == 3
+    for s in (tuned, plain):
+        s.step(5)
+    for a, b in zip(state(tuned), state(plain)):
+        assert np.array_equal(a, b)
+    tuned.close()
+    plain.close()
+
+
+def test_autotune_cache_is_written_then_read(tmp_path, monkeypatch):
+    from paper_1907_13415_gb300 import nlc
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("NLC_TUNE_CACHE", str(path))
+    w = droplet(shape=(16, 16, 32), seed=34)
+    first = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                           stream=stream())
+    first.set_fields(w.initial_q5())
+    r1 = first.autotune(trial_steps=2)
+    first.close()
+    assert r1["from_cache"] == 0
+    cache = json.loads(path.read_text())
+    assert len(cache) == 1
+    (key, val), = cache.items()
+    assert key.startswith("D3Q19/fp32/n1/32x16x16/std/") and val == r1["chunk"]
+    second = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                            stream=stream())
+    r2 = second.autotune(trial_steps=2)
+    assert r2["from_cache"] == 1 and r2["chunk"] == r1["chunk"]
+    assert second.chunk() == r1["chunk"]
+    # another stencil is another key
+    second.set_stencil(nlc.NLC_STENCIL_ISOTROPIC)
+    r3 = second.autotune(trial_steps=2)
+    assert r3["from_cache"] == 0
+    assert len(json.loads(path.read_text())) == 2
+    second.close()
+
+
+def test_autotune_single_plane_lattices_have_no_chunks(monkeypatch):
+    from paper_1907_13415_gb300 import nlc
+    monkeypatch.delenv("NLC_TUNE_CACHE", raising=False)
+    w = wl.disc_256().with_(shape=(1, 32, 48), size=10)
+    sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                         stream=stream())
+    r = sim.autotune(trial_steps=2)
+    assert r["chunk"] == 1 and r["candidates"] == 0 and sim.chunk() == 1
+    with pytest.raises(nlc.NlcError):
+        sim.autotune(trial_steps=0)
+    with pytest.raises(nlc.NlcError):
+        sim.set_chunk(-1)
+    sim.close()
