@@ -61,8 +61,8 @@ def alg_bytes(precision):
 # on; reported as null once those sources change.
 NCU_TRAFFIC = {
     # 256 x 256 x 64 capture (4,194,304 cells), see profiles/
-    "fused_lb": ((417.036e6 + 338.242e6) / 4194304, "de845dbf17f24908"),
-    "fused_be": ((153.700e6 + 62.329e6) / 4194304, "de845dbf17f24908"),
+    "fused_lb": ((422.474240e6 + 334.010880e6) / 4194304, "9d1819c0fd7ed3e3"),
+    "fused_be": ((153.790976e6 + 60.847872e6) / 4194304, "9d1819c0fd7ed3e3"),
 }
 
 KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",
