@@ -333,7 +333,7 @@ def run_ours(args, w):
     if args.chunk < 0:
         tune = sim.autotune(args.tune_steps)
     else:
-        sim.set_chunk(args.chunk)
+        sim.set_chunk(args.chunk, args.taper)
 
     # warm-up
     sim.step(args.warmup)
@@ -436,7 +436,7 @@ def run_ours(args, w):
                        "gamma": w.params["gamma"],
                        "parallelism": f"replicas{ws}",
                        "collision": "mrt" if args.mrt else "bgk",
-                       "chunk": nlc_chunk,
+                       "chunk": nlc_chunk[0], "taper": nlc_chunk[1],
                        "l2": "inputs larger than L2 (3.2 GB of state)"},
             "autotune": tune,
             "roofline": roofline, "step_roofline": step_roofline,
@@ -596,6 +596,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=-1,
                     help="z planes per block of the fused kernels: -1 autotune "
                          "(default), 0 the library default, N fixed")
+    ap.add_argument("--taper", action="store_true",
+                    help="with --chunk N: tapered chunk list")
     ap.add_argument("--tune-steps", type=int, default=8,
                     help="steps timed per candidate chunk depth by the autotuner")
     args = ap.parse_args()

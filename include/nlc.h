@@ -132,6 +132,7 @@ typedef struct {
 /* Result of nlc_autotune. */
 typedef struct {
   int32_t chunk;         /* z planes per block chosen for the fused kernels */
+  int32_t taper;         /* 1: the chosen chunk list is tapered             */
   int32_t from_cache;    /* 1: taken from the cache file, nothing was timed */
   int32_t candidates;    /* chunk depths timed                              */
   int32_t trial_steps;   /* steps timed per candidate                       */
@@ -223,28 +224,36 @@ NLC_API nlc_status nlc_set_check(nlc_ctx* ctx, int32_t every);
 NLC_API nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule);
 
 /* Depth of the z-chunks of the fused schedule on D3Q19 lattices: each
- * thread block of the two step kernels marches through `chunk` planes of one
- * 32 x 8 column of the lattice (capped at nz), so the chunk depth trades the
- * two extra planes every chunk recomputes against the number of blocks the
- * GPU spreads over its SMs.  It changes no result: every depth computes the
- * same step bit for bit.  chunk = 0 restores the library's default choice.
- * A runtime choice of this library; the paper has no counterpart.  No-op on
- * D2Q9.  Synchronises the stream.  Errors: NLC_EINVAL (chunk < 0). */
-NLC_API nlc_status nlc_set_chunk(nlc_ctx* ctx, int32_t chunk);
+ * thread block of the two step kernels marches through the planes of one
+ * chunk of one 32 x 8 column of the lattice.  The chunk depth trades the two
+ * extra planes every chunk recomputes against the number of blocks the GPU
+ * spreads over its SMs.  chunk > 0: chunks of that many planes (capped at
+ * nz); chunk = 0: the library's default depth.  taper = 1: chunks of `chunk`
+ * planes until at most 2 chunk planes of the column remain, then chunks
+ * halving down to about 8 planes; the blocks run chunk by chunk, so the last
+ * blocks are short and the last wave over the SMs idles less of the GPU.
+ * Neither changes any result: every chunk list computes the same step bit
+ * for bit.  A runtime choice of this library; the paper has no counterpart.
+ * No-op on D2Q9.  Synchronises the stream.  Errors: NLC_EINVAL (chunk < 0,
+ * taper not 0 or 1). */
+NLC_API nlc_status nlc_set_chunk(nlc_ctx* ctx, int32_t chunk, int32_t taper);
 
-/* Chunk depth in use for lattice inst (1 on D2Q9). */
-NLC_API int32_t nlc_get_chunk(const nlc_ctx* ctx, int32_t inst);
+/* Chunk depth in use for lattice inst (1 on D2Q9), or -1 for a NULL context
+ * or an instance out of range; *taper (may be NULL) gets 1 for a tapered
+ * chunk list. */
+NLC_API int32_t nlc_get_chunk(const nlc_ctx* ctx, int32_t inst, int32_t* taper);
 
 /* Autotuner of the fused schedule (a runtime choice of this library; the
  * paper has no counterpart).  Times trial_steps fused steps of the context's
- * own state for each candidate chunk depth (see nlc_set_chunk) with CUDA
- * events, restores the state bit for bit afterwards (populations and Q of
- * every lattice, buffer parity; the step counters are not touched) and keeps
- * the fastest depth.  If the environment variable NLC_TUNE_CACHE names a
- * file, results are cached there as a flat JSON object keyed by lattice,
- * precision, extents, collision, stencils and GPU (name, SM count): a key
- * found there is applied without timing (out->from_cache = 1), a new result
- * is added.  Needs two extra copies of the populations and Q of the whole
+ * own state for each candidate chunk list (uniform and tapered depths, see
+ * nlc_set_chunk) with CUDA events, restores the state bit for bit afterwards
+ * (populations and Q of every lattice, buffer parity; the step counters are
+ * not touched) and keeps the fastest.  If the environment variable
+ * NLC_TUNE_CACHE names a file, results are cached there as a flat JSON
+ * object keyed by lattice, precision, extents, collision, stencils and GPU
+ * (name, SM count), with the chunk depth as value (negative for a tapered
+ * list): a key found there is applied without timing (out->from_cache = 1),
+ * a new result is added.  Needs two extra copies of the populations and Q of the whole
  * context in device memory while it runs (freed before it returns).  No-op
  * on D2Q9 (out->chunk = 1).  out may be NULL.  Synchronises the stream.
  * Errors: NLC_EINVAL (trial_steps < 1), NLC_ENOMEM, NLC_ECUDA,

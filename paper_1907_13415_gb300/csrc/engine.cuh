@@ -171,7 +171,6 @@ class Engine final : public EngineBase {
       dev[i].q[1] = I.q[1];
       dev[i].u = I.u;
       dev[i].mrt = nullptr;
-      dev[i].tz = 1;
     }
     if ((s = alloc(&bad_, 1)) || (s = alloc(&derr_, 1)) || (s = alloc(&insts_dev_, (size_t)n)) ||
         (s = alloc(&qmaps_dev_, (size_t)2 * n)) || (s = alloc(&umaps_dev_, (size_t)n)))
@@ -180,23 +179,24 @@ class Engine final : public EngineBase {
     NLC_CK(cudaMemcpyAsync(insts_dev_, dev.data(), sizeof(InstDev<T, G>) * n, cudaMemcpyHostToDevice, st));
     NLC_CK(cudaMemcpyAsync(qmaps_dev_, qmaps.data(), sizeof(CUtensorMap) * 2 * n, cudaMemcpyHostToDevice, st));
     NLC_CK(cudaMemcpyAsync(umaps_dev_, umaps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, st));
-    return set_chunk(0);
+    return set_chunk(0, false);
   }
 
   // ---------------------------------------------------------------- chunks
   // Rebuilds the joint tile list with chunk depth tz (0: the default per
-  // lattice), updates the per-lattice depth on the device and drops captured
-  // step graphs (they hold the old list).  Synchronises the stream.
-  nlc_status set_chunk(int tz) override {
+  // lattice), tapered or not (chunk_bounds), and drops captured step graphs
+  // (they hold the old list).  Synchronises the stream.
+  nlc_status set_chunk(int tz, bool taper) override {
     cudaStream_t st = args_.stream;
     std::vector<TileRef> tiles;
+    taper_ = DIM == 3 && taper;
     for (size_t i = 0; i < inst_.size(); i++) {
       InstHost<T, G>& I = inst_[i];
       if (DIM == 2)
         I.tz = 1;
       else
         I.tz = tz > 0 ? std::min(tz, I.d.nz) : fused_tz<Lat>(I.d, (int64_t)tiles.size());
-      append_tiles<Lat>((int)i, I.d, I.tz, &tiles);
+      append_tiles<Lat>((int)i, I.d, I.tz, taper_, &tiles);
     }
     NLC_CK(cudaStreamSynchronize(st));  // no step may still read the old list
     if (tiles.size() > tiles_cap_) {
@@ -213,15 +213,13 @@ class Engine final : public EngineBase {
     ntiles_ = (int)tiles.size();
     NLC_CK(cudaMemcpyAsync(tiles_dev_, tiles.data(), sizeof(TileRef) * tiles.size(),
                            cudaMemcpyHostToDevice, st));
-    for (size_t i = 0; i < inst_.size(); i++)
-      NLC_CK(cudaMemcpyAsync(&insts_dev_[i].tz, &inst_[i].tz, sizeof(int), cudaMemcpyHostToDevice,
-                             st));
     NLC_CK(cudaStreamSynchronize(st));
     drop_graphs();
     return NLC_OK;
   }
 
   int chunk(int i) const override { return inst_[i].tz; }
+  bool tapered() const override { return taper_; }
 
   // Candidate depths are timed on the current state, which is saved first
   // and restored afterwards (the populations and Q of buffer parity cur_;
@@ -240,9 +238,12 @@ class Engine final : public EngineBase {
     }
     int maxz = 1;
     for (const auto& I : inst_) maxz = std::max(maxz, I.d.nz);
-    std::vector<int> cand = {0};  // 0: the default choice
+    // (depth, taper); depth 0: the default choice
+    std::vector<std::pair<int, bool>> cand = {{0, false}};
     for (int c : {4, 6, 8, 12, 16, 24, 32, 48, 64})
-      if (c <= maxz) cand.push_back(c);
+      if (c <= maxz) cand.push_back({c, false});
+    for (int c : {16, 24, 32, 48, 64, 96, 128})
+      if (c <= maxz) cand.push_back({c, true});
     // saved state
     const int cur0 = cur_;
     std::vector<G*> gsave(inst_.size(), nullptr);
@@ -272,14 +273,15 @@ class Engine final : public EngineBase {
     const bool timing = timer.on;
     timer.on = false;
     double best = 0.0;
-    int best_c = -1;
-    std::vector<std::vector<int>> timed;  // per-lattice depths already timed
+    int best_k = -1;
+    // per-lattice chunk boundaries already timed
+    std::vector<std::vector<std::vector<int>>> timed;
     for (size_t k = 0; k < cand.size() && s == NLC_OK; k++) {
-      if ((s = set_chunk(cand[k]))) break;
-      std::vector<int> depths;
-      for (const auto& I : inst_) depths.push_back(I.tz);
-      if (std::find(timed.begin(), timed.end(), depths) != timed.end()) continue;
-      timed.push_back(depths);
+      if ((s = set_chunk(cand[k].first, cand[k].second))) break;
+      std::vector<std::vector<int>> bounds;
+      for (const auto& I : inst_) bounds.push_back(chunk_bounds(I.d.nz, I.tz, taper_));
+      if (std::find(timed.begin(), timed.end(), bounds) != timed.end()) continue;
+      timed.push_back(bounds);
       if ((s = step_fused(st))) break;  // warm-up
       float ms = 0.f;
       if (cudaEventRecord(e0, st) != cudaSuccess) s = NLC_ECUDA;
@@ -293,10 +295,10 @@ class Engine final : public EngineBase {
       }
       const double per = ms / trial_steps;
       out->candidates++;
-      if (cand[k] == 0) out->default_ms = per;
-      if (best_c < 0 || per < best) {
+      if (k == 0) out->default_ms = per;
+      if (best_k < 0 || per < best) {
         best = per;
-        best_c = cand[k];
+        best_k = (int)k;
       }
     }
     timer.on = timing;
@@ -318,10 +320,11 @@ class Engine final : public EngineBase {
       return NLC_ECUDA;
     }
     if ((s = device_error())) return s;
-    if ((s = set_chunk(best_c))) return s;
+    if ((s = set_chunk(cand[best_k].first, cand[best_k].second))) return s;
     out->best_ms = best;
     out->chunk = 1;
     for (const auto& I : inst_) out->chunk = std::max(out->chunk, I.tz);
+    out->taper = taper_ ? 1 : 0;
     return NLC_OK;
   }
 
@@ -1068,6 +1071,7 @@ class Engine final : public EngineBase {
   CUtensorMap* umaps_dev_ = nullptr;
   TileRef* tiles_dev_ = nullptr;
   size_t tiles_cap_ = 0;
+  bool taper_ = false;  // tapered chunk lists (chunk_bounds)
   int ntiles_ = 0;
   bool maps_ok_ = false;
   unsigned long long* bad_ = nullptr;

@@ -80,9 +80,11 @@ struct EngineBase {
   virtual nlc_status set_mrt(int inst, const double* rates) = 0;
   virtual nlc_status set_stencil(bool isotropic) = 0;
   // z planes per block of the fused kernels on three-dimensional lattices:
-  // tz > 0 for every lattice (capped at its nz), 0 for the default choice
-  virtual nlc_status set_chunk(int tz) = 0;
+  // tz > 0 for every lattice (capped at its nz), 0 for the default choice;
+  // taper: the last chunks of every column shrink (chunk_bounds)
+  virtual nlc_status set_chunk(int tz, bool taper) = 0;
   virtual int chunk(int inst) const = 0;
+  virtual bool tapered() const = 0;
   // times `trial_steps` fused steps for each candidate chunk depth on the
   // current state, restores the state and keeps the fastest depth
   virtual nlc_status autotune(int trial_steps, nlc_tune* out) = 0;

@@ -210,16 +210,18 @@ nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule) {
   return NLC_OK;
 }
 
-nlc_status nlc_set_chunk(nlc_ctx* ctx, int32_t chunk) {
+nlc_status nlc_set_chunk(nlc_ctx* ctx, int32_t chunk, int32_t taper) {
   if (!ctx) return NLC_EINVAL;
   if (chunk < 0) return fail(ctx, NLC_EINVAL, "negative chunk depth");
-  nlc_status st = ctx->eng->set_chunk(chunk);
+  if (taper != 0 && taper != 1) return fail(ctx, NLC_EINVAL, "taper must be 0 or 1");
+  nlc_status st = ctx->eng->set_chunk(chunk, taper != 0);
   if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
   return NLC_OK;
 }
 
-int32_t nlc_get_chunk(const nlc_ctx* ctx, int32_t inst) {
+int32_t nlc_get_chunk(const nlc_ctx* ctx, int32_t inst, int32_t* taper) {
   if (!ctx || inst < 0 || inst >= (int32_t)ctx->grids.size()) return -1;
+  if (taper) *taper = ctx->eng->tapered() ? 1 : 0;
   return ctx->eng->chunk(inst);
 }
 
@@ -255,16 +257,21 @@ nlc_status nlc_autotune(nlc_ctx* ctx, int32_t trial_steps, nlc_tune* out) {
   const std::string key = tune_key(ctx);
   long cached = 0;
   nlc_status st;
-  if (!path.empty() && nlc::tune_cache_get(path, key, &cached) && cached >= 0) {
-    if ((st = ctx->eng->set_chunk((int)cached)) != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  // cached value: the chunk depth, negated for a tapered list
+  if (!path.empty() && nlc::tune_cache_get(path, key, &cached) && cached != 0) {
+    const bool taper = cached < 0;
+    const int depth = (int)(cached < 0 ? -cached : cached);
+    if ((st = ctx->eng->set_chunk(depth, taper)) != NLC_OK) return fail(ctx, st, ctx->eng->err);
     res.from_cache = 1;
     res.chunk = 1;
     for (size_t i = 0; i < ctx->grids.size(); i++)
       res.chunk = std::max(res.chunk, (int32_t)ctx->eng->chunk((int)i));
+    res.taper = ctx->eng->tapered() ? 1 : 0;
   } else {
     if ((st = ctx->eng->autotune(trial_steps, &res)) != NLC_OK)
       return fail(ctx, st, ctx->eng->err);
-    if (!path.empty() && !nlc::tune_cache_put(path, key, res.chunk))
+    if (!path.empty() &&
+        !nlc::tune_cache_put(path, key, res.taper ? -(long)res.chunk : (long)res.chunk))
       return fail(ctx, NLC_EINVAL, "nlc_autotune: cannot write the cache file " + path);
   }
   if (out) *out = res;

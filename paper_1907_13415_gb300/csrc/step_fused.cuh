@@ -30,6 +30,7 @@
 // of plane z.  FP32 runs the collision on packed pairs of opposite
 // populations (packed.cuh).
 #pragma once
+#include "chunks.h"
 #include "common.cuh"
 #include "lattice.cuh"
 #include "packed.cuh"
@@ -95,13 +96,12 @@ struct InstDev {
   Field<T> q[2];   // Q, ping-pong
   Field<T> u;      // u^n handed from the lb to the Beris-Edwards kernel
   const T* mrt;    // Q coefficients s_k / |v_k|^2 of the MRT collision, or nullptr
-  int tz;          // z planes per tile (1 on a single plane)
 };
 
 // One thread block's work: a 32 x 8 (x, y) tile of instance `inst`, planes
-// z0 .. z0 + tz - 1.
+// z0 .. z1 - 1 (z0 = 0, z1 = 1 on a single plane).
 struct TileRef {
-  int inst, x0, y0, z0;
+  int inst, x0, y0, z0, z1;
 };
 
 // ---------------------------------------------------------------------------
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
   const int tid = threadIdx.x;
   const int x0 = tile.x0, y0 = tile.y0;
   const int z0 = tile.z0;
-  const int z1 = DIM == 3 ? min(z0 + I.tz, d.nz) : 1;
+  const int z1 = DIM == 3 ? tile.z1 : 1;
   const int zq0 = DIM == 3 ? z0 - 2 : 0;  // first Q plane loaded
   const int zp0 = DIM == 3 ? z0 - 1 : 0;  // first Pi plane computed
   // z - zq0 and z - zp0 are never negative: unsigned arithmetic lets the
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
   const int tid = threadIdx.x;
   const int x0 = tile.x0, y0 = tile.y0;
   const int z0 = tile.z0;
-  const int z1 = DIM == 3 ? min(z0 + I.tz, d.nz) : 1;
+  const int z1 = DIM == 3 ? tile.z1 : 1;
   // Plane z of Q^n and u lives in slot (z - z0 + 2) mod NSQ (NSU), Q^P of
   // plane z in slot (z - z0 + 1) mod NSP.  The loop carries the slots of its
   // current plane and steps them with slot_add; every plane's copy is waited
@@ -835,14 +835,17 @@ __host__ inline int fused_tz(const Dims& d, int64_t other_tiles) {
   return tz < d.nz ? tz : d.nz;
 }
 
-// tile list of one instance, x fastest so neighbouring blocks share halos
+// tile list of one instance: chunk by chunk along z, x fastest within a
+// chunk, so neighbouring blocks run together and share halos in L2
 template <class Lat>
-__host__ inline void append_tiles(int inst, const Dims& d, int tz,
+__host__ inline void append_tiles(int inst, const Dims& d, int tz, bool taper,
                                   std::vector<TileRef>* out) {
-  const int nzc = Lat::DIM == 3 ? (d.nz + tz - 1) / tz : 1;
-  for (int zc = 0; zc < nzc; zc++)
+  const std::vector<int> b =
+      Lat::DIM == 3 ? chunk_bounds(d.nz, tz, taper) : std::vector<int>{0, 1};
+  for (size_t zc = 0; zc + 1 < b.size(); zc++)
     for (int y0 = 0; y0 < d.ny; y0 += FTY)
-      for (int x0 = 0; x0 < d.nx; x0 += FTX) out->push_back({inst, x0, y0, zc * tz});
+      for (int x0 = 0; x0 < d.nx; x0 += FTX)
+        out->push_back({inst, x0, y0, b[zc], b[zc + 1]});
 }
 
 template <class K>

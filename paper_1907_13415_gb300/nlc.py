@@ -60,7 +60,8 @@ class nlc_loss(ctypes.Structure):
 
 
 class nlc_tune(ctypes.Structure):
-    _fields_ = [("chunk", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+    _fields_ = [("chunk", ctypes.c_int32), ("taper", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("trial_steps", ctypes.c_int32),
                 ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
 
@@ -107,8 +108,8 @@ def load(build_if_missing=True):
         "nlc_set_mrt": ([P, I32, P, I32], I32),
         "nlc_set_stencil": ([P, I32], I32),
         "nlc_set_schedule": ([P, I32], I32),
-        "nlc_set_chunk": ([P, I32], I32),
-        "nlc_get_chunk": ([P, I32], I32),
+        "nlc_set_chunk": ([P, I32, I32], I32),
+        "nlc_get_chunk": ([P, I32, P], I32),
         "nlc_autotune": ([P, I32, ctypes.POINTER(nlc_tune)], I32),
         "nlc_set_fields": ([P, I32, P, P, P], I32),
         "nlc_get_fields": ([P, I32, P, P, P], I32),
@@ -230,12 +231,15 @@ def nlc_set_schedule(ctx, schedule):
     _check(ctx, load().nlc_set_schedule(ctx, schedule))
 
 
-def nlc_set_chunk(ctx, chunk):
-    _check(ctx, load().nlc_set_chunk(ctx, int(chunk)))
+def nlc_set_chunk(ctx, chunk, taper=False):
+    _check(ctx, load().nlc_set_chunk(ctx, int(chunk), 1 if taper else 0))
 
 
 def nlc_get_chunk(ctx, inst=0):
-    return int(load().nlc_get_chunk(ctx, int(inst)))
+    """(chunk depth, tapered) of lattice inst."""
+    t = ctypes.c_int32(0)
+    c = int(load().nlc_get_chunk(ctx, int(inst), ctypes.byref(t)))
+    return c, bool(t.value)
 
 
 def nlc_autotune(ctx, trial_steps):
@@ -399,10 +403,11 @@ class Batch:
     def step(self, n=1):
         nlc_step(self.ctx, n)
 
-    def set_chunk(self, chunk):
-        nlc_set_chunk(self.ctx, chunk)
+    def set_chunk(self, chunk, taper=False):
+        nlc_set_chunk(self.ctx, chunk, taper)
 
     def chunk(self, i=0):
+        """(chunk depth, tapered) of lattice i."""
         return nlc_get_chunk(self.ctx, i)
 
     def autotune(self, trial_steps=10):
@@ -475,10 +480,11 @@ class Simulation:
     def step(self, n=1):
         nlc_step(self.ctx, n)
 
-    def set_chunk(self, chunk):
-        nlc_set_chunk(self.ctx, chunk)
+    def set_chunk(self, chunk, taper=False):
+        nlc_set_chunk(self.ctx, chunk, taper)
 
     def chunk(self):
+        """(chunk depth, tapered)."""
         return nlc_get_chunk(self.ctx, 0)
 
     def autotune(self, trial_steps=10):

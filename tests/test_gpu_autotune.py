@@ -42,11 +42,16 @@ def test_every_chunk_depth_gives_the_same_step(precision):
     prec = getattr(nlc, precision)
     w = droplet()
     ref = None
-    for chunk in (0, 1, 2, 3, 4, 7, 23, 64):
+    for chunk, taper in ((0, False), (1, False), (2, False), (3, False), (4, False),
+                         (7, False), (23, False), (64, False), (4, True), (6, True),
+                         (16, True)):
         sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=prec,
                              stream=stream())
-        sim.set_chunk(chunk)
-        assert sim.chunk() == (min(chunk, w.shape[0]) if chunk else sim.chunk())
+        sim.set_chunk(chunk, taper)
+        depth, tapered = sim.chunk()
+        assert tapered == taper
+        if chunk:
+            assert depth == min(chunk, w.shape[0])
         sim.set_fields(w.initial_q5())
         sim.step(7)
         got = state(sim)
@@ -63,14 +68,14 @@ def test_chunk_change_between_steps_and_graphs():
     from paper_1907_13415_gb300 import nlc
     w = droplet(seed=32)
     sims = []
-    for chunks in ((0, 0), (5, 2)):
+    for chunks in (((0, False), (0, False)), ((5, False), (4, True))):
         sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
                              stream=stream())
         sim.set_graph(3)
         sim.set_fields(w.initial_q5())
-        sim.set_chunk(chunks[0])
+        sim.set_chunk(*chunks[0])
         sim.step(7)
-        sim.set_chunk(chunks[1])
+        sim.set_chunk(*chunks[1])
         sim.step(6)
         sims.append(state(sim))
         sim.close()
@@ -93,7 +98,8 @@ def test_autotune_keeps_the_state_and_the_trajectory(tmp_path, monkeypatch):
     r = tuned.autotune(trial_steps=3)
     assert r["from_cache"] == 0 and r["candidates"] >= 2 and r["trial_steps"] == 3
     assert r["best_ms"] > 0 and r["default_ms"] >= r["best_ms"]
-    assert tuned.chunk() == r["chunk"] and 1 <= r["chunk"] <= w.shape[0]
+    assert tuned.chunk() == (r["chunk"], bool(r["taper"]))
+    assert 1 <= r["chunk"] <= w.shape[0]
     after = state(tuned)
     for a, b in zip(before, after):
         assert np.array_equal(a, b)
@@ -120,12 +126,14 @@ def test_autotune_cache_is_written_then_read(tmp_path, monkeypatch):
     cache = json.loads(path.read_text())
     assert len(cache) == 1
     (key, val), = cache.items()
-    assert key.startswith("D3Q19/fp32/n1/32x16x16/std/") and val == r1["chunk"]
+    assert key.startswith("D3Q19/fp32/n1/32x16x16/std/")
+    assert val == (-r1["chunk"] if r1["taper"] else r1["chunk"])
     second = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
                             stream=stream())
     r2 = second.autotune(trial_steps=2)
     assert r2["from_cache"] == 1 and r2["chunk"] == r1["chunk"]
-    assert second.chunk() == r1["chunk"]
+    assert r2["taper"] == r1["taper"]
+    assert second.chunk() == (r1["chunk"], bool(r1["taper"]))
     # another stencil is another key
     second.set_stencil(nlc.NLC_STENCIL_ISOTROPIC)
     r3 = second.autotune(trial_steps=2)
@@ -141,9 +149,11 @@ def test_autotune_single_plane_lattices_have_no_chunks(monkeypatch):
     sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
                          stream=stream())
     r = sim.autotune(trial_steps=2)
-    assert r["chunk"] == 1 and r["candidates"] == 0 and sim.chunk() == 1
+    assert r["chunk"] == 1 and r["candidates"] == 0 and sim.chunk() == (1, False)
     with pytest.raises(nlc.NlcError):
         sim.autotune(trial_steps=0)
     with pytest.raises(nlc.NlcError):
         sim.set_chunk(-1)
+    with pytest.raises(nlc.NlcError):
+        nlc._check(sim.ctx, nlc.load().nlc_set_chunk(sim.ctx, 8, 2))
     sim.close()

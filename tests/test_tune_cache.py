@@ -104,6 +104,6 @@ def test_unwritable_cache_reports_failure(tool, tmp_path):
 def test_chunk_and_autotune_reject_null_context():
     from paper_1907_13415_gb300 import nlc
     lib = nlc.load()
-    assert lib.nlc_set_chunk(None, 8) == -1
-    assert lib.nlc_get_chunk(None, 0) == -1
+    assert lib.nlc_set_chunk(None, 8, 0) == -1
+    assert lib.nlc_get_chunk(None, 0, None) == -1
     assert lib.nlc_autotune(None, 5, None) == -1
