@@ -61,8 +61,8 @@ def alg_bytes(precision):
 # on; reported as null once those sources change.
 NCU_TRAFFIC = {
     # 256 x 256 x 64 capture (4,194,304 cells), see profiles/
-    "fused_lb": ((422.474240e6 + 334.010880e6) / 4194304, "9d1819c0fd7ed3e3"),
-    "fused_be": ((153.790976e6 + 60.847872e6) / 4194304, "9d1819c0fd7ed3e3"),
+    "fused_lb": ((423.054080e6 + 334.713856e6) / 4194304, "2cfe55b1b4ccfe34"),
+    "fused_be": ((153.838336e6 + 61.117696e6) / 4194304, "2cfe55b1b4ccfe34"),
 }
 
 KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",
