@@ -30,6 +30,13 @@ __global__ void __launch_bounds__(256) k_set_fields(
   if (rho_in) nbad += !isfinite(rho_in[idx]) || !(rho_in[idx] > 0.0);
   if (u_in)
     for (int a = 0; a < 3; a++) nbad += !isfinite(u_in[a * d.n + idx]);
+  if (!rho_in && !u_in) {
+    // rho = rho0 and u = 0 everywhere: every deviation is exactly zero
+#pragma unroll
+    for (int i = 0; i < Lat::Q; i++) g[(int64_t)i * d.n + idx] = G(0);
+    if (nbad) atomicAdd(bad, (unsigned long long)nbad);
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < Lat::Q; i++) {
     const int xs = wrap_add(x, Lat::c(i, 0), d.nx);
@@ -145,59 +152,67 @@ __global__ void __launch_bounds__(256) k_obs_partial(
     Field<T> Q, const G* __restrict__ gpost,
     const double* __restrict__ rho, const double* __restrict__ u, Dims d,
     Par<T> p, double s_ref, double* __restrict__ partial) {
+  // Per-cell terms in the arithmetic type T of the state (float for the
+  // FP32 engine, whose state carries no more digits), sums and maxima in
+  // float64.
   __shared__ double sh[32];
   double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0, 0};
   double umax = 0.0;
-  const double A0 = (double)p.A0, K = (double)p.K, gam = (double)p.gamma;
+  const T A0 = p.A0, K = p.K, gam = p.gamma;
+  const T c2 = A0 / T(2) * (T(1) - gam / T(3)), c3 = A0 * gam / T(3), c4 = A0 * gam / T(4);
+  const T kh = K / T(2), inv_sref = T(1.0 / s_ref);
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < d.n;
        idx += (int64_t)gridDim.x * blockDim.x) {
     int x, y, z;
     decode(d, idx, x, y, z);
     const double r = rho[idx];
-    double uu = 0.0;
+    T uu = T(0);
     acc[0] += r;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
       const double ua = u[a * d.n + idx];
       acc[1 + a] += r * ua;
-      uu += ua * ua;
+      uu += T(ua) * T(ua);
     }
-    umax = fmax(umax, sqrt(uu));
-    acc[7] += uu;
-    double q[5];
+    umax = fmax(umax, (double)sqrt(uu));
+    acc[7] += (double)uu;
+    T q[5];
     int nbad = 0;
 #pragma unroll
     for (int k = 0; k < 5; k++) {
-      q[k] = (double)Q.at(k, x, y, z);
+      q[k] = Q.at(k, x, y, z);
       nbad += !isfinite(q[k]);
     }
 #pragma unroll
-    for (int i = 0; i < Lat::Q; i++) nbad += !isfinite((double)gpost[(int64_t)i * d.n + idx]);
-    const double qzz = -q[0] - q[3];
-    const double tr2 = q[0] * q[0] + q[3] * q[3] + qzz * qzz +
-                       2.0 * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
-    // Tr Q^3 = det-free form via Q_ab Q_bc Q_ca
-    const double Qm[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], qzz}};
-    double tr3 = 0.0;
+    for (int i = 0; i < Lat::Q; i++) nbad += !isfinite((T)gpost[(int64_t)i * d.n + idx]);
+    const T qzz = -q[0] - q[3];
+    const T tr2 = q[0] * q[0] + q[3] * q[3] + qzz * qzz +
+                  T(2) * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
+    // Tr Q^3 = Q_ab Q_bc Q_ca
+    const T Qm[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], qzz}};
+    T tr3 = T(0);
+#pragma unroll
     for (int a = 0; a < 3; a++)
+#pragma unroll
       for (int b = 0; b < 3; b++)
+#pragma unroll
         for (int c = 0; c < 3; c++) tr3 += Qm[a][b] * Qm[b][c] * Qm[c][a];
-    double e = A0 / 2.0 * (1.0 - gam / 3.0) * tr2 - A0 * gam / 3.0 * tr3 +
-               A0 * gam / 4.0 * tr2 * tr2;
+    T e = c2 * tr2 - c3 * tr3 + c4 * tr2 * tr2;
     // forward-difference gradient energy K/2 sum_g |Q(x+e_g) - Q(x)|^2
     const int nb[3][3] = {{wrap_inc(x, d.nx), y, z},
                           {x, wrap_inc(y, d.ny), z},
                           {x, y, wrap_inc(z, d.nz)}};
+#pragma unroll
     for (int gdir = 0; gdir < 3; gdir++) {
-      double dv[5];
-      for (int k = 0; k < 5; k++)
-        dv[k] = (double)Q.at(k, nb[gdir][0], nb[gdir][1], nb[gdir][2]) - q[k];
-      const double dzz = -dv[0] - dv[3];
-      e += K / 2.0 * (dv[0] * dv[0] + dv[3] * dv[3] + dzz * dzz +
-                      2.0 * (dv[1] * dv[1] + dv[2] * dv[2] + dv[4] * dv[4]));
+      T dv[5];
+#pragma unroll
+      for (int k = 0; k < 5; k++) dv[k] = Q.at(k, nb[gdir][0], nb[gdir][1], nb[gdir][2]) - q[k];
+      const T dzz = -dv[0] - dv[3];
+      e += kh * (dv[0] * dv[0] + dv[3] * dv[3] + dzz * dzz +
+                 T(2) * (dv[1] * dv[1] + dv[2] * dv[2] + dv[4] * dv[4]));
     }
-    acc[4] += sqrt(1.5 * tr2) / s_ref;
-    acc[5] += e;
+    acc[4] += (double)(sqrt(T(1.5) * tr2) * inv_sref);
+    acc[5] += (double)e;
     acc[6] += (double)nbad;
   }
   double tot[OBS_SLOTS];
@@ -238,15 +253,16 @@ __global__ void __launch_bounds__(128) k_profile_partial(
   const int64_t rows = (int64_t)d.ny * d.nz;
   const int64_t r0 = (int64_t)chunk * rows_per_chunk;
   const int64_t r1 = r0 + rows_per_chunk < rows ? r0 + rows_per_chunk : rows;
+  // S per cell in the state's type T, summed in float64
   double s = 0.0;
   for (int64_t r = r0; r < r1; r++) {
-    const int yy = (int)(r % d.ny), zz = (int)(r / d.ny);
-    double q[5];
-    for (int k = 0; k < 5; k++) q[k] = (double)Q.at(k, x, yy, zz);
-    const double qzz = -q[0] - q[3];
-    const double tr2 = q[0] * q[0] + q[3] * q[3] + qzz * qzz +
-                       2.0 * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
-    s += sqrt(1.5 * tr2);
+    const int yy = (int)((unsigned)r % (unsigned)d.ny), zz = (int)((unsigned)r / (unsigned)d.ny);
+    T q[5];
+    for (int k = 0; k < 5; k++) q[k] = Q.at(k, x, yy, zz);
+    const T qzz = -q[0] - q[3];
+    const T tr2 = q[0] * q[0] + q[3] * q[3] + qzz * qzz +
+                  T(2) * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
+    s += (double)sqrt(T(1.5) * tr2);
   }
   partial[(int64_t)chunk * d.nx + x] = s;
 }

@@ -106,13 +106,16 @@ __device__ __forceinline__ void u_stencil_iso(const Field<T>& U, int x, int y, i
   }
 }
 
+// A lattice holds fewer than 2^32 cells (nlc_create refuses more), so the
+// cell index splits in unsigned 32-bit arithmetic.
 __device__ __forceinline__ bool decode(const Dims& d, int64_t idx, int& x,
                                        int& y, int& z) {
   if (idx >= d.n) return false;
-  x = (int)(idx % d.nx);
-  const int64_t r = idx / d.nx;
-  y = (int)(r % d.ny);
-  z = (int)(r / d.ny);
+  const unsigned i = (unsigned)idx, nx = (unsigned)d.nx, ny = (unsigned)d.ny;
+  const unsigned r = i / nx;
+  x = (int)(i - r * nx);
+  y = (int)(r % ny);
+  z = (int)(r / ny);
   return true;
 }
 
