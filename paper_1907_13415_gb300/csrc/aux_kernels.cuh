@@ -147,79 +147,140 @@ __global__ void __launch_bounds__(256) k_field_raw_in(const T* __restrict__ in, 
 // non-finite count, sum |u|^2, max |u| (last).
 constexpr int OBS_SLOTS = 9;
 
-template <class Lat, class T, class G>
-__global__ void __launch_bounds__(256) k_obs_partial(
-    Field<T> Q, const G* __restrict__ gpost,
-    const double* __restrict__ rho, const double* __restrict__ u, Dims d,
-    Par<T> p, double s_ref, double* __restrict__ partial) {
-  // Per-cell terms in the arithmetic type T of the state (float for the
-  // FP32 engine, whose state carries no more digits), sums and maxima in
-  // float64.
-  __shared__ double sh[32];
-  double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0, 0};
-  double umax = 0.0;
-  const T A0 = p.A0, K = p.K, gam = p.gamma;
-  const T c2 = A0 / T(2) * (T(1) - gam / T(3)), c3 = A0 * gam / T(3), c4 = A0 * gam / T(4);
-  const T kh = K / T(2), inv_sref = T(1.0 / s_ref);
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < d.n;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    int x, y, z;
-    decode(d, idx, x, y, z);
-    const double r = rho[idx];
-    T uu = T(0);
-    acc[0] += r;
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      const double ua = u[a * d.n + idx];
-      acc[1 + a] += r * ua;
-      uu += T(ua) * T(ua);
-    }
-    umax = fmax(umax, (double)sqrt(uu));
-    acc[7] += (double)uu;
-    T q[5];
-    int nbad = 0;
-#pragma unroll
-    for (int k = 0; k < 5; k++) {
-      q[k] = Q.at(k, x, y, z);
-      nbad += !isfinite(q[k]);
-    }
-#pragma unroll
-    for (int i = 0; i < Lat::Q; i++) nbad += !isfinite((T)gpost[(int64_t)i * d.n + idx]);
-    const T qzz = -q[0] - q[3];
-    const T tr2 = q[0] * q[0] + q[3] * q[3] + qzz * qzz +
-                  T(2) * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
-    // Tr Q^3 = Q_ab Q_bc Q_ca
-    const T Qm[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], qzz}};
-    T tr3 = T(0);
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int b = 0; b < 3; b++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) tr3 += Qm[a][b] * Qm[b][c] * Qm[c][a];
-    T e = c2 * tr2 - c3 * tr3 + c4 * tr2 * tr2;
-    // forward-difference gradient energy K/2 sum_g |Q(x+e_g) - Q(x)|^2
-    const int nb[3][3] = {{wrap_inc(x, d.nx), y, z},
-                          {x, wrap_inc(y, d.ny), z},
-                          {x, y, wrap_inc(z, d.nz)}};
-#pragma unroll
-    for (int gdir = 0; gdir < 3; gdir++) {
-      T dv[5];
-#pragma unroll
-      for (int k = 0; k < 5; k++) dv[k] = Q.at(k, nb[gdir][0], nb[gdir][1], nb[gdir][2]) - q[k];
-      const T dzz = -dv[0] - dv[3];
-      e += kh * (dv[0] * dv[0] + dv[3] * dv[3] + dzz * dzz +
-                 T(2) * (dv[1] * dv[1] + dv[2] * dv[2] + dv[4] * dv[4]));
-    }
-    acc[4] += (double)(sqrt(T(1.5) * tr2) * inv_sref);
-    acc[5] += (double)e;
-    acc[6] += (double)nbad;
+// One cell's contributions to the observables: rho and u (float64, of
+// Eq. 6), the cell's Q, and nbad non-finite stored values found by the
+// caller.  Per-cell terms in the arithmetic type T of the state (float for
+// the FP32 engine, whose state carries no more digits); acc (float64) and
+// umax collect them.
+template <class T>
+struct ObsConst {
+  T c2, c3, c4, kh, inv_sref;
+  __device__ ObsConst(const Par<T>& p, double s_ref) {
+    c2 = p.A0 / T(2) * (T(1) - p.gamma / T(3));
+    c3 = p.A0 * p.gamma / T(3);
+    c4 = p.A0 * p.gamma / T(4);
+    kh = p.K / T(2);
+    inv_sref = T(1.0 / s_ref);
   }
+};
+
+template <class T>
+__device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x, int y, int z,
+                                         double r, const double u[3], int nbad,
+                                         const ObsConst<T>& c, double acc[OBS_SLOTS - 1],
+                                         double& umax) {
+  T uu = T(0);
+  acc[0] += r;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    acc[1 + a] += r * u[a];
+    uu += T(u[a]) * T(u[a]);
+  }
+  umax = fmax(umax, (double)sqrt(uu));
+  acc[7] += (double)uu;
+  T q[5];
+#pragma unroll
+  for (int k = 0; k < 5; k++) {
+    q[k] = Q.at(k, x, y, z);
+    nbad += !isfinite(q[k]);
+  }
+  const T qzz = -q[0] - q[3];
+  const T tr2 = q[0] * q[0] + q[3] * q[3] + qzz * qzz +
+                T(2) * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
+  // Tr Q^3 = Q_ab Q_bc Q_ca
+  const T Qm[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], qzz}};
+  T tr3 = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+#pragma unroll
+      for (int e = 0; e < 3; e++) tr3 += Qm[a][b] * Qm[b][e] * Qm[e][a];
+  T en = c.c2 * tr2 - c.c3 * tr3 + c.c4 * tr2 * tr2;
+  // forward-difference gradient energy K/2 sum_g |Q(x+e_g) - Q(x)|^2
+  const int nb[3][3] = {{wrap_inc(x, d.nx), y, z},
+                        {x, wrap_inc(y, d.ny), z},
+                        {x, y, wrap_inc(z, d.nz)}};
+#pragma unroll
+  for (int gdir = 0; gdir < 3; gdir++) {
+    T dv[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) dv[k] = Q.at(k, nb[gdir][0], nb[gdir][1], nb[gdir][2]) - q[k];
+    const T dzz = -dv[0] - dv[3];
+    en += c.kh * (dv[0] * dv[0] + dv[3] * dv[3] + dzz * dzz +
+                  T(2) * (dv[1] * dv[1] + dv[2] * dv[2] + dv[4] * dv[4]));
+  }
+  acc[4] += (double)(sqrt(T(1.5) * tr2) * c.inv_sref);
+  acc[5] += (double)en;
+  acc[6] += (double)nbad;
+}
+
+// per-block float64 partials of the accumulators into partial[block]
+__device__ __forceinline__ void obs_block_out(const double acc[OBS_SLOTS - 1], double umax,
+                                              double* sh, double* __restrict__ partial) {
   double tot[OBS_SLOTS];
   for (int k = 0; k < OBS_SLOTS - 1; k++) tot[k] = block_sum(acc[k], sh);
   tot[OBS_SLOTS - 1] = block_max(umax, sh);
   if (threadIdx.x == 0)
     for (int k = 0; k < OBS_SLOTS; k++) partial[blockIdx.x * OBS_SLOTS + k] = tot[k];
+}
+
+// Observables, pass 1, from rho and u given as float64 arrays: per-block
+// float64 partial sums over cells.  partial[block][OBS_SLOTS]: mass,
+// mom x/y/z, sum S/s_ref, free energy, non-finite count, sum |u|^2,
+// max |u| (last).
+template <class Lat, class T, class G>
+__global__ void __launch_bounds__(256) k_obs_partial(
+    Field<T> Q, const G* __restrict__ gpost,
+    const double* __restrict__ rho, const double* __restrict__ u, Dims d,
+    Par<T> p, double s_ref, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double umax = 0.0;
+  const ObsConst<T> c(p, s_ref);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < d.n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    decode(d, idx, x, y, z);
+    int nbad = 0;
+#pragma unroll
+    for (int i = 0; i < Lat::Q; i++) nbad += !isfinite((T)gpost[(int64_t)i * d.n + idx]);
+    const double uc[3] = {u[idx], u[d.n + idx], u[2 * d.n + idx]};
+    obs_cell<T>(Q, d, x, y, z, rho[idx], uc, nbad, c, acc, umax);
+  }
+  obs_block_out(acc, umax, sh, partial);
+}
+
+// The same from the state itself: rho and u of Eq. 6 are formed per cell
+// from the pulled populations and the force of the stress Pi (k_stress);
+// every stored population is pulled by exactly one cell, so the non-finite
+// count covers each once.
+template <class Lat, class T, class G>
+__global__ void __launch_bounds__(256) k_obs_state(
+    Field<T> Q, const G* __restrict__ gin, const T* __restrict__ Pi, Dims d, Par<T> p,
+    double s_ref, bool iso, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double umax = 0.0;
+  const ObsConst<T> c(p, s_ref);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < d.n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    decode(d, idx, x, y, z);
+    T F[3], g[Lat::Q], rho, u[3];
+    if (iso)
+      force_at_iso<Lat, T>(Pi, d, x, y, z, F);
+    else
+      force_at<T, Lat::DIM>(Pi, d, x, y, z, F);
+    pull<Lat, T>(gin, d, x, y, z, g);
+    int nbad = 0;
+#pragma unroll
+    for (int i = 0; i < Lat::Q; i++) nbad += !isfinite(g[i]);
+    moments<Lat, T>(g, F, p, rho, u);
+    const double uc[3] = {(double)u[0], (double)u[1], (double)u[2]};
+    obs_cell<T>(Q, d, x, y, z, (double)rho, uc, nbad, c, acc, umax);
+  }
+  obs_block_out(acc, umax, sh, partial);
 }
 
 namespace {  // non-template kernels: one private copy per translation unit

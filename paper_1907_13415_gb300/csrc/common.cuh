@@ -113,6 +113,17 @@ __device__ __forceinline__ void store_with_images(const Field<T>& F, const Dims&
   }
 }
 
+// Stores NC component values of cell (x, y, z) of a padded field whose
+// periodic images the caller knows to lie outside the ghost ring (a cell at
+// least GHOST away from every face).
+template <class T, int NC>
+__device__ __forceinline__ void store_interior(const Field<T>& F, int x, int y, int z,
+                                               const T v[NC]) {
+  T* p = F.base + F.off(0, x, y, z);
+#pragma unroll
+  for (int k = 0; k < NC; k++) p[k * F.L.comp] = v[k];
+}
+
 // fixed-order FP64 block sum (blockDim.x a multiple of 32, <= 1024);
 // every thread returns the total
 __device__ __forceinline__ double block_sum(double v, double* sh) {

@@ -636,11 +636,13 @@ class Engine final : public EngineBase {
     const int64_t n = I.d.n;
     const Dims& d = I.d;
     cudaStream_t st = args_.stream;
-    if ((s = moments_to_stage(I))) return s;
     const double s_ref = 1.0 / 3.0;
-    k_obs_partial<Lat, T><<<I.obs_blocks, 256, 0, st>>>(
-        I.q[cur_], I.g[cur_], I.stage + 5 * n, I.stage + 6 * n, d, I.p, s_ref, I.partial);
-    NLC_CK_LAUNCH("k_obs_partial");
+    // stress of the current Q, then rho, u and the observables in one pass
+    k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[cur_], I.pi, I.d, I.p, iso_);
+    NLC_CK_LAUNCH("k_stress");
+    k_obs_state<Lat, T><<<I.obs_blocks, 256, 0, st>>>(I.q[cur_], I.g[cur_], I.pi, d, I.p, s_ref,
+                                                      iso_, I.partial);
+    NLC_CK_LAUNCH("k_obs_state");
     k_obs_final<<<1, 256, 0, st>>>(I.partial, I.obs_blocks, I.partial + I.obs_blocks * OBS_SLOTS);
     NLC_CK_LAUNCH("k_obs_final");
     const int64_t rows = (int64_t)d.ny * d.nz;

@@ -79,7 +79,11 @@ __host__ __device__ __forceinline__ void moments_pairs(float g0, const float2* g
   for (int p = 1; p < NP; p++) s = padd(s, gp[p]);
   drho = g0 + (s.x + s.y);
   rho = rho0 + drho;
+#ifdef __CUDA_ARCH__
+  const float inv = __fdividef(1.0f, rho);  // hardware reciprocal, 2 ulp, no slow path
+#else
   const float inv = 1.0f / rho;
+#endif
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     if (a >= Lat::DIM) {

@@ -352,6 +352,11 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
   }
   const int nxy = d.nx * d.ny;
   const int ic = (ty + 1) * RX1 + (tx + 1);
+  // every cell of the tile lies GHOST or more away from the x and y faces:
+  // its stores of u have no periodic images there (the same for the whole
+  // block)
+  const bool tile_inner = x0 >= GHOST && x0 + FTX <= d.nx - GHOST && y0 >= GHOST &&
+                          y0 + FTY <= d.ny - GHOST;
 
   // The populations of the next plane are pulled into registers (gn) as
   // soon as the current plane is done, so their loads are in flight while
@@ -461,7 +466,10 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
 #pragma unroll
       for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = G(g[i]);
     }
-    store_with_images<T, DIM, DIM>(U, d, x, y, z, u);
+    if (tile_inner && (DIM == 2 || (z >= GHOST && z < d.nz - GHOST)))
+      store_interior<T, DIM>(U, x, y, z, u);
+    else
+      store_with_images<T, DIM, DIM>(U, d, x, y, z, u);
     if (z + 1 < z1) pull_next(z + 1);
   };
 
