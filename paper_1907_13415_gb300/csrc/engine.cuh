@@ -434,6 +434,18 @@ class Engine final : public EngineBase {
   }
 
   // ---------------------------------------------------------------- I/O
+  // Device-side address of a page-locked (pinned) host array, which the
+  // kernels can read in place over the host link, or nullptr for any other
+  // memory (pageable host memory goes through a staging copy instead).
+  static const double* mapped_host(const double* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? static_cast<const double*>(a.devicePointer) : nullptr;
+  }
+
   nlc_status set_fields(int i, const double* Q5, const double* rho,
                         const double* u) override {
     InstHost<T, G>& I = inst_[i];
@@ -441,15 +453,24 @@ class Engine final : public EngineBase {
     if ((s = ensure_staging(I))) return s;
     const int64_t n = I.d.n;
     cudaStream_t st = args_.stream;
-    NLC_CK(cudaMemcpyAsync(I.stage, Q5, sizeof(double) * 5 * n, cudaMemcpyHostToDevice, st));
-    if (rho)
-      NLC_CK(cudaMemcpyAsync(I.stage + 5 * n, rho, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-    if (u)
-      NLC_CK(cudaMemcpyAsync(I.stage + 6 * n, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    // pinned inputs are read in place by the kernel (the transfer then
+    // overlaps the conversion); others are copied to the staging buffer
+    auto source = [&](const double* h, double* stage, int64_t count,
+                      const double** out) -> nlc_status {
+      *out = nullptr;
+      if (!h) return NLC_OK;
+      if ((*out = mapped_host(h))) return NLC_OK;
+      NLC_CK(cudaMemcpyAsync(stage, h, sizeof(double) * count, cudaMemcpyHostToDevice, st));
+      *out = stage;
+      return NLC_OK;
+    };
+    const double *qs, *rs, *us;
+    if ((s = source(Q5, I.stage, 5 * n, &qs)) || (s = source(rho, I.stage + 5 * n, n, &rs)) ||
+        (s = source(u, I.stage + 6 * n, 3 * n, &us)))
+      return s;
     NLC_CK(cudaMemsetAsync(bad_, 0, sizeof(unsigned long long), st));
-    k_set_fields<Lat, T><<<grid1(n), 256, 0, st>>>(
-        I.stage, rho ? I.stage + 5 * n : nullptr, u ? I.stage + 6 * n : nullptr,
-        I.q[cur_], I.g[cur_], I.d, args_.params[i].rho0, bad_);
+    k_set_fields<Lat, T><<<grid1(n), 256, 0, st>>>(qs, rs, us, I.q[cur_], I.g[cur_], I.d,
+                                                   args_.params[i].rho0, bad_);
     NLC_CK_LAUNCH("k_set_fields");
     unsigned long long nbad = 0;
     NLC_CK(cudaMemcpyAsync(&nbad, bad_, sizeof(nbad), cudaMemcpyDeviceToHost, st));

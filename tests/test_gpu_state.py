@@ -94,3 +94,43 @@ def test_periodic_check_reports_a_blow_up():
     s.step(40)
     assert s.observables()["nonfinite"] > 0
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_pinned_host_inputs_are_read_in_place(precision):
+    """nlc_set_fields reads page-locked host arrays directly from the kernel
+    instead of staging them; the state must equal the one set from ordinary
+    (pageable) arrays, also with rho and u given and a non-finite value
+    still refused."""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    w = wl.sphere_256().with_(shape=(9, 12, 34), size=4.0, noise=1e-3, seed=51)
+    rng = np.random.default_rng(52)
+    Q = w.initial_q5()
+    rho = 1.0 + 0.01 * rng.standard_normal(w.shape)
+    u = 1e-3 * rng.standard_normal((3,) + w.shape)
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    pQ, prho, pu = pinned(Q), pinned(rho), pinned(u)
+    a, b = make(w, precision), make(w, precision)
+    a.set_fields(Q, rho, u)
+    b.set_fields(pQ.numpy(), prho.numpy(), pu.numpy())
+    for x, y in zip(a.get_fields(), b.get_fields()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    a.step(3)
+    b.step(3)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    b.set_fields(pQ.numpy())            # Q only: rho0 and rest
+    a.set_fields(Q)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    pQ.numpy()[2, 1, 1, 1] = np.nan
+    with pytest.raises(nlc.NlcError) as ei:
+        b.set_fields(pQ.numpy())
+    assert ei.value.status == -4
+    a.close()
+    b.close()
