@@ -264,6 +264,10 @@ NLC_API nlc_status nlc_autotune(nlc_ctx* ctx, int32_t trial_steps, nlc_tune* out
  * layouts above).  The populations are set to the equilibrium
  * f_i^eq(rho, u) of Sec. 1.2.1.  rho may be NULL (rho0 everywhere) and u may
  * be NULL (at rest).  The lattice's step counter restarts at 0.
+ * Page-locked (pinned) host arrays are read in place by the device, which
+ * overlaps the transfer with the conversion; other host arrays are first
+ * copied to a device staging buffer.  Either way the arrays are no longer
+ * needed once the call returns.
  * Synchronises the stream.  Errors: NLC_EINVAL (null Q5, inst out of range),
  * NLC_EUNSTABLE (a non-finite input value; the state is then undefined),
  * NLC_ECUDA. */

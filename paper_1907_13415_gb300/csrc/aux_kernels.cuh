@@ -285,20 +285,20 @@ __global__ void __launch_bounds__(256) k_obs_state(
 
 namespace {  // non-template kernels: one private copy per translation unit
 
-// pass 2: one block sums the partials in a fixed order
+// pass 2: block k (launch OBS_SLOTS blocks) sums slot k of the partials in a
+// fixed order
 __global__ void __launch_bounds__(256) k_obs_final(const double* __restrict__ partial,
                                                    int nblocks,
                                                    double* __restrict__ out) {
   __shared__ double sh[32];
-  for (int k = 0; k < OBS_SLOTS; k++) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-      const double pv = partial[b * OBS_SLOTS + k];
-      v = (k == OBS_SLOTS - 1) ? fmax(v, pv) : v + pv;
-    }
-    const double t = (k == OBS_SLOTS - 1) ? block_max(v, sh) : block_sum(v, sh);
-    if (threadIdx.x == 0) out[k] = t;
+  const int k = blockIdx.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const double pv = partial[b * OBS_SLOTS + k];
+    v = (k == OBS_SLOTS - 1) ? fmax(v, pv) : v + pv;
   }
+  const double t = (k == OBS_SLOTS - 1) ? block_max(v, sh) : block_sum(v, sh);
+  if (threadIdx.x == 0) out[k] = t;
 }
 
 }  // namespace
@@ -329,14 +329,17 @@ __global__ void __launch_bounds__(128) k_profile_partial(
 }
 
 namespace {
-__global__ void __launch_bounds__(128) k_profile_final(
+// block x (launch nx blocks of 256 threads) sums the chunk partials of
+// column x in a fixed order
+__global__ void __launch_bounds__(256) k_profile_final(
     const double* __restrict__ partial, int nchunks, Dims d,
     double* __restrict__ out) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= d.nx) return;
+  __shared__ double sh[32];
+  const int x = blockIdx.x;
   double s = 0.0;
-  for (int c = 0; c < nchunks; c++) s += partial[(int64_t)c * d.nx + x];
-  out[x] = s / ((double)d.ny * (double)d.nz);
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x) s += partial[(int64_t)c * d.nx + x];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[x] = s / ((double)d.ny * (double)d.nz);
 }
 }  // namespace
 

@@ -664,7 +664,7 @@ class Engine final : public EngineBase {
     k_obs_state<Lat, T><<<I.obs_blocks, 256, 0, st>>>(I.q[cur_], I.g[cur_], I.pi, d, I.p, s_ref,
                                                       iso_, I.partial);
     NLC_CK_LAUNCH("k_obs_state");
-    k_obs_final<<<1, 256, 0, st>>>(I.partial, I.obs_blocks, I.partial + I.obs_blocks * OBS_SLOTS);
+    k_obs_final<<<OBS_SLOTS, 256, 0, st>>>(I.partial, I.obs_blocks, I.partial + I.obs_blocks * OBS_SLOTS);
     NLC_CK_LAUNCH("k_obs_final");
     const int64_t rows = (int64_t)d.ny * d.nz;
     const int rows_per_chunk = 64;
@@ -672,7 +672,7 @@ class Engine final : public EngineBase {
     dim3 pg((d.nx + 127) / 128, nchunks);
     k_profile_partial<T><<<pg, 128, 0, st>>>(I.q[cur_], d, rows_per_chunk, I.prof_partial);
     NLC_CK_LAUNCH("k_profile_partial");
-    k_profile_final<<<(d.nx + 127) / 128, 128, 0, st>>>(I.prof_partial, nchunks, d, I.prof);
+    k_profile_final<<<d.nx, 256, 0, st>>>(I.prof_partial, nchunks, d, I.prof);
     NLC_CK_LAUNCH("k_profile_final");
     double tot[OBS_SLOTS];
     std::vector<double> prof(d.nx);
@@ -760,7 +760,7 @@ class Engine final : public EngineBase {
     NLC_CK(cudaGetDevice(&dev));
     NLC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int64_t want = (n + 255) / 256;
-    I.obs_blocks = (int)(want < 4 * sms ? want : 4 * sms);
+    I.obs_blocks = (int)(want < 16 * sms ? want : 16 * sms);
     if (I.obs_blocks < 1) I.obs_blocks = 1;
     if ((s = alloc(&I.partial, (size_t)(I.obs_blocks + 1) * OBS_SLOTS))) return s;
     const int64_t rows = (int64_t)I.d.ny * I.d.nz;

@@ -90,13 +90,13 @@ nlc_status run(const Dims& d, const Par<double>& p, const double* f, const doubl
   const int blocks = (int)(gb < (unsigned)kObsBlocks ? gb : (unsigned)kObsBlocks);
   const double s_ref = 1.0 / 3.0;
   k_obs_partial<Lat, double><<<blocks, 256, 0, st>>>(Qf, f, rho, u, d, p, s_ref, part);
-  k_obs_final<<<1, 256, 0, st>>>(part, blocks, part + blocks * OBS_SLOTS);
+  k_obs_final<<<OBS_SLOTS, 256, 0, st>>>(part, blocks, part + blocks * OBS_SLOTS);
   const int64_t rows = (int64_t)d.ny * d.nz;
   const int rows_per_chunk = 64;
   const int nchunks = (int)((rows + rows_per_chunk - 1) / rows_per_chunk);
   k_profile_partial<double><<<dim3((d.nx + 127) / 128, nchunks), 128, 0, st>>>(
       Qf, d, rows_per_chunk, profp);
-  k_profile_final<<<(d.nx + 127) / 128, 128, 0, st>>>(profp, nchunks, d, prof);
+  k_profile_final<<<d.nx, 256, 0, st>>>(profp, nchunks, d, prof);
   if (cudaGetLastError() != cudaSuccess) return NLC_ECUDA;
   double tot[OBS_SLOTS];
   double hprof[kMaxNx];

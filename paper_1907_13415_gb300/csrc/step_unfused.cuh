@@ -154,11 +154,15 @@ template <class T, int DIM>
 __device__ __forceinline__ void force_at(const T* __restrict__ Pi,
                                          const Dims& d, int x, int y, int z,
                                          T F[3]) {
-  const int64_t nb[3][2] = {
-      {cell_of(d, wrap_inc(x, d.nx), y, z), cell_of(d, wrap_dec(x, d.nx), y, z)},
-      {cell_of(d, x, wrap_inc(y, d.ny), z), cell_of(d, x, wrap_dec(y, d.ny), z)},
-      {DIM == 3 ? cell_of(d, x, y, wrap_inc(z, d.nz)) : 0,
-       DIM == 3 ? cell_of(d, x, y, wrap_dec(z, d.nz)) : 0}};
+  // neighbour cells in unsigned 32-bit arithmetic (a lattice holds fewer
+  // than 2^32 cells)
+  const unsigned nx = (unsigned)d.nx, nxy = nx * (unsigned)d.ny;
+  const unsigned pz = (unsigned)z * nxy, ry = (unsigned)y * nx;
+  const unsigned nb[3][2] = {
+      {pz + ry + (unsigned)wrap_inc(x, d.nx), pz + ry + (unsigned)wrap_dec(x, d.nx)},
+      {pz + (unsigned)wrap_inc(y, d.ny) * nx + x, pz + (unsigned)wrap_dec(y, d.ny) * nx + x},
+      {DIM == 3 ? (unsigned)wrap_inc(z, d.nz) * nxy + ry + x : 0u,
+       DIM == 3 ? (unsigned)wrap_dec(z, d.nz) * nxy + ry + x : 0u}};
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     T s = T(0);
@@ -196,12 +200,19 @@ __device__ __forceinline__ void force_at_iso(const T* __restrict__ Pi, const Dim
 template <class Lat, class T, class G>
 __device__ __forceinline__ void pull(const G* __restrict__ gin, const Dims& d,
                                      int x, int y, int z, T g[Lat::Q]) {
+  // source offsets along each axis for c = +1, 0, -1 (index 1 - c), in
+  // unsigned 32-bit arithmetic (a lattice holds fewer than 2^32 cells)
+  const unsigned nx = (unsigned)d.nx, nxy = nx * (unsigned)d.ny;
+  const unsigned col[3] = {(unsigned)wrap_dec(x, d.nx), (unsigned)x, (unsigned)wrap_inc(x, d.nx)};
+  const unsigned row[3] = {(unsigned)wrap_dec(y, d.ny) * nx, (unsigned)y * nx,
+                           (unsigned)wrap_inc(y, d.ny) * nx};
+  const unsigned pz = (unsigned)z * nxy;
+  const unsigned pla[3] = {Lat::DIM == 3 ? (unsigned)wrap_dec(z, d.nz) * nxy : pz, pz,
+                           Lat::DIM == 3 ? (unsigned)wrap_inc(z, d.nz) * nxy : pz};
 #pragma unroll
   for (int i = 0; i < Lat::Q; i++) {
-    const int xs = wrap_add(x, -Lat::c(i, 0), d.nx);
-    const int ys = wrap_add(y, -Lat::c(i, 1), d.ny);
-    const int zs = Lat::DIM == 3 ? wrap_add(z, -Lat::c(i, 2), d.nz) : z;
-    g[i] = T(gin[(int64_t)i * d.n + cell_of(d, xs, ys, zs)]);
+    const unsigned off = pla[1 - Lat::c(i, 2)] + row[1 - Lat::c(i, 1)] + col[1 - Lat::c(i, 0)];
+    g[i] = T(gin[(int64_t)i * d.n + off]);
   }
 }
 
