@@ -256,6 +256,16 @@ def baseline_shape(w):
     return (max(8, nz // 8), ny, nx)
 
 
+def workload_config(args, w, ws):
+    """The workload a bench line measures; the same dict on both arms."""
+    nz, ny, nx = w.shape
+    return {"workload": w.name, "lattice": "D3Q19", "precision": args.precision,
+            "shape": [nx, ny, nz], "radius": w.size, "gamma": w.params["gamma"],
+            "parallelism": f"replicas{ws}",
+            "collision": "mrt" if args.mrt else "bgk",
+            "l2": "inputs larger than L2 (3.2 GB of state)"}
+
+
 def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -289,8 +299,7 @@ def run_reference(args, w):
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "lattice": "D3Q19",
-                   "shape": [nx, ny, shape[0]], "note": "CPU oracle sample"},
+        "config": workload_config(args, w, ws),
         "cpu_baseline": {"value": value, "unit": UNIT,
                          "cores": int(os.environ["OMP_NUM_THREADS"]),
                          "kind": "oracle", "sample": sample},
@@ -430,15 +439,8 @@ def run_ours(args, w):
             "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic",
-            "config": {"workload": w.name, "lattice": "D3Q19",
-                       "precision": args.precision,
-                       "shape": [nx, ny, nz], "radius": w.size,
-                       "gamma": w.params["gamma"],
-                       "parallelism": f"replicas{ws}",
-                       "collision": "mrt" if args.mrt else "bgk",
-                       "chunk": nlc_chunk[0], "taper": nlc_chunk[1],
-                       "l2": "inputs larger than L2 (3.2 GB of state)"},
-            "autotune": tune,
+            "config": workload_config(args, w, ws),
+            "tuning": {"chunk": nlc_chunk[0], "taper": nlc_chunk[1], "autotune": tune},
             "roofline": roofline, "step_roofline": step_roofline,
             "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
