@@ -164,11 +164,14 @@ struct ObsConst {
   }
 };
 
+// (The non-finite count is kept as an integer and the maximum of |u| in T,
+// where both are exact; GB300 runs float64 arithmetic at a small fraction of
+// its float32 rate.)
 template <class T>
 __device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x, int y, int z,
-                                         double r, const double u[3], int nbad,
+                                         double r, const double u[3], int& nbad,
                                          const ObsConst<T>& c, double acc[OBS_SLOTS - 1],
-                                         double& umax) {
+                                         T& umax) {
   T uu = T(0);
   acc[0] += r;
 #pragma unroll
@@ -176,7 +179,7 @@ __device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x
     acc[1 + a] += r * u[a];
     uu += T(u[a]) * T(u[a]);
   }
-  umax = fmax(umax, (double)sqrt(uu));
+  umax = fmax(umax, sqrt(uu));
   acc[7] += (double)uu;
   T q[5];
 #pragma unroll
@@ -212,15 +215,17 @@ __device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x
   }
   acc[4] += (double)(sqrt(T(1.5) * tr2) * c.inv_sref);
   acc[5] += (double)en;
-  acc[6] += (double)nbad;
 }
 
 // per-block float64 partials of the accumulators into partial[block]
-__device__ __forceinline__ void obs_block_out(const double acc[OBS_SLOTS - 1], double umax,
+// (slot 6, the non-finite count, from the integer count nbad)
+template <class T>
+__device__ __forceinline__ void obs_block_out(double acc[OBS_SLOTS - 1], int nbad, T umax,
                                               double* sh, double* __restrict__ partial) {
+  acc[6] = (double)nbad;
   double tot[OBS_SLOTS];
   for (int k = 0; k < OBS_SLOTS - 1; k++) tot[k] = block_sum(acc[k], sh);
-  tot[OBS_SLOTS - 1] = block_max(umax, sh);
+  tot[OBS_SLOTS - 1] = block_max((double)umax, sh);
   if (threadIdx.x == 0)
     for (int k = 0; k < OBS_SLOTS; k++) partial[blockIdx.x * OBS_SLOTS + k] = tot[k];
 }
@@ -236,19 +241,19 @@ __global__ void __launch_bounds__(256) k_obs_partial(
     Par<T> p, double s_ref, double* __restrict__ partial) {
   __shared__ double sh[32];
   double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0, 0};
-  double umax = 0.0;
+  T umax = T(0);
+  int nbad = 0;
   const ObsConst<T> c(p, s_ref);
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < d.n;
        idx += (int64_t)gridDim.x * blockDim.x) {
     int x, y, z;
     decode(d, idx, x, y, z);
-    int nbad = 0;
 #pragma unroll
     for (int i = 0; i < Lat::Q; i++) nbad += !isfinite((T)gpost[(int64_t)i * d.n + idx]);
     const double uc[3] = {u[idx], u[d.n + idx], u[2 * d.n + idx]};
     obs_cell<T>(Q, d, x, y, z, rho[idx], uc, nbad, c, acc, umax);
   }
-  obs_block_out(acc, umax, sh, partial);
+  obs_block_out<T>(acc, nbad, umax, sh, partial);
 }
 
 // The same from the state itself: rho and u of Eq. 6 are formed per cell
@@ -261,7 +266,8 @@ __global__ void __launch_bounds__(256) k_obs_state(
     double s_ref, bool iso, double* __restrict__ partial) {
   __shared__ double sh[32];
   double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0, 0};
-  double umax = 0.0;
+  T umax = T(0);
+  int nbad = 0;
   const ObsConst<T> c(p, s_ref);
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < d.n;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -273,14 +279,13 @@ __global__ void __launch_bounds__(256) k_obs_state(
     else
       force_at<T, Lat::DIM>(Pi, d, x, y, z, F);
     pull<Lat, T>(gin, d, x, y, z, g);
-    int nbad = 0;
 #pragma unroll
     for (int i = 0; i < Lat::Q; i++) nbad += !isfinite(g[i]);
     moments<Lat, T>(g, F, p, rho, u);
     const double uc[3] = {(double)u[0], (double)u[1], (double)u[2]};
     obs_cell<T>(Q, d, x, y, z, (double)rho, uc, nbad, c, acc, umax);
   }
-  obs_block_out(acc, umax, sh, partial);
+  obs_block_out<T>(acc, nbad, umax, sh, partial);
 }
 
 namespace {  // non-template kernels: one private copy per translation unit
