@@ -1,6 +1,7 @@
-"""Parity at the full size the bench measures: the 256^3 D3Q19 spherical
-droplet in FP32, in the bench's launch configuration (the chunk list the
-autotuner picks), two steps.
+"""Parity at the full sizes of the measured workloads.
+
+The 256^3 D3Q19 spherical droplet in FP32, in the bench's launch
+configuration (the chunk list the autotuner picks), two steps:
 
 The oracle cannot step the whole lattice in seconds, so it checks sampled
 cells one by one: one step at a cell depends only on inputs within four
@@ -11,6 +12,11 @@ outside, on every lattice face (periodic wrap), and on tile and z-chunk
 boundaries.  Properties that hold at any size are checked over the whole
 lattice: mass is conserved and the total momentum stays zero (the force is
 the divergence of the stress, which sums to zero on a periodic lattice).
+
+The 256^2 circular droplet and members of the 64-lattice temperature sweep
+are small enough to compare every cell with the oracle; the adjoint
+workload (128^2, 2000 steps) is checked against central differences of the
+forward run.
 """
 import numpy as np
 import pytest
@@ -115,3 +121,104 @@ def test_sampled_cells_match_oracle_at_full_size(orc):
         df = np.abs(f[:, cz, cy, cx] - fo[perm][:, HALF, HALF, HALF]).max()
         assert dq < tol * q_scale, ((cz, cy, cx), dq)
         assert df < tol * f_scale, ((cz, cy, cx), df)
+
+
+def run_gpu_steps(w, steps, precision):
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=precision,
+                         stream=torch.cuda.current_stream().cuda_stream)
+    sim.set_fields(w.initial_q5())
+    sim.step(steps)
+    Q, _, _ = sim.get_fields()
+    f = sim.get_populations()
+    obs = sim.observables()
+    sim.close()
+    return Q, f, obs
+
+
+@pytest.mark.parametrize("delta", [0.0, 0.005])
+def test_disc_256_fp32_matches_oracle_in_full(orc, delta):
+    """The circular droplet (256^2 D2Q9, R = 32) at its full size in the FP32
+    bulk form, every cell against the FP64 oracle, with the FP64 drift of
+    mass and radius."""
+    w = wl.disc_256(delta)
+    steps = 50
+    Q, f, obs = run_gpu_steps(w, steps, precision=1)
+    p = wl.param_vector(w.params)
+    f0 = orc.init_equilibrium(w.lattice, w.shape)
+    fo, Qo = orc.step(w.lattice, p, f0, w.initial_q5(), steps)
+    oo = orc.observables(w.lattice, p, fo, Qo)
+    perm = perm_to_oracle(orc, w.lattice)
+    tol = fp32_tolerance(steps)
+    assert np.abs(Q - Qo).max() < tol * np.abs(Qo).max()
+    assert np.abs(f - fo[perm]).max() < tol * np.abs(fo).max()
+    assert abs(obs["radius"] - float(oo["radius"])) < 1e-4
+    assert abs(obs["mass"] - float(oo["mass"])) < 1e-6 * float(oo["mass"])
+
+
+def test_sweep_64_members_match_oracle(orc):
+    """The batched temperature sweep at its full size (64 lattices in one
+    tile list, steps replayed as CUDA graphs as the bench runs it): the
+    largest, the smallest and a middle member, every cell against the
+    oracle."""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    ws = wl.sweep_64()
+    steps = 10
+    b = nlc.Batch(wl.D2Q9, [w.shape for w in ws], [w.params for w in ws],
+                  precision=nlc.NLC_FP32,
+                  stream=torch.cuda.current_stream().cuda_stream, graph_steps=5)
+    for i, w in enumerate(ws):
+        b.set_fields(i, w.initial_q5())
+    b.step(steps)
+    cells = [w.n_cells for w in ws]
+    picks = {int(np.argmax(cells)), int(np.argmin(cells)), len(ws) // 2}
+    perm = perm_to_oracle(orc, wl.D2Q9)
+    tol = fp32_tolerance(steps)
+    for i in sorted(picks):
+        w = ws[i]
+        Q, _, _ = b.get_fields(i)
+        f = b.get_populations(i)
+        p = wl.param_vector(w.params)
+        fo, Qo = orc.step(w.lattice, p, orc.init_equilibrium(w.lattice, w.shape),
+                          w.initial_q5(), steps)
+        assert np.abs(Q - Qo).max() < tol * np.abs(Qo).max(), i
+        assert np.abs(f - fo[perm]).max() < tol * np.abs(fo).max(), i
+    b.close()
+
+
+def test_adjoint_workload_in_full_matches_central_differences():
+    """The adjoint workload at its full size (128^2 D2Q9 disc, 2000 steps,
+    checkpoints every 100): the FP64 adjoint's dL/dgamma against central
+    differences (h = 1e-6) of the FP64 forward run, and the FP32 adjoint
+    within 2% of the FP64 one.  (The oracle's own derivative, by complex
+    step, is the check at smaller sizes.)"""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    w = wl.adjoint_disc_128()
+    steps, ckpt, target = w.steps, w.extra["ckpt_every"], w.extra["target_radius"]
+    st = torch.cuda.current_stream().cuda_stream
+
+    def adjoint(precision):
+        s = nlc.Simulation(w.lattice, w.shape, w.params, precision=precision, stream=st)
+        s.set_fields(w.initial_q5())
+        g = s.adjoint(target, 1.0, 1.0, nsteps=steps, ckpt_every=ckpt, want_dQ0=False)
+        s.close()
+        return g
+
+    g64, g32 = adjoint(0), adjoint(1)
+    h = 1e-6
+    Ls = []
+    for sgn in (1, -1):
+        p = dict(w.params, gamma=w.params["gamma"] + sgn * h)
+        s = nlc.Simulation(w.lattice, w.shape, p, precision=0, stream=st)
+        s.set_fields(w.initial_q5())
+        s.step(steps)
+        o = s.observables()
+        Ls.append((o["radius"] - target) ** 2 + o["u_l2"])
+        s.close()
+    fd = (Ls[0] - Ls[1]) / (2 * h)
+    assert g64["dgamma"] == pytest.approx(fd, rel=1e-5)
+    for k in ("dgamma", "dK", "dGamma"):
+        assert g32[k] == pytest.approx(g64[k], rel=2e-2), k
