@@ -667,7 +667,7 @@ class Engine final : public EngineBase {
     k_obs_final<<<OBS_SLOTS, 256, 0, st>>>(I.partial, I.obs_blocks, I.partial + I.obs_blocks * OBS_SLOTS);
     NLC_CK_LAUNCH("k_obs_final");
     const int64_t rows = (int64_t)d.ny * d.nz;
-    const int rows_per_chunk = 64;
+    const int rows_per_chunk = profile_rows_per_chunk(d);
     const int nchunks = (int)((rows + rows_per_chunk - 1) / rows_per_chunk);
     dim3 pg((d.nx + 127) / 128, nchunks);
     k_profile_partial<T><<<pg, 128, 0, st>>>(I.q[cur_], d, rows_per_chunk, I.prof_partial);
@@ -708,6 +708,14 @@ class Engine final : public EngineBase {
 
  private:
   static unsigned grid1(int64_t count) { return (unsigned)((count + 255) / 256); }
+
+  // rows (y, z) per block of the S-profile pass: about 2048 blocks over the
+  // lattice, so that small lattices still spread over the SMs
+  static int profile_rows_per_chunk(const Dims& d) {
+    const int64_t xb = (d.nx + 127) / 128, rows = (int64_t)d.ny * d.nz;
+    const int64_t chunks = std::max<int64_t>(1, 2048 / xb);
+    return (int)std::max<int64_t>(1, (rows + chunks - 1) / chunks);
+  }
 
   template <class U>
   nlc_status alloc(U** p, size_t count) {
@@ -764,7 +772,8 @@ class Engine final : public EngineBase {
     if (I.obs_blocks < 1) I.obs_blocks = 1;
     if ((s = alloc(&I.partial, (size_t)(I.obs_blocks + 1) * OBS_SLOTS))) return s;
     const int64_t rows = (int64_t)I.d.ny * I.d.nz;
-    const int64_t nchunks = (rows + 63) / 64;
+    const int rpc = profile_rows_per_chunk(I.d);
+    const int64_t nchunks = (rows + rpc - 1) / rpc;
     if ((s = alloc(&I.prof_partial, (size_t)(nchunks * I.d.nx)))) return s;
     if ((s = alloc(&I.prof, (size_t)I.d.nx))) return s;
     return NLC_OK;
