@@ -223,22 +223,24 @@ NLC_API nlc_status nlc_set_check(nlc_ctx* ctx, int32_t every);
 /* Selects the kernel schedule (NLC_SCHED_*) for later nlc_step calls. */
 NLC_API nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule);
 
-/* Depth of the z-chunks of the fused schedule on D3Q19 lattices: each
- * thread block of the two step kernels marches through the planes of one
- * chunk of one 32 x 8 column of the lattice.  The chunk depth trades the two
- * extra planes every chunk recomputes against the number of blocks the GPU
- * spreads over its SMs.  chunk > 0: chunks of that many planes (capped at
- * nz); chunk = 0: the library's default depth.  taper = 1: chunks of `chunk`
- * planes until at most 2 chunk planes of the column remain, then chunks
- * halving down to about 8 planes; the blocks run chunk by chunk, so the last
- * blocks are short and the last wave over the SMs idles less of the GPU.
- * Neither changes any result: every chunk list computes the same step bit
- * for bit.  A runtime choice of this library; the paper has no counterpart.
- * No-op on D2Q9.  Synchronises the stream.  Errors: NLC_EINVAL (chunk < 0,
- * taper not 0 or 1). */
+/* Depth of the chunks of the fused schedule.  On D3Q19 each thread block of
+ * the two step kernels marches through the z planes of one chunk of one
+ * 32 x 8 column of the lattice, and the depth trades the two extra planes
+ * every chunk recomputes against the number of blocks the GPU spreads over
+ * its SMs.  On D2Q9 each block works through a chunk of 32 x 8 tiles
+ * stacked along y, loading the next tile while it computes the current one;
+ * the depth counts those tiles.  chunk > 0: chunks of that many planes
+ * (tiles), capped at the column's length; chunk = 0: the library's default
+ * depth.  taper = 1: chunks of `chunk` until at most 2 chunk of the column
+ * remain, then chunks halving down to about 8 planes (tiles); the blocks run
+ * chunk by chunk, so the last blocks are short and the last wave over the
+ * SMs idles less of the GPU.  Neither changes any result: every chunk list
+ * computes the same step bit for bit.  A runtime choice of this library;
+ * the paper has no counterpart.  Synchronises the stream.  Errors:
+ * NLC_EINVAL (chunk < 0, taper not 0 or 1). */
 NLC_API nlc_status nlc_set_chunk(nlc_ctx* ctx, int32_t chunk, int32_t taper);
 
-/* Chunk depth in use for lattice inst (1 on D2Q9), or -1 for a NULL context
+/* Chunk depth in use for lattice inst, or -1 for a NULL context
  * or an instance out of range; *taper (may be NULL) gets 1 for a tapered
  * chunk list. */
 NLC_API int32_t nlc_get_chunk(const nlc_ctx* ctx, int32_t inst, int32_t* taper);
@@ -254,8 +256,8 @@ NLC_API int32_t nlc_get_chunk(const nlc_ctx* ctx, int32_t inst, int32_t* taper);
  * (name, SM count), with the chunk depth as value (negative for a tapered
  * list): a key found there is applied without timing (out->from_cache = 1),
  * a new result is added.  Needs two extra copies of the populations and Q of the whole
- * context in device memory while it runs (freed before it returns).  No-op
- * on D2Q9 (out->chunk = 1).  out may be NULL.  Synchronises the stream.
+ * context in device memory while it runs (freed before it returns).  out may
+ * be NULL.  Synchronises the stream.
  * Errors: NLC_EINVAL (trial_steps < 1), NLC_ENOMEM, NLC_ECUDA,
  * NLC_ETIMEOUT. */
 NLC_API nlc_status nlc_autotune(nlc_ctx* ctx, int32_t trial_steps, nlc_tune* out);

@@ -189,13 +189,11 @@ class Engine final : public EngineBase {
   nlc_status set_chunk(int tz, bool taper) override {
     cudaStream_t st = args_.stream;
     std::vector<TileRef> tiles;
-    taper_ = DIM == 3 && taper;
+    taper_ = taper;
     for (size_t i = 0; i < inst_.size(); i++) {
       InstHost<T, G>& I = inst_[i];
-      if (DIM == 2)
-        I.tz = 1;
-      else
-        I.tz = tz > 0 ? std::min(tz, I.d.nz) : fused_tz<Lat>(I.d, (int64_t)tiles.size());
+      I.tz = tz > 0 ? std::min(tz, column_length<Lat>(I.d))
+                    : fused_tz<Lat>(I.d, (int64_t)tiles.size());
       append_tiles<Lat>((int)i, I.d, I.tz, taper_, &tiles);
     }
     NLC_CK(cudaStreamSynchronize(st));  // no step may still read the old list
@@ -228,21 +226,22 @@ class Engine final : public EngineBase {
     cudaStream_t st = args_.stream;
     *out = nlc_tune{};
     out->trial_steps = trial_steps;
-    if (DIM == 2) {
-      out->chunk = 1;
-      return NLC_OK;
-    }
     if (!maps_ok_) {
       err = "TMA tensor maps unavailable: the fused schedule cannot run";
       return NLC_EUNSUPPORTED;
     }
     int maxz = 1;
-    for (const auto& I : inst_) maxz = std::max(maxz, I.d.nz);
-    // (depth, taper); depth 0: the default choice
+    for (const auto& I : inst_) maxz = std::max(maxz, column_length<Lat>(I.d));
+    // (depth, taper); depth 0: the default choice.  Depths count z planes on
+    // D3Q19 and stacked tiles on a single plane.
     std::vector<std::pair<int, bool>> cand = {{0, false}};
-    for (int c : {4, 6, 8, 12, 16, 24, 32, 48, 64})
+    const std::vector<int> uni = DIM == 3 ? std::vector<int>{4, 6, 8, 12, 16, 24, 32, 48, 64}
+                                          : std::vector<int>{1, 2, 4, 8, 16, 32};
+    const std::vector<int> tap = DIM == 3 ? std::vector<int>{16, 24, 32, 48, 64, 96, 128}
+                                          : std::vector<int>{4, 8, 16, 32};
+    for (int c : uni)
       if (c <= maxz) cand.push_back({c, false});
-    for (int c : {16, 24, 32, 48, 64, 96, 128})
+    for (int c : tap)
       if (c <= maxz) cand.push_back({c, true});
     // saved state
     const int cur0 = cur_;
@@ -279,7 +278,8 @@ class Engine final : public EngineBase {
     for (size_t k = 0; k < cand.size() && s == NLC_OK; k++) {
       if ((s = set_chunk(cand[k].first, cand[k].second))) break;
       std::vector<std::vector<int>> bounds;
-      for (const auto& I : inst_) bounds.push_back(chunk_bounds(I.d.nz, I.tz, taper_));
+      for (const auto& I : inst_)
+        bounds.push_back(chunk_bounds(column_length<Lat>(I.d), I.tz, taper_));
       if (std::find(timed.begin(), timed.end(), bounds) != timed.end()) continue;
       timed.push_back(bounds);
       if ((s = step_fused(st))) break;  // warm-up

@@ -99,7 +99,8 @@ struct InstDev {
 };
 
 // One thread block's work: a 32 x 8 (x, y) tile of instance `inst`, planes
-// z0 .. z1 - 1 (z0 = 0, z1 = 1 on a single plane).
+// z0 .. z1 - 1; on a single plane, z1 tiles stacked along y from row y0
+// (z0 = 0).
 struct TileRef {
   int inst, x0, y0, z0, z1;
 };
@@ -117,11 +118,13 @@ struct LbCfg {
   static constexpr int THREADS = 352;  // 11 warps
   static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;
   static_assert(THREADS >= RING_T && THREADS >= CELL0 + FTX * FTY, "block too small");
-  static constexpr int NSQ = DIM == 3 ? 4 : 1;  // Q plane slots
+  // Q plane slots (on a single plane: tile slots, the next tile's copy in
+  // flight while the current one is used)
+  static constexpr int NSQ = DIM == 3 ? 4 : 2;
   // Pi plane slots: the ring phase of plane z+1 may start while slower
   // threads still read Pi(z-2..z) for plane z-1, so four slots let one
-  // barrier per plane suffice
-  static constexpr int NSP = DIM == 3 ? 4 : 1;
+  // barrier per plane suffice (on a single plane, two tile slots)
+  static constexpr int NSP = DIM == 3 ? 4 : 2;
   static constexpr size_t q_slot = align128<T>(sizeof(T) * 5 * BA);
   static constexpr size_t p_slot = align128<T>(sizeof(T) * NPI * A1);
   static constexpr size_t off_p = NSQ * q_slot;
@@ -333,30 +336,39 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     }
   };
 
-  // per-thread pull offsets (x, y fixed for the whole chunk)
+  // per-thread pull offsets (x fixed for the block; y fixed for a chunk of
+  // planes, and set per tile on a single plane, where a block works through
+  // tiles stacked along y: set_tile)
   const int ct = tid - C::CELL0;
   const int tx = ct % FTX, ty = ct / FTX;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool cell = ct >= 0 && ct < FTX * FTY && x < d.nx && y < d.ny;
+  const int x = x0 + tx;
+  int y = y0 + ty;
+  bool cell = false;
   // source offsets within a plane for c_x, c_y in {-1, 0, 1} (index c + 1);
   // a lattice holds fewer than 2^31 cells, so 32-bit offsets suffice
   int colx[3] = {0, 0, 0};
   int rowy[3] = {0, 0, 0};
-  if (cell) {
-    colx[0] = wrap_inc(x, d.nx);
-    colx[1] = x;
-    colx[2] = wrap_dec(x, d.nx);
-    rowy[0] = wrap_inc(y, d.ny) * d.nx;
-    rowy[1] = y * d.nx;
-    rowy[2] = wrap_dec(y, d.ny) * d.nx;
-  }
-  const int nxy = d.nx * d.ny;
-  const int ic = (ty + 1) * RX1 + (tx + 1);
   // every cell of the tile lies GHOST or more away from the x and y faces:
   // its stores of u have no periodic images there (the same for the whole
   // block)
-  const bool tile_inner = x0 >= GHOST && x0 + FTX <= d.nx - GHOST && y0 >= GHOST &&
-                          y0 + FTY <= d.ny - GHOST;
+  bool tile_inner = false;
+  auto set_tile = [&](int yt0) {  // tile rows yt0 .. yt0 + FTY - 1
+    y = yt0 + ty;
+    cell = ct >= 0 && ct < FTX * FTY && x < d.nx && y < d.ny;
+    if (cell) {
+      colx[0] = wrap_inc(x, d.nx);
+      colx[1] = x;
+      colx[2] = wrap_dec(x, d.nx);
+      rowy[0] = wrap_inc(y, d.ny) * d.nx;
+      rowy[1] = y * d.nx;
+      rowy[2] = wrap_dec(y, d.ny) * d.nx;
+    }
+    tile_inner = x0 >= GHOST && x0 + FTX <= d.nx - GHOST && yt0 >= GHOST &&
+                 yt0 + FTY <= d.ny - GHOST;
+  };
+  set_tile(y0);
+  const int nxy = d.nx * d.ny;
+  const int ic = (ty + 1) * RX1 + (tx + 1);
 
   // The populations of the next plane are pulled into registers (gn) as
   // soon as the current plane is done, so their loads are in flight while
@@ -391,9 +403,12 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     }
   };
 
-  auto lb_cell = [&](int z) {
+  // moments, collision and stores of this thread's cell on plane z, whose
+  // stress is in Pi slot ps (the planes above and below in the slots of
+  // z -+ 1)
+  auto lb_cell = [&](int z, int ps) {
     if (!cell) return;
-    const T* Pc = sP(pslot(z));
+    const T* Pc = sP(ps);
     T F[3] = {T(0), T(0), T(0)};
     const T* Pm = DIM == 3 ? sP(pslot(z - 1)) : Pc;
     const T* Pp = DIM == 3 ? sP(pslot(z + 1)) : Pc;
@@ -474,15 +489,34 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
   };
 
   if constexpr (DIM == 2) {
-    if (tid == 0) issue(0);
+    // tile.z1 tiles stacked along y: tile t (rows y0 + FTY t ..) has its Q box
+    // in slot t & 1 and its stress in Pi slot t & 1; the copy of tile t + 1
+    // is in flight while tile t is computed
+    const int nt = tile.z1;
+    auto issue2 = [&](int t) {  // thread 0 only
+      const int sl = t & 1;
+      mbar_expect_tx(&bars[sl], C::tx_bytes);
+      tma_load_4d(sQ(sl), qmap, x0, y0 + FTY * t, 0, 0, &bars[sl]);
+    };
+    if (tid == 0) issue2(0);
     pull_next(0);
-    wait(0);
-    if (tid < C::RING_T) stress_ring_cell<Lat, T, ISO>(tid, sQ(0), sQ(0), sQ(0), sP(0), p);
-    if (__syncthreads_or(late)) {
-      abort_block();
-      return;
+    for (int t = 0; t < nt; t++) {
+      // tile t + 1 goes to the slot of tile t - 1, whose ring phase every
+      // thread finished before the previous barrier
+      if (tid == 0 && t + 1 < nt) issue2(t + 1);
+      late |= !mbar_wait(&bars[t & 1], (unsigned)(t >> 1) & 1u);
+      if (tid < C::RING_T)
+        stress_ring_cell<Lat, T, ISO>(tid, sQ(t & 1), sQ(t & 1), sQ(t & 1), sP(t & 1), p);
+      if (__syncthreads_or(late)) {
+        abort_block();
+        return;
+      }
+      lb_cell(0, t & 1);
+      if (t + 1 < nt) {
+        set_tile(y0 + FTY * (t + 1));
+        pull_next(0);
+      }
     }
-    lb_cell(0);
   } else {
     if (tid == 0)
       for (int z = z0 - 2; z <= z0 + 1; z++) issue(z);
@@ -517,7 +551,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
         abort_block();
         return;
       }
-      lb_cell(z);
+      lb_cell(z, pslot(z));
     }
   }
   (void)NPI;
@@ -541,9 +575,13 @@ struct BeCfg {
   static constexpr int THREADS = 352;  // 11 warps
   static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;
   static_assert(THREADS >= RING_T && THREADS >= CELL0 + CELL_T, "block too small");
-  static constexpr int NSQ = DIM == 3 ? 5 : 1;   // Q^n plane slots
-  static constexpr int NSU = DIM == 3 ? 6 : 1;   // u plane slots
-  static constexpr int NSP = DIM == 3 ? 4 : 1;   // Q^P plane slots
+  // On a single plane the slots hold stacked tiles instead: the copies of
+  // tile t + 1 are in flight while tile t is computed, and they may not
+  // overwrite tile t - 1, whose corrector can still run (three Q^n and u
+  // slots, two Q^P slots).
+  static constexpr int NSQ = DIM == 3 ? 5 : 3;   // Q^n plane slots
+  static constexpr int NSU = DIM == 3 ? 6 : 3;   // u plane slots
+  static constexpr int NSP = DIM == 3 ? 4 : 2;   // Q^P plane slots
   static constexpr size_t q_slot = align128<T>(sizeof(T) * 5 * BA);
   static constexpr size_t u_slot = align128<T>(sizeof(T) * DIM * BA);
   static constexpr size_t p_slot = align128<T>(sizeof(T) * 5 * A1);
@@ -719,12 +757,13 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     mbar_fence_init();
   }
   __syncthreads();
-  // copies of plane z into Q slot s and u slot t (thread 0)
-  auto issue = [&](int z, int s, int t) {
+  // copies of plane z of the tile at rows yt0 .. into Q slot s and u slot t
+  // (thread 0)
+  auto issue = [&](int z, int s, int t, int yt0) {
     mbar_expect_tx(&qbar[s], C::q_tx);
-    tma_load_4d(sQ(s), qmap, x0, y0, z + zoff, 0, &qbar[s]);
+    tma_load_4d(sQ(s), qmap, x0, yt0, z + zoff, 0, &qbar[s]);
     mbar_expect_tx(&ubar[t], C::u_tx);
-    tma_load_4d(sU(t), umap, x0, y0, z + zoff, 0, &ubar[t]);
+    tma_load_4d(sU(t), umap, x0, yt0, z + zoff, 0, &ubar[t]);
   };
   bool late = false;
   uint32_t qph = 0, uph = 0;  // phase bit per slot
@@ -758,11 +797,17 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     for (int k = 0; k < 5; k++) qpo[k * A1 + c] = q[k] + r[k];
   };
 
-  // corrector threads: one tile cell each
+  // corrector threads: one tile cell each (on a single plane, of the tile
+  // at rows yt0 .., set per stacked tile)
   const int ct = tid - C::CELL0;
   const int tx = ct % FTX, ty = ct / FTX;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool cell = ct >= 0 && ct < C::CELL_T && x < d.nx && y < d.ny;
+  const int x = x0 + tx;
+  int y = y0 + ty;
+  bool cell = ct >= 0 && ct < C::CELL_T && x < d.nx && y < d.ny;
+  auto set_tile = [&](int yt0) {
+    y = yt0 + ty;
+    cell = ct >= 0 && ct < C::CELL_T && x < d.nx && y < d.ny;
+  };
   const int ic = (ty + 1) * RX1 + (tx + 1);
   const int o2 = box_at(tx, ty);
 
@@ -784,19 +829,31 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
   };
 
   if constexpr (DIM == 2) {
-    if (tid == 0) issue(0, 0, 0);
-    wait(0, 0);
-    if (tid < C::RING_T) predict(tid, 0, 0, 0, 0, 0, 0, 0);
-    if (__syncthreads_or(late)) {
-      abort_block();
-      return;
+    // tile.z1 tiles stacked along y: tile t (rows y0 + FTY t ..) has its Q^n
+    // and u boxes in slots t mod 3 and its Q^P in slot t & 1
+    const int nt = tile.z1;
+    if (tid == 0) issue(0, 0, 0, y0);
+    int sq = 0;  // Q^n and u slot of tile t
+    for (int t = 0; t < nt; t++) {
+      // tile t + 1 goes to the slots of tile t - 2, whose predictor and
+      // corrector every thread finished before the previous barrier
+      const int sn = slot_add<3>(sq, 1);
+      if (tid == 0 && t + 1 < nt) issue(0, sn, sn, y0 + FTY * (t + 1));
+      wait(sq, sq);
+      if (tid < C::RING_T) predict(tid, sq, sq, sq, sq, sq, sq, t & 1);
+      if (__syncthreads_or(late)) {
+        abort_block();
+        return;
+      }
+      set_tile(y0 + FTY * t);
+      correct(0, sq, sq, sq, sq, t & 1, t & 1, t & 1);
+      sq = sn;
     }
-    correct(0, 0, 0, 0, 0, 0, 0, 0);
   } else {
     constexpr int NQ = C::NSQ, NU = C::NSU, NP = C::NSP;
     // planes z0-2 .. z0+2 go to Q and u slots 0..4
     if (tid == 0)
-      for (int k = 0; k <= 4; k++) issue(z0 - 2 + k, k, k);
+      for (int k = 0; k <= 4; k++) issue(z0 - 2 + k, k, k, y0);
     wait(0, 0);
     wait(1, 1);
     wait(2, 2);
@@ -813,7 +870,8 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
       const int sq1 = slot_add<NQ>(sq, 1), sq2 = slot_add<NQ>(sq, 2);
       const int su1 = slot_add<NU>(su, 1), su2 = slot_add<NU>(su, 2);
       const int sp1 = slot_add<NP>(sp, 1);
-      if (tid == 0 && z + 3 <= z1 + 1) issue(z + 3, slot_add<NQ>(sq, 3), slot_add<NU>(su, 3));
+      if (tid == 0 && z + 3 <= z1 + 1)
+        issue(z + 3, slot_add<NQ>(sq, 3), slot_add<NU>(su, 3), y0);
       wait(sq2, su2);
       if (tid < C::RING_T) predict(tid, sq1, sq, sq2, su1, su, su2, sp1);  // plane z+1
       if (__syncthreads_or(late)) {
@@ -832,28 +890,45 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
 // launch helpers
 // ---------------------------------------------------------------------------
 
-// z planes per tile on D3Q19: enough tiles for several waves over the SMs
-// while amortising the two-plane prologue of each chunk
+// Length of a column in chunk units: z planes on D3Q19, 32 x 8 tiles along
+// y on a single plane (where a block works through tiles stacked along y).
 template <class Lat>
-__host__ inline int fused_tz(const Dims& d, int64_t other_tiles) {
-  if (Lat::DIM == 2) return 1;
-  const int64_t tiles = (int64_t)((d.nx + FTX - 1) / FTX) * ((d.ny + FTY - 1) / FTY);
-  int tz = 32;
-  while (tz > 4 && other_tiles + tiles * ((d.nz + tz - 1) / tz) < 1200) tz /= 2;
-  return tz < d.nz ? tz : d.nz;
+__host__ inline int column_length(const Dims& d) {
+  return Lat::DIM == 3 ? d.nz : (d.ny + FTY - 1) / FTY;
 }
 
-// tile list of one instance: chunk by chunk along z, x fastest within a
-// chunk, so neighbouring blocks run together and share halos in L2
+// Default chunk depth: enough blocks for several waves over the SMs while
+// amortising the two-plane prologue of each chunk (D3Q19), or the wait for
+// the first tile's copy (a single plane)
+template <class Lat>
+__host__ inline int fused_tz(const Dims& d, int64_t other_tiles) {
+  const int len = column_length<Lat>(d);
+  const int64_t columns = (int64_t)((d.nx + FTX - 1) / FTX) *
+                          (Lat::DIM == 3 ? (d.ny + FTY - 1) / FTY : 1);
+  const int lo = Lat::DIM == 3 ? 4 : 1;
+  int tz = Lat::DIM == 3 ? 32 : 8;
+  while (tz > lo && other_tiles + columns * ((len + tz - 1) / tz) < 1200) tz /= 2;
+  return tz < len ? tz : len;
+}
+
+// tile list of one instance: chunk by chunk along z (tiles stacked along y
+// on a single plane), x fastest within a chunk, so neighbouring blocks run
+// together and share halos in L2.  On a single plane a tile's z0 is 0 and
+// z1 the number of tiles stacked from y0.
 template <class Lat>
 __host__ inline void append_tiles(int inst, const Dims& d, int tz, bool taper,
                                   std::vector<TileRef>* out) {
-  const std::vector<int> b =
-      Lat::DIM == 3 ? chunk_bounds(d.nz, tz, taper) : std::vector<int>{0, 1};
-  for (size_t zc = 0; zc + 1 < b.size(); zc++)
-    for (int y0 = 0; y0 < d.ny; y0 += FTY)
+  const std::vector<int> b = chunk_bounds(column_length<Lat>(d), tz, taper);
+  for (size_t zc = 0; zc + 1 < b.size(); zc++) {
+    if (Lat::DIM == 3) {
+      for (int y0 = 0; y0 < d.ny; y0 += FTY)
+        for (int x0 = 0; x0 < d.nx; x0 += FTX)
+          out->push_back({inst, x0, y0, b[zc], b[zc + 1]});
+    } else {
       for (int x0 = 0; x0 < d.nx; x0 += FTX)
-        out->push_back({inst, x0, y0, b[zc], b[zc + 1]});
+        out->push_back({inst, x0, FTY * b[zc], 0, b[zc + 1] - b[zc]});
+    }
+  }
 }
 
 template <class K>

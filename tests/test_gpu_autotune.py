@@ -36,22 +36,32 @@ def state(sim):
     return Q, sim.get_populations(), rho, u
 
 
+CHUNKS = ((0, False), (1, False), (2, False), (3, False), (4, False), (7, False),
+          (23, False), (64, False), (4, True), (6, True), (16, True))
+
+
+@pytest.mark.parametrize("lattice", ["D3Q19", "D2Q9"])
 @pytest.mark.parametrize("precision", ["NLC_FP32", "NLC_FP64"])
-def test_every_chunk_depth_gives_the_same_step(precision):
+def test_every_chunk_depth_gives_the_same_step(precision, lattice):
+    """Chunks of z planes on D3Q19, of 32 x 8 tiles stacked along y on D2Q9
+    (a ragged 70 x 61 lattice: 8 tiles per column, the last one partial)."""
     from paper_1907_13415_gb300 import nlc
     prec = getattr(nlc, precision)
-    w = droplet()
+    if lattice == "D3Q19":
+        w = droplet()
+        length = w.shape[0]
+    else:
+        w = wl.disc_256().with_(shape=(1, 61, 70), size=14.0, noise=1e-3, seed=35)
+        length = 8
     ref = None
-    for chunk, taper in ((0, False), (1, False), (2, False), (3, False), (4, False),
-                         (7, False), (23, False), (64, False), (4, True), (6, True),
-                         (16, True)):
+    for chunk, taper in CHUNKS:
         sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=prec,
                              stream=stream())
         sim.set_chunk(chunk, taper)
         depth, tapered = sim.chunk()
         assert tapered == taper
         if chunk:
-            assert depth == min(chunk, w.shape[0])
+            assert depth == min(chunk, length)
         sim.set_fields(w.initial_q5())
         sim.step(7)
         got = state(sim)
@@ -142,14 +152,22 @@ def test_autotune_cache_is_written_then_read(tmp_path, monkeypatch):
     second.close()
 
 
-def test_autotune_single_plane_lattices_have_no_chunks(monkeypatch):
+def test_autotune_single_plane_keeps_the_state(monkeypatch):
+    """On D2Q9 the tuner times stacks of tiles along y (a 64 x 200 lattice
+    has 25 tiles per column) and restores the state."""
     from paper_1907_13415_gb300 import nlc
     monkeypatch.delenv("NLC_TUNE_CACHE", raising=False)
-    w = wl.disc_256().with_(shape=(1, 32, 48), size=10)
+    w = wl.disc_256().with_(shape=(1, 200, 64), size=30, noise=1e-3, seed=36)
     sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
                          stream=stream())
+    sim.set_fields(w.initial_q5())
+    sim.step(3)
+    before = state(sim)
     r = sim.autotune(trial_steps=2)
-    assert r["chunk"] == 1 and r["candidates"] == 0 and sim.chunk() == (1, False)
+    assert r["candidates"] >= 3 and 1 <= r["chunk"] <= 25
+    assert sim.chunk() == (r["chunk"], bool(r["taper"]))
+    for a, b in zip(before, state(sim)):
+        assert np.array_equal(a, b)
     with pytest.raises(nlc.NlcError):
         sim.autotune(trial_steps=0)
     with pytest.raises(nlc.NlcError):
