@@ -470,6 +470,9 @@ def run_sweep(args):
                   graph_steps=args.graph_steps)
     for i, w in enumerate(ws):
         b.set_fields(i, w.initial_q5())
+    # both arms run the chunk lists the autotuner picks for them (the state
+    # is restored after tuning)
+    tune_b = b.autotune(args.tune_steps) if args.chunk < 0 else None
 
     def timed(fn, steps):
         torch.cuda.synchronize()
@@ -489,6 +492,8 @@ def run_sweep(args):
         s = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
                            stream=stream.cuda_stream)
         s.set_fields(w.initial_q5())
+        if args.chunk < 0:
+            s.autotune(args.tune_steps)
         sims.append(s)
 
     def seq(steps):
@@ -511,6 +516,7 @@ def run_sweep(args):
                                   "gamma in [2.60, 2.80]",
                       "instances": len(ws), "cells": cells,
                       "graph_steps": args.graph_steps},
+           "tuning": {"batched": tune_b},
            "sequential": {"value": v_s, "unit": UNIT,
                           "ms_per_step": t_seq / args.steps,
                           "launches_per_step": 2 * len(ws)},
