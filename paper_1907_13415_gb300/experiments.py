@@ -30,6 +30,12 @@ from . import nlc
 from . import workloads as wl
 
 
+# whole runs of this many steps replay a captured CUDA graph (the same
+# arithmetic as stepping kernel by kernel, without the launch overhead that
+# dominates the small lattices of the paper's experiments)
+GRAPH_STEPS = 50
+
+
 def _stream():
     import torch
     return torch.cuda.current_stream().cuda_stream
@@ -39,6 +45,7 @@ def _run(w, precision, steps, every, stencil=0):
     """Runs w, returning observables every `every` steps and the final Q."""
     s = nlc.Simulation(w.lattice, w.shape, w.params, precision=precision,
                        stream=_stream())
+    s.set_graph(GRAPH_STEPS)
     s.set_stencil(stencil)
     s.set_fields(w.initial_q5())
     trace = [s.observables()]
@@ -114,6 +121,7 @@ def paper_circle(angle_deg=0.0, steps=35000, every=1000, gamma=2.707681,
                     (math.sin(a), math.cos(a), 0.0), 0.0, 0)
     s = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP64,
                        stream=_stream())
+    s.set_graph(GRAPH_STEPS)
     s.set_stencil(stencil)
     s.set_fields(w.initial_q5())
     trace = [s.observables()]
@@ -183,6 +191,7 @@ def flat_paper(gamma=2.7, steps=350000, lx=200, ly=8, every=10000):
     Q0 = wl.uniaxial_q5(np.broadcast_to(S, (1, ly, lx)).copy(), (0, 1, 0))
     s = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP64,
                        stream=_stream())
+    s.set_graph(GRAPH_STEPS)
     s.set_fields(Q0)
     xs, done = [], 0
     while done < steps:
