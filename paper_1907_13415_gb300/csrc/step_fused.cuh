@@ -18,6 +18,9 @@
 // arrive by TMA (one cp.async.bulk.tensor per plane and field) into rings of
 // shared-memory slots, each completed on its own mbarrier, issued one plane
 // ahead of use so the copy overlaps the computation of the current plane.
+// On a single plane (D2Q9) it works the same way through a chunk of tiles
+// stacked along y instead, the next tile's boxes in flight while the
+// current tile is computed.
 // Q and u are padded fields with periodic ghost rings (common.cuh), so every
 // tile box is a plain rectangle; the kernels that write them also write the
 // images.  Populations are read by pull with precomputed periodic offsets.
