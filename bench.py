@@ -61,8 +61,8 @@ def alg_bytes(precision):
 # on; reported as null once those sources change.
 NCU_TRAFFIC = {
     # 256 x 256 x 64 capture (4,194,304 cells), see profiles/
-    "fused_lb": ((421.471232e6 + 334.225664e6) / 4194304, "7b2bb063c14e13b9"),
-    "fused_be": ((153.883392e6 + 60.461824e6) / 4194304, "7b2bb063c14e13b9"),
+    "fused_lb": ((421.175296e6 + 334.067712e6) / 4194304, "63ac9605e32f4fab"),
+    "fused_be": ((153.899008e6 + 61.059840e6) / 4194304, "63ac9605e32f4fab"),
 }
 
 KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",
@@ -73,10 +73,18 @@ KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",
 
 
 def source_hash():
+    """SHA-256 of the kernel sources with their comments and blank lines
+    removed (a comment edit leaves the kernels, and their counters, as
+    they were)."""
+    import re
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, p)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(text.encode())
     return h.hexdigest()[:16]
 
 
