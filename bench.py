@@ -479,8 +479,12 @@ def run_sweep(args):
     for i, w in enumerate(ws):
         b.set_fields(i, w.initial_q5())
     # both arms run the chunk lists the autotuner picks for them (the state
-    # is restored after tuning)
-    tune_b = b.autotune(args.tune_steps) if args.chunk < 0 else None
+    # is restored after tuning), or the one --chunk gives
+    tune_b = None
+    if args.chunk < 0:
+        tune_b = b.autotune(args.tune_steps)
+    else:
+        b.set_chunk(args.chunk, args.taper)
 
     def timed(fn, steps):
         torch.cuda.synchronize()
@@ -502,6 +506,8 @@ def run_sweep(args):
         s.set_fields(w.initial_q5())
         if args.chunk < 0:
             s.autotune(args.tune_steps)
+        else:
+            s.set_chunk(args.chunk, args.taper)
         sims.append(s)
 
     def seq(steps):
@@ -524,7 +530,7 @@ def run_sweep(args):
                                   "gamma in [2.60, 2.80]",
                       "instances": len(ws), "cells": cells,
                       "graph_steps": args.graph_steps},
-           "tuning": {"batched": tune_b},
+           "tuning": {"batched": tune_b, "chunk": args.chunk, "taper": args.taper},
            "sequential": {"value": v_s, "unit": UNIT,
                           "ms_per_step": t_seq / args.steps,
                           "launches_per_step": 2 * len(ws)},
