@@ -131,7 +131,13 @@ struct LbCfg {
   static constexpr size_t q_slot = align128<T>(sizeof(T) * 5 * BA);
   static constexpr size_t p_slot = align128<T>(sizeof(T) * NPI * A1);
   static constexpr size_t off_p = NSQ * q_slot;
-  static constexpr size_t off_bar = off_p + NSP * p_slot;
+  // D3Q19: the force of the tile's cells, two plane slots [3][FTX FTY]
+  // (formed by the warps without a tile cell, read by the cell phase one
+  // plane later)
+  static constexpr int NSF = DIM == 3 ? 2 : 0;
+  static constexpr size_t f_slot = align128<T>(sizeof(T) * 3 * FTX * FTY);
+  static constexpr size_t off_f = off_p + NSP * p_slot;
+  static constexpr size_t off_bar = off_f + NSF * f_slot;
   static constexpr size_t bytes = off_bar + 8 * NSQ;
   static constexpr uint32_t tx_bytes = sizeof(T) * 5 * BA;
 };
@@ -409,12 +415,14 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
   // moments, collision and stores of this thread's cell on plane z, whose
   // stress is in Pi slot ps (the planes above and below in the slots of
   // z -+ 1)
-  auto lb_cell = [&](int z, int ps) {
-    if (!cell) return;
+  // F at the tile cell with ring index icc from the stress of its plane in
+  // Pi slot ps (the planes below and above in slots psm, psp)
+  auto force_cell = [&](int icc, int ps, int psm, int psp, T F[3]) {
     const T* Pc = sP(ps);
-    T F[3] = {T(0), T(0), T(0)};
-    const T* Pm = DIM == 3 ? sP(pslot(z - 1)) : Pc;
-    const T* Pp = DIM == 3 ? sP(pslot(z + 1)) : Pc;
+    const T* Pm = sP(psm);
+    const T* Pp = sP(psp);
+    const int ic = icc;
+    F[0] = F[1] = F[2] = T(0);
     if constexpr (ISO) {
       // F_a = 3 sum_i w_i sum_b c_ib Pi_ab(x + c_i)
 #pragma unroll
@@ -441,6 +449,12 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
         F[a] = s * T(0.5);
       }
     }
+  };
+
+  // moments, collision and stores of this thread's cell on plane z, with the
+  // force F of the cell
+  auto lb_cell_F = [&](int z, T F[3]) {
+    if (!cell) return;
     const unsigned o = (unsigned)(z * nxy + rowy[1] + x);
     const unsigned n32 = (unsigned)d.n;
     T rho, u[3];
@@ -489,6 +503,14 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     else
       store_with_images<T, DIM, DIM>(U, d, x, y, z, u);
     if (z + 1 < z1) pull_next(z + 1);
+  };
+
+  // the same with F formed here from the stress of the plane (single plane)
+  auto lb_cell = [&](int z, int ps) {
+    if (!cell) return;
+    T F[3];
+    force_cell(ic, ps, ps, ps, F);
+    lb_cell_F(z, F);
   };
 
   if constexpr (DIM == 2) {
@@ -542,6 +564,27 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     // the first copy of the loop (plane z0 + 3) goes to the slot of Q(z0 - 1),
     // which the ring phase of plane z0 just above still reads
     __syncthreads();
+    // After the barrier of plane z, the warps without a tile cell form the
+    // force F(z) of the tile's cells into F slot z & 1, while the cell warps
+    // update plane z - 1 with F(z - 1), formed one plane earlier.  F(z) reads
+    // Pi(z - 1 .. z + 1), which the ring phase of plane z + 2 (the slot of
+    // Pi(z - 2)) leaves alone; F slot z & 1 held F(z - 2), which the cell
+    // warps read before the previous barrier.
+    T* sF = reinterpret_cast<T*>(smem + C::off_f);
+    constexpr int NT = FTX * FTY;
+    auto force_plane = [&](int z) {  // threads NT .. THREADS - 1
+      T* Fo = sF + (z & 1) * (C::f_slot / sizeof(T));
+      for (int k = tid - NT; k < NT; k += C::THREADS - NT) {
+        T F[3];
+        force_cell((k / FTX + 1) * RX1 + (k % FTX) + 1, pslot(z), pslot(z - 1), pslot(z + 1), F);
+        Fo[k] = F[0], Fo[NT + k] = F[1], Fo[2 * NT + k] = F[2];
+      }
+    };
+    auto cell_plane = [&](int z) {  // threads 0 .. NT - 1
+      const T* Fi = sF + (z & 1) * (C::f_slot / sizeof(T));
+      T F[3] = {Fi[ct], Fi[NT + ct], Fi[2 * NT + ct]};
+      lb_cell_F(z, F);
+    };
     for (int z = z0; z < z1; z++) {
       // Q(z+3) reuses the slot of Q(z-1), last read by the ring phase of
       // plane z, which every thread finished before the previous barrier
@@ -554,8 +597,13 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
         abort_block();
         return;
       }
-      lb_cell(z, pslot(z));
+      if (tid >= NT)
+        force_plane(z);
+      else if (z > z0)
+        cell_plane(z - 1);
     }
+    __syncthreads();  // F(z1 - 1) is complete
+    if (tid < NT) cell_plane(z1 - 1);
   }
   (void)NPI;
 }
