@@ -61,8 +61,8 @@ def alg_bytes(precision):
 # on; reported as null once those sources change.
 NCU_TRAFFIC = {
     # 256 x 256 x 64 capture (4,194,304 cells), see profiles/
-    "fused_lb": ((421.175296e6 + 334.067712e6) / 4194304, "63ac9605e32f4fab"),
-    "fused_be": ((153.899008e6 + 61.059840e6) / 4194304, "63ac9605e32f4fab"),
+    "fused_lb": ((420.588544e6 + 333.293056e6) / 4194304, "7515a2e058462eef"),
+    "fused_be": ((153.839104e6 + 61.012736e6) / 4194304, "7515a2e058462eef"),
 }
 
 KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",
