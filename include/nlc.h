@@ -146,6 +146,10 @@ typedef struct nlc_ctx nlc_ctx;
  * allocates its device state (two copies of the q populations and of the 5 Q
  * components, plus work arrays).  The state starts at Q = 0, rho = rho0,
  * u = 0.  stream: a cudaStream_t (may be NULL).  *out is set on success.
+ * The fused kernels address the populations with 32-bit offsets when every
+ * lattice of the context has q nx ny nz < 2^32, else with 64-bit ones; the
+ * environment variable NLC_POP_INDEX64=1, read here, forces the 64-bit form
+ * (both give the same step bit for bit).
  * Errors: NLC_EINVAL (bad sizes or parameters, D2Q9 with nz != 1),
  * NLC_ENOMEM, NLC_ECUDA. */
 NLC_API nlc_status nlc_create(const nlc_grid* grid, const nlc_params* params,

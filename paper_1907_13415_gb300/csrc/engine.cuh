@@ -5,6 +5,7 @@
 #include <cmath>
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "adjoint.cuh"
@@ -172,6 +173,11 @@ class Engine final : public EngineBase {
       dev[i].u = I.u;
       dev[i].mrt = nullptr;
     }
+    ix32_ = true;
+    for (const InstHost<T, G>& I : inst_)
+      ix32_ = ix32_ && (uint64_t)Q * (uint64_t)I.d.n < (1ull << 32);
+    if (const char* w = std::getenv("NLC_POP_INDEX64"))
+      if (w[0] == '1') ix32_ = false;
     if ((s = alloc(&bad_, 1)) || (s = alloc(&derr_, 1)) || (s = alloc(&insts_dev_, (size_t)n)) ||
         (s = alloc(&qmaps_dev_, (size_t)2 * n)) || (s = alloc(&umaps_dev_, (size_t)n)))
       return s;
@@ -1009,7 +1015,7 @@ class Engine final : public EngineBase {
     const int a = cur_;
     const int e0 = mark();
     cudaError_t e = launch_fused_lb<Lat, T>(insts_dev_, qmaps_dev_, tiles_dev_, ntiles_, a,
-                                            derr_, st, any_mrt_, iso_);
+                                            derr_, st, any_mrt_, iso_, ix32_);
     if (e != cudaSuccess) {
       err = std::string("fused lb kernel: ") + cudaGetErrorString(e);
       return NLC_ECUDA;
@@ -1121,6 +1127,7 @@ class Engine final : public EngineBase {
   std::vector<bool> mrt_on_;              // per lattice: MRT collision
   bool any_mrt_ = false;
   bool iso_ = false;                      // isotropic stencils
+  bool ix32_ = false;                     // Q n < 2^32 on every lattice (pop_off)
   cudaEvent_t seg_ev_[5] = {};
   int graph_len_[2] = {0, 0};
 };

@@ -6,12 +6,19 @@
 // kernels are bound by instruction issue, so pairing independent lanes of
 // arithmetic frees issue slots for their loads, stores and index math.
 //
-// On the host (tests compile the physics for the CPU) the pairs fall back to
-// two scalar operations with the same rounding.
+// On the host (tests compile the physics for the CPU), and in device passes
+// for GPUs without the paired instructions, the pairs fall back to two
+// scalar operations with the same rounding.
 #pragma once
 #include <cuda_runtime.h>
 
 #include <cmath>
+
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+#define NLC_PAIRED_FP32 1
+#else
+#define NLC_PAIRED_FP32 0
+#endif
 
 namespace nlc {
 
@@ -19,7 +26,7 @@ __host__ __device__ __forceinline__ float2 pk(float a, float b) { return make_fl
 __host__ __device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
 
 __host__ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
-#ifdef __CUDA_ARCH__
+#if NLC_PAIRED_FP32
   return __ffma2_rn(a, b, c);
 #else
   return make_float2(std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y));
@@ -27,7 +34,7 @@ __host__ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
 }
 
 __host__ __device__ __forceinline__ float2 padd(float2 a, float2 b) {
-#ifdef __CUDA_ARCH__
+#if NLC_PAIRED_FP32
   return __fadd2_rn(a, b);
 #else
   return make_float2(a.x + b.x, a.y + b.y);
@@ -36,7 +43,7 @@ __host__ __device__ __forceinline__ float2 padd(float2 a, float2 b) {
 
 // a - b as one fused multiply-add, fma(b, -1, a), exact like a subtraction
 __host__ __device__ __forceinline__ float2 psub(float2 a, float2 b) {
-#ifdef __CUDA_ARCH__
+#if NLC_PAIRED_FP32
   return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
 #else
   return make_float2(a.x - b.x, a.y - b.y);
@@ -44,7 +51,7 @@ __host__ __device__ __forceinline__ float2 psub(float2 a, float2 b) {
 }
 
 __host__ __device__ __forceinline__ float2 pmul(float2 a, float2 b) {
-#ifdef __CUDA_ARCH__
+#if NLC_PAIRED_FP32
   return __fmul2_rn(a, b);
 #else
   return make_float2(a.x * b.x, a.y * b.y);

@@ -6,6 +6,9 @@
 // molecular field (Eq. 3), Pi the stress of Eq. 5 without P0, S the
 // co-rotational term of Eq. 1, G[a][b] = d_b u_a the velocity gradient.
 #pragma once
+#ifdef __CUDACC__
+#include "packed.cuh"
+#endif
 
 namespace nlc {
 
@@ -93,6 +96,27 @@ __host__ __device__ __forceinline__ void molecular_field(const T q[5], const T l
   h[4] = c1 * e + Ag * qq4 + p.K * lap[4];
 }
 
+// d_a Q : d_b Q over all nine entries of the full tensors, from the
+// derivatives A = d_a q, B = d_b q of the five stored components
+// (Qzz = -Qxx - Qyy makes the zz entry add A_0 B_0 + A_3 B_3 + A_0 B_3 + A_3 B_0,
+// and the off-diagonals count twice):  2 sum_k A_k B_k + A_0 B_3 + A_3 B_0.
+template <class T>
+__host__ __device__ __forceinline__ T grad_dot(const T A[5], const T B[5]) {
+  const T s = fma_(A[0], B[0], fma_(A[1], B[1], fma_(A[2], B[2], fma_(A[3], B[3], A[4] * B[4]))));
+  return fma_(T(2), s, fma_(A[0], B[3], A[3] * B[0]));
+}
+
+#ifdef __CUDACC__
+// FP32: the first four products on packed pairs of components (packed.cuh;
+// plain C++ builds of this file take the template above)
+__host__ __device__ __forceinline__ float grad_dot(const float A[5], const float B[5]) {
+  float2 s2 = pmul(pk(A[0], A[1]), pk(B[0], B[1]));
+  s2 = pfma(pk(A[2], A[3]), pk(B[2], B[3]), s2);
+  const float s = fma_(A[4], B[4], s2.x + s2.y);
+  return fma_(2.0f, s, fma_(A[0], B[3], A[3] * B[0]));
+}
+#endif
+
 // Eq. 5 without P0, with dF/d(d_b Q) = K d_b Q:
 //   Pi_ab = 2 xi Qt_ab (Q:H) - xi (H Qt)_ab - xi (Qt H)_ab
 //           - K d_a Q : d_b Q + (Q H)_ab - (H Q)_ab,      Qt = Q + I/3.
@@ -121,11 +145,7 @@ __host__ __device__ __forceinline__ void stress(const T q[5], const T h[5],
   for (int a = 0; a < DIM; a++)
 #pragma unroll
     for (int b = a; b < DIM; b++) {
-      // d_a Q : d_b Q over all nine entries (off-diagonals twice, zz included)
-      const T el = T(2) * fma_(dq[a][0], dq[b][0], dq[a][3] * dq[b][3]) +
-                   fma_(dq[a][0], dq[b][3], dq[a][3] * dq[b][0]) +
-                   T(2) * fma_(dq[a][1], dq[b][1],
-                               fma_(dq[a][2], dq[b][2], dq[a][4] * dq[b][4]));
+      const T el = grad_dot(dq[a], dq[b]);
       const T qt = Q[a][b] + (a == b ? T(1) / T(3) : T(0));
       const T sym = fma_(xqh, qt, fma_(-x23, H[a][b], -p.K * el));
       Pi[a][b] = fma_(-xm1, X[a][b], fma_(-xp1, X[b][a], sym));

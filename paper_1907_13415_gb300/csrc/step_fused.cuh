@@ -277,9 +277,22 @@ struct CellPops<Lat, float> {
   float2 gp[(Lat::Q - 1) / 2];
 };
 
+// Element offset i n + o of cell o in population plane i.  When every
+// lattice of the launch has Q n < 2^32 (IX32) the sum stays in 32 bits,
+// which saves the wide arithmetic on each of the Q loads and stores of a
+// cell; larger lattices take the 64-bit form.
+template <bool IX32>
+__device__ __forceinline__ size_t pop_off(int i, unsigned n, unsigned o) {
+  if constexpr (IX32)
+    return (unsigned)(i * n + o);
+  else
+    return (size_t)i * n + o;
+}
+
 // MRT: the multiple-relaxation-time collision (physics.cuh: collide_mrt);
-// a lattice of the launch without its own rates gets the BGK rates 1/tau
-template <class Lat, class T, class G, bool MRT, bool ISO>
+// a lattice of the launch without its own rates gets the BGK rates 1/tau.
+// IX32: population offsets in 32 bits (pop_off).
+template <class Lat, class T, class G, bool MRT, bool ISO, bool IX32>
 __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     k_fused_lb(const InstDev<T, G>* __restrict__ insts,
                const CUtensorMap* __restrict__ qmaps,
@@ -397,7 +410,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     auto ld = [&](int i) {
       const unsigned off = (unsigned)(plane[Lat::c(i, 2) + 1] + rowy[Lat::c(i, 1) + 1] +
                                       colx[Lat::c(i, 0) + 1]);
-      return T(__ldg(gin + (size_t)i * n32 + off));
+      return T(__ldg(gin + pop_off<IX32>(i, n32, off)));
     };
     if constexpr (kPacked) {
       gn.g0 = ld(0);
@@ -474,7 +487,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
       moments<Lat, T>(g, F, p, rho, u);
       collide_mrt<Lat, T>(g, rho, u, F, p, s_mrt);
 #pragma unroll
-      for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = G(g[i]);
+      for (int i = 0; i < Lat::Q; i++) gout[pop_off<IX32>(i, n32, o)] = G(g[i]);
     } else if constexpr (kPacked) {
       float g0 = gn.g0, drho;
       float2 gp[NP];
@@ -486,8 +499,8 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
 #pragma unroll
       for (int q = 0; q < NP; q++) {
         const int i = pair_first<Lat>(q);
-        gout[(size_t)i * n32 + o] = gp[q].x;
-        gout[(size_t)Lat::opp(i) * n32 + o] = gp[q].y;
+        gout[pop_off<IX32>(i, n32, o)] = gp[q].x;
+        gout[pop_off<IX32>(Lat::opp(i), n32, o)] = gp[q].y;
       }
     } else {
       T g[Lat::Q];
@@ -496,7 +509,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
       moments<Lat, T>(g, F, p, rho, u);
       collide_bgk<Lat, T>(g, rho, u, F, p);
 #pragma unroll
-      for (int i = 0; i < Lat::Q; i++) gout[(size_t)i * n32 + o] = G(g[i]);
+      for (int i = 0; i < Lat::Q; i++) gout[pop_off<IX32>(i, n32, o)] = G(g[i]);
     }
     if (tile_inner && (DIM == 2 || (z >= GHOST && z < d.nz - GHOST)))
       store_interior<T, DIM>(U, x, y, z, u);
@@ -994,28 +1007,39 @@ inline cudaError_t set_smem(K kernel, size_t bytes, unsigned long long* done_mas
   return e;
 }
 
-template <class Lat, class T, class G, bool MRT, bool ISO>
+template <class Lat, class T, class G, bool MRT, bool ISO, bool IX32>
 cudaError_t launch_fused_lb_as(const InstDev<T, G>* insts, const CUtensorMap* qmaps,
                                const TileRef* tiles, int ntiles, int cur, unsigned* err,
                                cudaStream_t st) {
   static unsigned long long configured = 0;
-  cudaError_t e = set_smem(k_fused_lb<Lat, T, G, MRT, ISO>, LbCfg<Lat, T>::bytes, &configured);
+  cudaError_t e =
+      set_smem(k_fused_lb<Lat, T, G, MRT, ISO, IX32>, LbCfg<Lat, T>::bytes, &configured);
   if (e != cudaSuccess) return e;
-  k_fused_lb<Lat, T, G, MRT, ISO><<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(
-      insts, qmaps, tiles, cur, err);
+  k_fused_lb<Lat, T, G, MRT, ISO, IX32>
+      <<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(insts, qmaps, tiles, cur,
+                                                                      err);
   return cudaGetLastError();
 }
 
-// mrt: MRT collision; iso: isotropic stencils
+// mrt: MRT collision; iso: isotropic stencils; ix32: every lattice of the
+// launch has Q n < 2^32 (32-bit population offsets, taken by the BGK
+// kernel with the standard stencils)
 template <class Lat, class T, class G>
 cudaError_t launch_fused_lb(const InstDev<T, G>* insts, const CUtensorMap* qmaps,
                             const TileRef* tiles, int ntiles, int cur, unsigned* err,
-                            cudaStream_t st, bool mrt, bool iso) {
+                            cudaStream_t st, bool mrt, bool iso, bool ix32) {
   if (iso)
-    return mrt ? launch_fused_lb_as<Lat, T, G, true, true>(insts, qmaps, tiles, ntiles, cur, err, st)
-               : launch_fused_lb_as<Lat, T, G, false, true>(insts, qmaps, tiles, ntiles, cur, err, st);
-  return mrt ? launch_fused_lb_as<Lat, T, G, true, false>(insts, qmaps, tiles, ntiles, cur, err, st)
-             : launch_fused_lb_as<Lat, T, G, false, false>(insts, qmaps, tiles, ntiles, cur, err, st);
+    return mrt ? launch_fused_lb_as<Lat, T, G, true, true, false>(insts, qmaps, tiles, ntiles,
+                                                                  cur, err, st)
+               : launch_fused_lb_as<Lat, T, G, false, true, false>(insts, qmaps, tiles, ntiles,
+                                                                   cur, err, st);
+  if (mrt)
+    return launch_fused_lb_as<Lat, T, G, true, false, false>(insts, qmaps, tiles, ntiles, cur,
+                                                             err, st);
+  return ix32 ? launch_fused_lb_as<Lat, T, G, false, false, true>(insts, qmaps, tiles, ntiles,
+                                                                  cur, err, st)
+              : launch_fused_lb_as<Lat, T, G, false, false, false>(insts, qmaps, tiles, ntiles,
+                                                                   cur, err, st);
 }
 
 template <class Lat, class T, class G, bool ISO>

@@ -175,3 +175,30 @@ def test_autotune_single_plane_keeps_the_state(monkeypatch):
     with pytest.raises(nlc.NlcError):
         nlc._check(sim.ctx, nlc.load().nlc_set_chunk(sim.ctx, 8, 2))
     sim.close()
+
+
+@pytest.mark.parametrize("lattice", ["D3Q19", "D2Q9"])
+@pytest.mark.parametrize("precision", ["NLC_FP32", "NLC_FP64", "NLC_FP32_QF64"])
+def test_population_offsets_in_32_and_64_bits_give_the_same_step(precision, lattice,
+                                                                monkeypatch):
+    """The fused lb kernel addresses populations with 32-bit offsets on
+    lattices with q n < 2^32 and with 64-bit ones above; NLC_POP_INDEX64=1
+    forces the 64-bit form, which must give the same step bit for bit."""
+    from paper_1907_13415_gb300 import nlc
+    prec = getattr(nlc, precision)
+    if lattice == "D3Q19":
+        w = droplet(seed=41)
+    else:
+        w = wl.disc_256().with_(shape=(1, 61, 70), size=14.0, noise=1e-3, seed=43)
+    got = []
+    for wide in ("0", "1"):
+        monkeypatch.setenv("NLC_POP_INDEX64", wide)
+        sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=prec,
+                             stream=stream())
+        sim.set_chunk(3 if lattice == "D3Q19" else 2, False)
+        sim.set_fields(w.initial_q5())
+        sim.step(6)
+        got.append(state(sim))
+        sim.close()
+    for a, b in zip(*got):
+        assert np.array_equal(a, b)
