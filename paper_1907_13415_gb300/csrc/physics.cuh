@@ -200,20 +200,22 @@ __host__ __device__ __forceinline__ void corotation(const T G[3][3], const T q[5
 // 2 xi div(u)/3 identically, so Tr(R) = 2 xi (G_xx + G_yy + G_zz)/3.
 // Inputs: q (5), its central first derivatives dq[g][k], its Laplacian
 // lap[k], u (3), G.
-// The same from the advection term adv[k] = u_g d_g Q_k already formed.
+// The same from the advection term already formed, adv[k] = u_g d_g Q_k
+// times -1/am (am = -1: adv itself; the fused kernel passes twice the term
+// with am = -1/2).
 template <class T>
 __host__ __device__ __forceinline__ void be_rhs_adv(const T q[5], const T adv[5],
                                            const T lap[5], const T G[3][3],
-                                           const Par<T>& p, T r[5]) {
+                                           const Par<T>& p, T r[5], T am = T(-1)) {
   T h[5], s[5];
   molecular_field(q, lap, p, h);
   corotation(G, q, p.hp, p.hm, p.x2, s);
   const T tr3 = p.x29 * (G[0][0] + G[1][1] + G[2][2]);
-  r[0] = fma_(p.Gamma, h[0], s[0] - adv[0]) - tr3;
-  r[1] = fma_(p.Gamma, h[1], s[1] - adv[1]);
-  r[2] = fma_(p.Gamma, h[2], s[2] - adv[2]);
-  r[3] = fma_(p.Gamma, h[3], s[3] - adv[3]) - tr3;
-  r[4] = fma_(p.Gamma, h[4], s[4] - adv[4]);
+  r[0] = fma_(p.Gamma, h[0], fma_(am, adv[0], s[0])) - tr3;
+  r[1] = fma_(p.Gamma, h[1], fma_(am, adv[1], s[1]));
+  r[2] = fma_(p.Gamma, h[2], fma_(am, adv[2], s[2]));
+  r[3] = fma_(p.Gamma, h[3], fma_(am, adv[3], s[3])) - tr3;
+  r[4] = fma_(p.Gamma, h[4], fma_(am, adv[4], s[4]));
 }
 
 template <class T, int DIM>

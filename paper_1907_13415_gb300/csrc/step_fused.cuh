@@ -657,28 +657,28 @@ struct BeCfg {
   static constexpr uint32_t u_tx = sizeof(T) * DIM * BA;
 };
 
-// u and G[a][b] = d_b u_a at box offset o (z neighbours from
-// the planes above and below)
+// u and G2[a][b] = 2 d_b u_a (plain differences, twice the central
+// difference) at box offset o (z neighbours from the planes above and
+// below); the caller halves the factors that multiply G2, which gives the
+// same products as the gradient with its halved coefficients, exactly
 template <class Lat, class T, bool ISO>
 __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
                                           const T* __restrict__ m,
                                           const T* __restrict__ pp, int o,
                                           T u[3], T G[3][3]) {
   constexpr int DIM = Lat::DIM;
-  const T half = T(0.5);
   // FP32: u_x and u_y as a packed pair
   constexpr int AP = (std::is_same<T, float>::value && !ISO) ? 2 : 0;
   if constexpr (AP == 2) {
     const float* F0 = c;
     const float* F1 = c + BA;
-    const float2 h2 = bc(0.5f);
-    const float2 gx = pmul(psub(pk(F0[o + 1], F1[o + 1]), pk(F0[o - 1], F1[o - 1])), h2);
-    const float2 gy = pmul(psub(pk(F0[o + BXW], F1[o + BXW]), pk(F0[o - BXW], F1[o - BXW])), h2);
+    const float2 gx = psub(pk(F0[o + 1], F1[o + 1]), pk(F0[o - 1], F1[o - 1]));
+    const float2 gy = psub(pk(F0[o + BXW], F1[o + BXW]), pk(F0[o - BXW], F1[o - BXW]));
     u[0] = F0[o], u[1] = F1[o];
     G[0][0] = gx.x, G[1][0] = gx.y;
     G[0][1] = gy.x, G[1][1] = gy.y;
     if (DIM == 3) {
-      const float2 gz = pmul(psub(pk(pp[o], pp[BA + o]), pk(m[o], m[BA + o])), h2);
+      const float2 gz = psub(pk(pp[o], pp[BA + o]), pk(m[o], m[BA + o]));
       G[0][2] = gz.x, G[1][2] = gz.y;
     } else {
       G[0][2] = G[1][2] = 0.0f;
@@ -695,16 +695,15 @@ __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
       T d2[3], unused;
       u[a] = c[oa];
       lattice_stencil<Lat, T>(at, u[a], d2, unused);
-      G[a][0] = d2[0] * half;
-      G[a][1] = d2[1] * half;
-      G[a][2] = d2[2] * half;
+      G[a][0] = d2[0];
+      G[a][1] = d2[1];
+      G[a][2] = d2[2];
     } else if (a < DIM) {
       const T* F = c + a * BA;
       u[a] = F[o];
-      G[a][0] = (F[o + 1] - F[o - 1]) * half;
-      G[a][1] = (F[o + BXW] - F[o - BXW]) * half;
-      G[a][2] = DIM == 3 ? ((pp + a * BA)[o] - (m + a * BA)[o]) * half
-                         : T(0);
+      G[a][0] = F[o + 1] - F[o - 1];
+      G[a][1] = F[o + BXW] - F[o - BXW];
+      G[a][2] = DIM == 3 ? (pp + a * BA)[o] - (m + a * BA)[o] : T(0);
     } else {
       u[a] = T(0);
       G[a][0] = G[a][1] = G[a][2] = T(0);
@@ -712,16 +711,17 @@ __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
   }
 }
 
-// Q, the advection u.grad Q and the Laplacian at offset o
-// of a plane array c (row stride row, component stride comp; z neighbours in
-// m and pp).  The differences are kept plain (twice the central difference)
-// and meet u/2: (u/2).(2 dQ) = u.dQ exactly.
+// Q, twice the advection, u.(2 dQ) = 2 u.grad Q, and the Laplacian at
+// offset o of a plane array c (row stride row, component stride comp; z
+// neighbours in m and pp).  The differences are kept plain (twice the
+// central difference); the caller takes the advection with the factor -1/2
+// (be_rhs_adv), which is exact.
 template <class Lat, class T, bool ISO>
 __device__ __forceinline__ void stencil_adv(const T* __restrict__ c, const T* __restrict__ m,
                                             const T* __restrict__ pp, int o, int row, int comp,
                                             const T u[3], T q[5], T adv[5], T lap[5]) {
   constexpr int DIM = Lat::DIM;
-  const T uh0 = u[0] * T(0.5), uh1 = u[1] * T(0.5), uh2 = u[2] * T(0.5);
+  const T uh0 = u[0], uh1 = u[1], uh2 = u[2];
   // FP32: components (0, 1) and (2, 3) as packed pairs (same operations in
   // the same order as the scalar form, lane by lane)
   constexpr int KP = (std::is_same<T, float>::value && !ISO) ? 4 : 0;
@@ -801,6 +801,13 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
   const InstDev<T, G>& I = insts[tile.inst];
   const Dims d = I.d;
   const Par<T> p = I.p;
+  // the factors of Eq. 1 that multiply the velocity gradient, halved: the
+  // gradient arrives doubled (box_ugrad)
+  Par<T> p2 = p;
+  p2.hp = p.hp * T(0.5);
+  p2.hm = p.hm * T(0.5);
+  p2.x2 = p.x2 * T(0.5);
+  p2.x29 = p.x29 * T(0.5);
   const Field<T> Qout = I.q[cur ^ 1];
   const int zoff = Qout.L.zoff;
   const CUtensorMap* qmap = &qmaps[2 * tile.inst + cur];
@@ -855,10 +862,19 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     T q[5], adv[5], lap[5], u[3], G[3][3], r[5];
     box_ugrad<Lat, T, ISO>(sU(su), sU(sum), sU(sup), o, u, G);
     stencil_adv<Lat, T, ISO>(sQ(sq), sQ(sqm), sQ(sqp), o, BXW, BA, u, q, adv, lap);
-    be_rhs_adv<T>(q, adv, lap, G, p, r);
+    be_rhs_adv<T>(q, adv, lap, G, p2, r, T(-0.5));
     T* qpo = sQP(spo);
+    if constexpr (std::is_same<T, float>::value) {
+      // components (0, 1) and (2, 3) as packed pairs
+      const float2 a = padd(pk(q[0], q[1]), pk(r[0], r[1]));
+      const float2 b = padd(pk(q[2], q[3]), pk(r[2], r[3]));
+      qpo[c] = a.x, qpo[A1 + c] = a.y;
+      qpo[2 * A1 + c] = b.x, qpo[3 * A1 + c] = b.y;
+      qpo[4 * A1 + c] = q[4] + r[4];
+    } else {
 #pragma unroll
-    for (int k = 0; k < 5; k++) qpo[k * A1 + c] = q[k] + r[k];
+      for (int k = 0; k < 5; k++) qpo[k * A1 + c] = q[k] + r[k];
+    }
   };
 
   // corrector threads: one tile cell each (on a single plane, of the tile
@@ -882,13 +898,28 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     T qp[5], adv[5], lap[5], u[3], G[3][3], r2[5];
     box_ugrad<Lat, T, ISO>(sU(su), sU(sum), sU(sup), o2, u, G);
     stencil_adv<Lat, T, ISO>(sQP(sp), sQP(spm), sQP(spp), ic, RX1, A1, u, qp, adv, lap);
-    be_rhs_adv<T>(qp, adv, lap, G, p, r2);
+    be_rhs_adv<T>(qp, adv, lap, G, p2, r2, T(-0.5));
     // Q^{n+1} = Q^n + [R(Q^n) + R(Q^P)]/2 = [Q^n + Q^P + R(Q^P)]/2, since
     // Q^P = Q^n + R(Q^n)
     const T* qn = sQ(sq);
     T out[5];
+    if constexpr (std::is_same<T, float>::value) {
+      // components (0, 1) and (2, 3) as packed pairs, lane by lane the
+      // same operations as the scalar form
+      const float2 h = bc(0.5f);
 #pragma unroll
-    for (int k = 0; k < 5; k++) out[k] = (qn[k * BA + o2] + qp[k] + r2[k]) * T(0.5);
+      for (int k = 0; k < 4; k += 2) {
+        const float2 v = pmul(padd(padd(pk(qn[k * BA + o2], qn[(k + 1) * BA + o2]),
+                                        pk(qp[k], qp[k + 1])),
+                                   pk(r2[k], r2[k + 1])),
+                              h);
+        out[k] = v.x, out[k + 1] = v.y;
+      }
+      out[4] = (qn[4 * BA + o2] + qp[4] + r2[4]) * 0.5f;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 5; k++) out[k] = (qn[k * BA + o2] + qp[k] + r2[k]) * T(0.5);
+    }
     store_with_images<T, 5, DIM>(Qout, d, x, y, z, out);
   };
 

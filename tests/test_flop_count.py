@@ -29,8 +29,8 @@ def step_flops(c, d=3):
     q_stencil = 5 * (d + (2 * d - 1) + 2)        # d differences, Laplacian adds + 1 FMA
     force = d * (d + (d - 1) + 1)                  # differences, adds, the 1/2
     lb = q_stencil + c["H"] + c["Pi_3d"] + force + c["moments_d3q19"] + c["bgk_d3q19"]
-    adv = 5 * (2 * (d - 1) + 1)                    # u/2 . (2 dQ): FMAs + 1 multiply
-    u_stencil = d * (2 * d) + d                    # differences and 1/2 of G, u/2
+    adv = 5 * (2 * (d - 1) + 1)                    # u . (2 dQ): FMAs + 1 multiply
+    u_stencil = d * d                              # differences (2 G, exact)
     rhs = q_stencil + adv + u_stencil + c["R_from_adv"]
     be = 2 * rhs + 5 + 5 * 3                       # Q^P = Q + R; [Q + Q^P + R(Q^P)]/2
     return lb, be
@@ -44,7 +44,7 @@ def test_operation_counts(tmp_path):
     assert 200 <= c["Pi_3d"] <= 260 and c["Pi_2d"] < c["Pi_3d"]
     assert 90 <= c["S"] <= 130
     # R from the advection term = H + S + the assembly with the projection
-    assert c["R_from_adv"] == c["H"] + c["S"] + 20
+    assert c["R_from_adv"] == c["H"] + c["S"] + 25
     # MRT costs two transforms of the non-conserved moments on top of BGK
     assert c["mrt_d3q19"] > 2.5 * c["bgk_d3q19"]
     lb, be = step_flops(c)
