@@ -123,6 +123,8 @@ __host__ __device__ __forceinline__ float grad_dot(const float A[5], const float
 // With X = Q H (so H Q = X^T, H Qt = X^T + H/3, Qt H = X + H/3):
 //   Pi_ab = 2 xi Qt_ab (Q:H) - (xi - 1) X_ab - (xi + 1) X_ba
 //           - (2 xi/3) H_ab - K d_a Q : d_b Q.
+// Q:H is the trace of X (Q, H symmetric), and on the diagonal the two X
+// terms combine to -2 xi X_aa.
 // dq[g][k]: d_g of stored component k.  Only a, b < DIM are produced.
 template <class T, int DIM>
 __host__ __device__ __forceinline__ void stress(const T q[5], const T h[5],
@@ -130,17 +132,16 @@ __host__ __device__ __forceinline__ void stress(const T q[5], const T h[5],
                                        T Pi[3][3]) {
   const T Q[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], -q[0] - q[3]}};
   const T H[3][3] = {{h[0], h[1], h[2]}, {h[1], h[3], h[4]}, {h[2], h[4], -h[0] - h[3]}};
-  // Q:H over all nine entries
-  const T qh = fma_(Q[0][0], H[0][0], fma_(Q[1][1], H[1][1], Q[2][2] * H[2][2])) +
-               T(2) * fma_(q[1], h[1], fma_(q[2], h[2], q[4] * h[4]));
   const T xm1 = p.xm1, xp1 = p.xp1, x23 = p.x23;
-  const T xqh = p.x2 * qh;
   T X[3][3];  // X = Q H
 #pragma unroll
   for (int a = 0; a < DIM; a++)
 #pragma unroll
     for (int b = 0; b < DIM; b++)
       X[a][b] = fma_(Q[a][0], H[0][b], fma_(Q[a][1], H[1][b], Q[a][2] * H[2][b]));
+  const T x22 = DIM == 3 ? X[2][2]
+                         : fma_(Q[2][0], H[0][2], fma_(Q[2][1], H[1][2], Q[2][2] * H[2][2]));
+  const T xqh = p.x2 * (X[0][0] + X[1][1] + x22);  // 2 xi Q:H
 #pragma unroll
   for (int a = 0; a < DIM; a++)
 #pragma unroll
@@ -148,8 +149,12 @@ __host__ __device__ __forceinline__ void stress(const T q[5], const T h[5],
       const T el = grad_dot(dq[a], dq[b]);
       const T qt = Q[a][b] + (a == b ? T(1) / T(3) : T(0));
       const T sym = fma_(xqh, qt, fma_(-x23, H[a][b], -p.K * el));
-      Pi[a][b] = fma_(-xm1, X[a][b], fma_(-xp1, X[b][a], sym));
-      if (b != a) Pi[b][a] = fma_(-xm1, X[b][a], fma_(-xp1, X[a][b], sym));
+      if (b == a) {
+        Pi[a][a] = fma_(-p.x2, X[a][a], sym);
+      } else {
+        Pi[a][b] = fma_(-xm1, X[a][b], fma_(-xp1, X[b][a], sym));
+        Pi[b][a] = fma_(-xm1, X[b][a], fma_(-xp1, X[a][b], sym));
+      }
     }
 }
 
