@@ -61,8 +61,8 @@ def alg_bytes(precision):
 # on; reported as null once those sources change.
 NCU_TRAFFIC = {
     # 256 x 256 x 64 capture (4,194,304 cells), see profiles/
-    "fused_lb": ((420.588544e6 + 333.293056e6) / 4194304, "7515a2e058462eef"),
-    "fused_be": ((153.839104e6 + 61.012736e6) / 4194304, "7515a2e058462eef"),
+    "fused_lb": ((420.533760e6 + 333.174272e6) / 4194304, "b8662062c8ca4142"),
+    "fused_be": ((153.880320e6 + 60.854528e6) / 4194304, "b8662062c8ca4142"),
 }
 
 KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",
