@@ -147,11 +147,53 @@ __global__ void __launch_bounds__(256) k_field_raw_in(const T* __restrict__ in, 
 // non-finite count, sum |u|^2, max |u| (last).
 constexpr int OBS_SLOTS = 9;
 
-// One cell's contributions to the observables: rho and u (float64, of
-// Eq. 6), the cell's Q, and nbad non-finite stored values found by the
-// caller.  Per-cell terms in the arithmetic type T of the state (float for
-// the FP32 engine, whose state carries no more digits); acc (float64) and
-// umax collect them.
+// Running sum of float32 terms as the unevaluated pair hi + lo: every
+// addition is made exact by Knuth's TwoSum, its rounding error collected in
+// lo, so a thread's sum over its cells keeps about 48 significant bits at
+// float32 speed (GB300 runs float64 arithmetic at a small fraction of its
+// float32 rate); the pair is read out in float64 for the block and grid
+// sums.
+struct AccFF {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float s = hi + v;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (v - bp);
+    hi = s;
+    lo += err;
+  }
+  // a b, exactly: the fused multiply-add gives the product's rounding error
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float pr = a * b;
+    const float e = fmaf(a, b, -pr);
+    add(pr);
+    lo += e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// plain float64 running sum (float64 state)
+struct AccD {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add_prod(double a, double b) { v += a * b; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
+template <class T>
+struct AccFor {
+  using type = AccD;
+};
+template <>
+struct AccFor<float> {
+  using type = AccFF;
+};
+
+// One cell's contributions to the observables: rho and u (of Eq. 6), the
+// cell's Q, and nbad non-finite stored values found by the caller.
+// Per-cell terms in the arithmetic type T of the state (float for the FP32
+// engine, whose state carries no more digits); acc (AccFor<T>: float-float
+// for float, float64 for double) and umax collect them.
 template <class T>
 struct ObsConst {
   T c2, c3, c4, kh, inv_sref;
@@ -167,20 +209,20 @@ struct ObsConst {
 // (The non-finite count is kept as an integer and the maximum of |u| in T,
 // where both are exact; GB300 runs float64 arithmetic at a small fraction of
 // its float32 rate.)
-template <class T>
+template <class T, class A>
 __device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x, int y, int z,
-                                         double r, const double u[3], int& nbad,
-                                         const ObsConst<T>& c, double acc[OBS_SLOTS - 1],
+                                         T r, const T u[3], int& nbad,
+                                         const ObsConst<T>& c, A acc[OBS_SLOTS - 1],
                                          T& umax) {
   T uu = T(0);
-  acc[0] += r;
+  acc[0].add(r);
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    acc[1 + a] += r * u[a];
-    uu += T(u[a]) * T(u[a]);
+    acc[1 + a].add_prod(r, u[a]);
+    uu += u[a] * u[a];
   }
   umax = fmax(umax, sqrt(uu));
-  acc[7] += (double)uu;
+  acc[7].add(uu);
   T q[5];
 #pragma unroll
   for (int k = 0; k < 5; k++) {
@@ -213,18 +255,18 @@ __device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x
     en += c.kh * (dv[0] * dv[0] + dv[3] * dv[3] + dzz * dzz +
                   T(2) * (dv[1] * dv[1] + dv[2] * dv[2] + dv[4] * dv[4]));
   }
-  acc[4] += (double)(sqrt(T(1.5) * tr2) * c.inv_sref);
-  acc[5] += (double)en;
+  acc[4].add(sqrt(T(1.5) * tr2) * c.inv_sref);
+  acc[5].add(en);
 }
 
 // per-block float64 partials of the accumulators into partial[block]
 // (slot 6, the non-finite count, from the integer count nbad)
-template <class T>
-__device__ __forceinline__ void obs_block_out(double acc[OBS_SLOTS - 1], int nbad, T umax,
+template <class T, class A>
+__device__ __forceinline__ void obs_block_out(const A acc[OBS_SLOTS - 1], int nbad, T umax,
                                               double* sh, double* __restrict__ partial) {
-  acc[6] = (double)nbad;
   double tot[OBS_SLOTS];
-  for (int k = 0; k < OBS_SLOTS - 1; k++) tot[k] = block_sum(acc[k], sh);
+  for (int k = 0; k < OBS_SLOTS - 1; k++)
+    tot[k] = block_sum(k == 6 ? (double)nbad : acc[k].value(), sh);
   tot[OBS_SLOTS - 1] = block_max((double)umax, sh);
   if (threadIdx.x == 0)
     for (int k = 0; k < OBS_SLOTS; k++) partial[blockIdx.x * OBS_SLOTS + k] = tot[k];
@@ -240,7 +282,7 @@ __global__ void __launch_bounds__(256) k_obs_partial(
     const double* __restrict__ rho, const double* __restrict__ u, Dims d,
     Par<T> p, double s_ref, double* __restrict__ partial) {
   __shared__ double sh[32];
-  double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0, 0};
+  typename AccFor<T>::type acc[OBS_SLOTS - 1];
   T umax = T(0);
   int nbad = 0;
   const ObsConst<T> c(p, s_ref);
@@ -250,8 +292,8 @@ __global__ void __launch_bounds__(256) k_obs_partial(
     decode(d, idx, x, y, z);
 #pragma unroll
     for (int i = 0; i < Lat::Q; i++) nbad += !isfinite((T)gpost[(int64_t)i * d.n + idx]);
-    const double uc[3] = {u[idx], u[d.n + idx], u[2 * d.n + idx]};
-    obs_cell<T>(Q, d, x, y, z, rho[idx], uc, nbad, c, acc, umax);
+    const T uc[3] = {(T)u[idx], (T)u[d.n + idx], (T)u[2 * d.n + idx]};
+    obs_cell(Q, d, x, y, z, (T)rho[idx], uc, nbad, c, acc, umax);
   }
   obs_block_out<T>(acc, nbad, umax, sh, partial);
 }
@@ -265,7 +307,7 @@ __global__ void __launch_bounds__(256) k_obs_state(
     Field<T> Q, const G* __restrict__ gin, const T* __restrict__ Pi, Dims d, Par<T> p,
     double s_ref, bool iso, double* __restrict__ partial) {
   __shared__ double sh[32];
-  double acc[OBS_SLOTS - 1] = {0, 0, 0, 0, 0, 0, 0, 0};
+  typename AccFor<T>::type acc[OBS_SLOTS - 1];
   T umax = T(0);
   int nbad = 0;
   const ObsConst<T> c(p, s_ref);
@@ -282,8 +324,7 @@ __global__ void __launch_bounds__(256) k_obs_state(
 #pragma unroll
     for (int i = 0; i < Lat::Q; i++) nbad += !isfinite(g[i]);
     moments<Lat, T>(g, F, p, rho, u);
-    const double uc[3] = {(double)u[0], (double)u[1], (double)u[2]};
-    obs_cell<T>(Q, d, x, y, z, (double)rho, uc, nbad, c, acc, umax);
+    obs_cell(Q, d, x, y, z, rho, u, nbad, c, acc, umax);
   }
   obs_block_out<T>(acc, nbad, umax, sh, partial);
 }
