@@ -665,7 +665,7 @@ template <class Lat, class T, bool ISO>
 __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
                                           const T* __restrict__ m,
                                           const T* __restrict__ pp, int o,
-                                          T u[3], T G[3][3]) {
+                                          T u[3], T G2[3][3]) {
   constexpr int DIM = Lat::DIM;
   // FP32: u_x and u_y as a packed pair
   constexpr int AP = (std::is_same<T, float>::value && !ISO) ? 2 : 0;
@@ -675,13 +675,13 @@ __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
     const float2 gx = psub(pk(F0[o + 1], F1[o + 1]), pk(F0[o - 1], F1[o - 1]));
     const float2 gy = psub(pk(F0[o + BXW], F1[o + BXW]), pk(F0[o - BXW], F1[o - BXW]));
     u[0] = F0[o], u[1] = F1[o];
-    G[0][0] = gx.x, G[1][0] = gx.y;
-    G[0][1] = gy.x, G[1][1] = gy.y;
+    G2[0][0] = gx.x, G2[1][0] = gx.y;
+    G2[0][1] = gy.x, G2[1][1] = gy.y;
     if (DIM == 3) {
       const float2 gz = psub(pk(pp[o], pp[BA + o]), pk(m[o], m[BA + o]));
-      G[0][2] = gz.x, G[1][2] = gz.y;
+      G2[0][2] = gz.x, G2[1][2] = gz.y;
     } else {
-      G[0][2] = G[1][2] = 0.0f;
+      G2[0][2] = G2[1][2] = 0.0f;
     }
   }
 #pragma unroll
@@ -695,18 +695,18 @@ __device__ __forceinline__ void box_ugrad(const T* __restrict__ c,
       T d2[3], unused;
       u[a] = c[oa];
       lattice_stencil<Lat, T>(at, u[a], d2, unused);
-      G[a][0] = d2[0];
-      G[a][1] = d2[1];
-      G[a][2] = d2[2];
+      G2[a][0] = d2[0];
+      G2[a][1] = d2[1];
+      G2[a][2] = d2[2];
     } else if (a < DIM) {
       const T* F = c + a * BA;
       u[a] = F[o];
-      G[a][0] = F[o + 1] - F[o - 1];
-      G[a][1] = F[o + BXW] - F[o - BXW];
-      G[a][2] = DIM == 3 ? (pp + a * BA)[o] - (m + a * BA)[o] : T(0);
+      G2[a][0] = F[o + 1] - F[o - 1];
+      G2[a][1] = F[o + BXW] - F[o - BXW];
+      G2[a][2] = DIM == 3 ? (pp + a * BA)[o] - (m + a * BA)[o] : T(0);
     } else {
       u[a] = T(0);
-      G[a][0] = G[a][1] = G[a][2] = T(0);
+      G2[a][0] = G2[a][1] = G2[a][2] = T(0);
     }
   }
 }
@@ -859,10 +859,10 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     int cx, cy, c;
     ring_cell(t, cx, cy, c);
     const int o = box_at(cx, cy);
-    T q[5], adv[5], lap[5], u[3], G[3][3], r[5];
-    box_ugrad<Lat, T, ISO>(sU(su), sU(sum), sU(sup), o, u, G);
+    T q[5], adv[5], lap[5], u[3], G2[3][3], r[5];
+    box_ugrad<Lat, T, ISO>(sU(su), sU(sum), sU(sup), o, u, G2);
     stencil_adv<Lat, T, ISO>(sQ(sq), sQ(sqm), sQ(sqp), o, BXW, BA, u, q, adv, lap);
-    be_rhs_adv<T>(q, adv, lap, G, p2, r, T(-0.5));
+    be_rhs_adv<T>(q, adv, lap, G2, p2, r, T(-0.5));
     T* qpo = sQP(spo);
     if constexpr (std::is_same<T, float>::value) {
       // components (0, 1) and (2, 3) as packed pairs
@@ -895,10 +895,10 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
   // Q^P slots are sq, su, sp (neighbouring planes in sum, sup, spm, spp)
   auto correct = [&](int z, int sq, int su, int sum, int sup, int sp, int spm, int spp) {
     if (!cell) return;
-    T qp[5], adv[5], lap[5], u[3], G[3][3], r2[5];
-    box_ugrad<Lat, T, ISO>(sU(su), sU(sum), sU(sup), o2, u, G);
+    T qp[5], adv[5], lap[5], u[3], G2[3][3], r2[5];
+    box_ugrad<Lat, T, ISO>(sU(su), sU(sum), sU(sup), o2, u, G2);
     stencil_adv<Lat, T, ISO>(sQP(sp), sQP(spm), sQP(spp), ic, RX1, A1, u, qp, adv, lap);
-    be_rhs_adv<T>(qp, adv, lap, G, p2, r2, T(-0.5));
+    be_rhs_adv<T>(qp, adv, lap, G2, p2, r2, T(-0.5));
     // Q^{n+1} = Q^n + [R(Q^n) + R(Q^P)]/2 = [Q^n + Q^P + R(Q^P)]/2, since
     // Q^P = Q^n + R(Q^n)
     const T* qn = sQ(sq);
