@@ -209,7 +209,7 @@ struct ObsConst {
 // (The non-finite count is kept as an integer and the maximum of |u| in T,
 // where both are exact; GB300 runs float64 arithmetic at a small fraction of
 // its float32 rate.)
-template <class T, class A>
+template <int DIM, class T, class A>
 __device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x, int y, int z,
                                          T r, const T u[3], int& nbad,
                                          const ObsConst<T>& c, A acc[OBS_SLOTS - 1],
@@ -223,34 +223,31 @@ __device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x
   }
   umax = fmax(umax, sqrt(uu));
   acc[7].add(uu);
+  // Q is stored padded with its periodic images (common.cuh), so the
+  // forward neighbours are plain offsets from the cell
+  const T* qc = Q.base + Q.off(0, x, y, z);
+  const int64_t cs = Q.L.comp;
   T q[5];
 #pragma unroll
   for (int k = 0; k < 5; k++) {
-    q[k] = Q.at(k, x, y, z);
+    q[k] = qc[k * cs];
     nbad += !isfinite(q[k]);
   }
   const T qzz = -q[0] - q[3];
   const T tr2 = q[0] * q[0] + q[3] * q[3] + qzz * qzz +
                 T(2) * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
-  // Tr Q^3 = Q_ab Q_bc Q_ca
-  const T Qm[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], qzz}};
-  T tr3 = T(0);
-#pragma unroll
-  for (int a = 0; a < 3; a++)
-#pragma unroll
-    for (int b = 0; b < 3; b++)
-#pragma unroll
-      for (int e = 0; e < 3; e++) tr3 += Qm[a][b] * Qm[b][e] * Qm[e][a];
+  // Tr Q^3 = 3 det Q for traceless Q (Cayley-Hamilton)
+  const T tr3 = T(3) * (q[0] * (q[3] * qzz - q[4] * q[4]) - q[1] * (q[1] * qzz - q[4] * q[2]) +
+                        q[2] * (q[1] * q[4] - q[3] * q[2]));
   T en = c.c2 * tr2 - c.c3 * tr3 + c.c4 * tr2 * tr2;
   // forward-difference gradient energy K/2 sum_g |Q(x+e_g) - Q(x)|^2
-  const int nb[3][3] = {{wrap_inc(x, d.nx), y, z},
-                        {x, wrap_inc(y, d.ny), z},
-                        {x, y, wrap_inc(z, d.nz)}};
+  const int64_t step[3] = {1, Q.L.nxp, Q.L.plane};
 #pragma unroll
-  for (int gdir = 0; gdir < 3; gdir++) {
+  for (int gdir = 0; gdir < DIM; gdir++) {
+    const T* qn = qc + step[gdir];
     T dv[5];
 #pragma unroll
-    for (int k = 0; k < 5; k++) dv[k] = Q.at(k, nb[gdir][0], nb[gdir][1], nb[gdir][2]) - q[k];
+    for (int k = 0; k < 5; k++) dv[k] = qn[k * cs] - q[k];
     const T dzz = -dv[0] - dv[3];
     en += c.kh * (dv[0] * dv[0] + dv[3] * dv[3] + dzz * dzz +
                   T(2) * (dv[1] * dv[1] + dv[2] * dv[2] + dv[4] * dv[4]));
@@ -293,7 +290,7 @@ __global__ void __launch_bounds__(256) k_obs_partial(
 #pragma unroll
     for (int i = 0; i < Lat::Q; i++) nbad += !isfinite((T)gpost[(int64_t)i * d.n + idx]);
     const T uc[3] = {(T)u[idx], (T)u[d.n + idx], (T)u[2 * d.n + idx]};
-    obs_cell(Q, d, x, y, z, (T)rho[idx], uc, nbad, c, acc, umax);
+    obs_cell<Lat::DIM>(Q, d, x, y, z, (T)rho[idx], uc, nbad, c, acc, umax);
   }
   obs_block_out<T>(acc, nbad, umax, sh, partial);
 }
@@ -324,7 +321,7 @@ __global__ void __launch_bounds__(256) k_obs_state(
 #pragma unroll
     for (int i = 0; i < Lat::Q; i++) nbad += !isfinite(g[i]);
     moments<Lat, T>(g, F, p, rho, u);
-    obs_cell(Q, d, x, y, z, rho, u, nbad, c, acc, umax);
+    obs_cell<Lat::DIM>(Q, d, x, y, z, rho, u, nbad, c, acc, umax);
   }
   obs_block_out<T>(acc, nbad, umax, sh, partial);
 }
