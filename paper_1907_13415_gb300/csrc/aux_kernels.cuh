@@ -206,14 +206,10 @@ struct ObsConst {
   }
 };
 
-// (The non-finite count is kept as an integer and the maximum of |u| in T,
-// where both are exact; GB300 runs float64 arithmetic at a small fraction of
-// its float32 rate.)
-template <int DIM, class T, class A>
-__device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x, int y, int z,
-                                         T r, const T u[3], int& nbad,
-                                         const ObsConst<T>& c, A acc[OBS_SLOTS - 1],
-                                         T& umax) {
+// The flow terms of one cell from rho and u of Eq. 6: mass (acc[0]),
+// momentum (acc[1..3]), |u|^2 (acc[7]) and the maximum of |u|.
+template <class T, class A>
+__device__ __forceinline__ void obs_u_terms(T r, const T u[3], A acc[OBS_SLOTS - 1], T& umax) {
   T uu = T(0);
   acc[0].add(r);
 #pragma unroll
@@ -223,10 +219,16 @@ __device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x
   }
   umax = fmax(umax, sqrt(uu));
   acc[7].add(uu);
-  // Q is stored padded with its periodic images (common.cuh), so the
-  // forward neighbours are plain offsets from the cell
-  const T* qc = Q.base + Q.off(0, x, y, z);
-  const int64_t cs = Q.L.comp;
+}
+
+// The Q terms of one cell: S/s_ref (acc[4]), the free energy of Eq. 2 with
+// its forward-difference gradient term (acc[5]) and the non-finite count.
+// qc: component 0 of the cell, component k at qc[k cs]; st[g]: offset of
+// the forward neighbour along axis g (DIM axes).
+template <int DIM, class T, class A>
+__device__ __forceinline__ void obs_q_terms(const T* qc, int64_t cs, const int64_t st[3],
+                                            const ObsConst<T>& c, A acc[OBS_SLOTS - 1],
+                                            int& nbad) {
   T q[5];
 #pragma unroll
   for (int k = 0; k < 5; k++) {
@@ -241,10 +243,9 @@ __device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x
                         q[2] * (q[1] * q[4] - q[3] * q[2]));
   T en = c.c2 * tr2 - c.c3 * tr3 + c.c4 * tr2 * tr2;
   // forward-difference gradient energy K/2 sum_g |Q(x+e_g) - Q(x)|^2
-  const int64_t step[3] = {1, Q.L.nxp, Q.L.plane};
 #pragma unroll
-  for (int gdir = 0; gdir < DIM; gdir++) {
-    const T* qn = qc + step[gdir];
+  for (int g = 0; g < DIM; g++) {
+    const T* qn = qc + st[g];
     T dv[5];
 #pragma unroll
     for (int k = 0; k < 5; k++) dv[k] = qn[k * cs] - q[k];
@@ -254,6 +255,21 @@ __device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x
   }
   acc[4].add(sqrt(T(1.5) * tr2) * c.inv_sref);
   acc[5].add(en);
+}
+
+// (The non-finite count is kept as an integer and the maximum of |u| in T,
+// where both are exact; GB300 runs float64 arithmetic at a small fraction of
+// its float32 rate.)
+template <int DIM, class T, class A>
+__device__ __forceinline__ void obs_cell(const Field<T>& Q, const Dims& d, int x, int y, int z,
+                                         T r, const T u[3], int& nbad,
+                                         const ObsConst<T>& c, A acc[OBS_SLOTS - 1],
+                                         T& umax) {
+  obs_u_terms(r, u, acc, umax);
+  // Q is stored padded with its periodic images (common.cuh), so the
+  // forward neighbours are plain offsets from the cell
+  const int64_t st[3] = {1, Q.L.nxp, Q.L.plane};
+  obs_q_terms<DIM>(Q.base + Q.off(0, x, y, z), Q.L.comp, st, c, acc, nbad);
 }
 
 // per-block float64 partials of the accumulators into partial[block]

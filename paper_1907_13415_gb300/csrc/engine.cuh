@@ -91,6 +91,11 @@ struct InstHost {
   double* fstage = nullptr;
   double* partial = nullptr;
   double* prof_partial = nullptr;
+  // observables by the fused lb kernel (k_fused_lb with OBS): this
+  // lattice's own tile list and one partial row per tile (+ the total)
+  TileRef* obs_tiles = nullptr;
+  int obs_ntiles = 0;
+  double* obs_part = nullptr;
   double* prof = nullptr;
   int obs_blocks = 1;
   // adjoint work arrays (dense [comp][n])
@@ -664,14 +669,42 @@ class Engine final : public EngineBase {
     const Dims& d = I.d;
     cudaStream_t st = args_.stream;
     const double s_ref = 1.0 / 3.0;
-    // stress of the current Q, then rho, u and the observables in one pass
-    k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[cur_], I.pi, I.d, I.p, iso_);
-    NLC_CK_LAUNCH("k_stress");
-    k_obs_state<Lat, T><<<I.obs_blocks, 256, 0, st>>>(I.q[cur_], I.g[cur_], I.pi, d, I.p, s_ref,
-                                                      iso_, I.partial);
-    NLC_CK_LAUNCH("k_obs_state");
-    k_obs_final<<<OBS_SLOTS, 256, 0, st>>>(I.partial, I.obs_blocks, I.partial + I.obs_blocks * OBS_SLOTS);
-    NLC_CK_LAUNCH("k_obs_final");
+    const double* total;
+    if (maps_ok_ && !iso_ && ix32_) {
+      // one pass of the fused lb kernel in its observing form over this
+      // lattice's tiles (the step's tile machinery, nothing stored)
+      if (!I.obs_tiles) {
+        std::vector<TileRef> tl;
+        append_tiles<Lat>(i, I.d, fused_tz<Lat>(I.d, 0), false, &tl);
+        if ((s = alloc(&I.obs_tiles, tl.size())) ||
+            (s = alloc(&I.obs_part, (tl.size() + 1) * OBS_SLOTS)))
+          return s;
+        NLC_CK(cudaMemcpyAsync(I.obs_tiles, tl.data(), sizeof(TileRef) * tl.size(),
+                               cudaMemcpyHostToDevice, st));
+        I.obs_ntiles = (int)tl.size();
+      }
+      cudaError_t e = launch_fused_obs<Lat, T>(insts_dev_, qmaps_dev_, I.obs_tiles, I.obs_ntiles,
+                                               cur_, derr_, I.obs_part, st);
+      if (e != cudaSuccess) {
+        err = std::string("fused observables kernel: ") + cudaGetErrorString(e);
+        return NLC_ECUDA;
+      }
+      k_obs_final<<<OBS_SLOTS, 256, 0, st>>>(I.obs_part, I.obs_ntiles,
+                                             I.obs_part + (int64_t)I.obs_ntiles * OBS_SLOTS);
+      NLC_CK_LAUNCH("k_obs_final");
+      total = I.obs_part + (int64_t)I.obs_ntiles * OBS_SLOTS;
+    } else {
+      // stress of the current Q, then rho, u and the observables in one pass
+      k_stress<Lat, T><<<grid1(n), 256, 0, st>>>(I.q[cur_], I.pi, I.d, I.p, iso_);
+      NLC_CK_LAUNCH("k_stress");
+      k_obs_state<Lat, T><<<I.obs_blocks, 256, 0, st>>>(I.q[cur_], I.g[cur_], I.pi, d, I.p,
+                                                        s_ref, iso_, I.partial);
+      NLC_CK_LAUNCH("k_obs_state");
+      k_obs_final<<<OBS_SLOTS, 256, 0, st>>>(I.partial, I.obs_blocks,
+                                             I.partial + I.obs_blocks * OBS_SLOTS);
+      NLC_CK_LAUNCH("k_obs_final");
+      total = I.partial + I.obs_blocks * OBS_SLOTS;
+    }
     const int64_t rows = (int64_t)d.ny * d.nz;
     const int rows_per_chunk = profile_rows_per_chunk(d);
     const int nchunks = (int)((rows + rows_per_chunk - 1) / rows_per_chunk);
@@ -682,8 +715,7 @@ class Engine final : public EngineBase {
     NLC_CK_LAUNCH("k_profile_final");
     double tot[OBS_SLOTS];
     std::vector<double> prof(d.nx);
-    NLC_CK(cudaMemcpyAsync(tot, I.partial + I.obs_blocks * OBS_SLOTS, sizeof(tot),
-                           cudaMemcpyDeviceToHost, st));
+    NLC_CK(cudaMemcpyAsync(tot, total, sizeof(tot), cudaMemcpyDeviceToHost, st));
     NLC_CK(cudaMemcpyAsync(prof.data(), I.prof, sizeof(double) * d.nx, cudaMemcpyDeviceToHost, st));
     NLC_CK(cudaStreamSynchronize(st));
     if ((s = device_error())) return s;

@@ -33,6 +33,7 @@
 // of plane z.  FP32 runs the collision on packed pairs of opposite
 // populations (packed.cuh).
 #pragma once
+#include "aux_kernels.cuh"
 #include "chunks.h"
 #include "common.cuh"
 #include "lattice.cuh"
@@ -292,12 +293,16 @@ __device__ __forceinline__ size_t pop_off(int i, unsigned n, unsigned o) {
 // MRT: the multiple-relaxation-time collision (physics.cuh: collide_mrt);
 // a lattice of the launch without its own rates gets the BGK rates 1/tau.
 // IX32: population offsets in 32 bits (pop_off).
-template <class Lat, class T, class G, bool MRT, bool ISO, bool IX32>
+// OBS: instead of a step, the observables of the current state (the terms
+// of aux_kernels.cuh: rho and u of Eq. 6 in the cell phase, the Q terms of
+// the tile's cells in the ring phase), summed per block into
+// obs_partial[block][OBS_SLOTS]; nothing is stored.
+template <class Lat, class T, class G, bool MRT, bool ISO, bool IX32, bool OBS = false>
 __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     k_fused_lb(const InstDev<T, G>* __restrict__ insts,
                const CUtensorMap* __restrict__ qmaps,
                const TileRef* __restrict__ tiles, int cur,
-               unsigned* __restrict__ err) {
+               unsigned* __restrict__ err, double* __restrict__ obs_partial) {
   using C = LbCfg<Lat, T>;
   constexpr int DIM = Lat::DIM;
   constexpr int NPI = C::NPI;
@@ -392,6 +397,25 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
   const int nxy = d.nx * d.ny;
   const int ic = (ty + 1) * RX1 + (tx + 1);
 
+  // OBS: running sums of this thread (float-float for FP32), the
+  // non-finite count and the maximum of |u|
+  typename AccFor<T>::type oacc[OBS_SLOTS - 1];
+  int onbad = 0;
+  T oumax = T(0);
+  const ObsConst<T> oconst(p, 1.0 / 3.0);
+  // OBS: the Q terms of the tile cell (if any) of ring-phase thread t on
+  // plane zr (rows from yt0), whose Q box is in sq, the plane above in sqp
+  auto obs_ring = [&](int t, int zr, int yt0, const T* sq, const T* sqp) {
+    int cx, cy, c;
+    ring_cell(t, cx, cy, c);
+    if (cx < 0 || cx >= FTX || cy < 0 || cy >= FTY || x0 + cx >= d.nx || yt0 + cy >= d.ny ||
+        zr < z0 || zr >= z1)
+      return;
+    const T* qc = sq + box_at(cx, cy);
+    const int64_t st[3] = {1, BXW, (int64_t)(sqp - sq)};
+    obs_q_terms<DIM>(qc, (int64_t)BA, st, oconst, oacc, onbad);
+  };
+
   // The populations of the next plane are pulled into registers (gn) as
   // soon as the current plane is done, so their loads are in flight while
   // the block computes the next plane's stress.
@@ -468,6 +492,31 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
   // force F of the cell
   auto lb_cell_F = [&](int z, T F[3]) {
     if (!cell) return;
+    if constexpr (OBS) {
+      T rho, u[3];
+      if constexpr (kPacked) {
+        float g0 = gn.g0, drho;
+        float2 gp[NP];
+        onbad += !isfinite(g0);
+#pragma unroll
+        for (int q = 0; q < NP; q++) {
+          gp[q] = gn.gp[q];
+          onbad += !isfinite(gp[q].x) + !isfinite(gp[q].y);
+        }
+        moments_pairs<Lat>(g0, gp, F, p.rho0, rho, drho, u);
+      } else {
+        T g[Lat::Q];
+#pragma unroll
+        for (int i = 0; i < Lat::Q; i++) {
+          g[i] = gn.g[i];
+          onbad += !isfinite(g[i]);
+        }
+        moments<Lat, T>(g, F, p, rho, u);
+      }
+      obs_u_terms(rho, u, oacc, oumax);
+      if (z + 1 < z1) pull_next(z + 1);
+      return;
+    }
     const unsigned o = (unsigned)(z * nxy + rowy[1] + x);
     const unsigned n32 = (unsigned)d.n;
     T rho, u[3];
@@ -543,8 +592,10 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
       // thread finished before the previous barrier
       if (tid == 0 && t + 1 < nt) issue2(t + 1);
       late |= !mbar_wait(&bars[t & 1], (unsigned)(t >> 1) & 1u);
-      if (tid < C::RING_T)
+      if (tid < C::RING_T) {
         stress_ring_cell<Lat, T, ISO>(tid, sQ(t & 1), sQ(t & 1), sQ(t & 1), sP(t & 1), p);
+        if constexpr (OBS) obs_ring(tid, 0, y0 + FTY * t, sQ(t & 1), sQ(t & 1));
+      }
       if (__syncthreads_or(late)) {
         abort_block();
         return;
@@ -571,9 +622,11 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     }
     if (tid == 0) issue(z0 + 2);
     wait(z0 + 1);
-    if (tid < C::RING_T)
+    if (tid < C::RING_T) {
       stress_ring_cell<Lat, T, ISO>(tid, sQ(qslot(z0)), sQ(qslot(z0 - 1)), sQ(qslot(z0 + 1)),
                                sP(pslot(z0)), p);
+      if constexpr (OBS) obs_ring(tid, z0, y0, sQ(qslot(z0)), sQ(qslot(z0 + 1)));
+    }
     // the first copy of the loop (plane z0 + 3) goes to the slot of Q(z0 - 1),
     // which the ring phase of plane z0 just above still reads
     __syncthreads();
@@ -603,9 +656,11 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
       // plane z, which every thread finished before the previous barrier
       if (tid == 0 && z + 3 <= z1 + 1) issue(z + 3);
       wait(z + 2);
-      if (tid < C::RING_T)
+      if (tid < C::RING_T) {
         stress_ring_cell<Lat, T, ISO>(tid, sQ(qslot(z + 1)), sQ(qslot(z)), sQ(qslot(z + 2)),
                                  sP(pslot(z + 1)), p);
+        if constexpr (OBS) obs_ring(tid, z + 1, y0, sQ(qslot(z + 1)), sQ(qslot(z + 2)));
+      }
       if (__syncthreads_or(late)) {
         abort_block();
         return;
@@ -617,6 +672,10 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     }
     __syncthreads();  // F(z1 - 1) is complete
     if (tid < NT) cell_plane(z1 - 1);
+  }
+  if constexpr (OBS) {
+    __shared__ double s_obs[32];
+    obs_block_out<T>(oacc, onbad, oumax, s_obs, obs_partial);
   }
   (void)NPI;
 }
@@ -1048,7 +1107,24 @@ cudaError_t launch_fused_lb_as(const InstDev<T, G>* insts, const CUtensorMap* qm
   if (e != cudaSuccess) return e;
   k_fused_lb<Lat, T, G, MRT, ISO, IX32>
       <<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(insts, qmaps, tiles, cur,
-                                                                      err);
+                                                                      err, nullptr);
+  return cudaGetLastError();
+}
+
+// the observables of the current state (buffers cur) over the tiles given
+// (standard stencils, 32-bit population offsets): per-block partial sums
+// into partial[ntiles][OBS_SLOTS]
+template <class Lat, class T, class G>
+cudaError_t launch_fused_obs(const InstDev<T, G>* insts, const CUtensorMap* qmaps,
+                             const TileRef* tiles, int ntiles, int cur, unsigned* err,
+                             double* partial, cudaStream_t st) {
+  static unsigned long long configured = 0;
+  cudaError_t e = set_smem(k_fused_lb<Lat, T, G, false, false, true, true>, LbCfg<Lat, T>::bytes,
+                           &configured);
+  if (e != cudaSuccess) return e;
+  k_fused_lb<Lat, T, G, false, false, true, true>
+      <<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(insts, qmaps, tiles, cur,
+                                                                      err, partial);
   return cudaGetLastError();
 }
 
