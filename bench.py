@@ -401,31 +401,35 @@ def run_ours(args, w):
                for k, v in kt.items() if v[1]}
 
     # end to end through the public API with host buffers: upload Q from
-    # pinned host memory, one step, observables back to the host
+    # pinned host memory (float32 for a float32 state, nlc_set_fields_f32;
+    # float64 otherwise), one step, observables back to the host
     e2e = None
     if not args.no_e2e:
-        pinned = torch.empty(Q0.shape, dtype=torch.float64, pin_memory=True)
+        f32_in = args.precision == "fp32"
+        hdt = torch.float32 if f32_in else torch.float64
+        pinned = torch.empty(Q0.shape, dtype=hdt, pin_memory=True)
         pinned.numpy()[...] = Q0
         qhost = pinned.numpy()
+        upload = sim.set_fields_f32 if f32_in else sim.set_fields
         for _ in range(2):
-            sim.set_fields(qhost)
+            upload(qhost)
             sim.step(1)
             sim.observables()
         barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            sim.set_fields(qhost)
+            upload(qhost)
             sim.step(1)
             sim.observables()
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
         e2e = {"value": cells * args.e2e_steps * ws / e2e_s / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": int(Q0.nbytes),
+               "h2d_bytes_per_step": int(qhost.nbytes),
                "d2h_bytes_per_step": int(np.dtype(np.float64).itemsize * 8 + 32),
                "steps": args.e2e_steps,
-               "what": "nlc_set_fields(Q from pinned host) + nlc_step(1) + "
-                       "nlc_observables() per step"}
+               "what": ("nlc_set_fields_f32" if f32_in else "nlc_set_fields") +
+                       "(Q from pinned host) + nlc_step(1) + nlc_observables() per step"}
     nlc_chunk = sim.chunk()
     sim.close()
 

@@ -7,12 +7,13 @@
 
 namespace nlc {
 
-// Q from float64 input; populations to the pull-layout image of f^eq(rho, u):
-// the deviation stored at y for direction i is g^eq_i evaluated at y + c_i,
-// so that pulling reproduces f^eq at every cell.  Counts non-finite inputs.
-template <class Lat, class T, class G>
+// Q from float64 (or, QIn = float, float32) input; populations to the
+// pull-layout image of f^eq(rho, u): the deviation stored at y for
+// direction i is g^eq_i evaluated at y + c_i, so that pulling reproduces
+// f^eq at every cell.  Counts non-finite inputs.
+template <class Lat, class T, class G, class QIn = double>
 __global__ void __launch_bounds__(256) k_set_fields(
-    const double* __restrict__ q_in, const double* __restrict__ rho_in,
+    const QIn* __restrict__ q_in, const double* __restrict__ rho_in,
     const double* __restrict__ u_in, Field<T> Q, G* __restrict__ g,
     Dims d, double rho0, unsigned long long* __restrict__ bad) {
   int x, y, z;
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(256) k_set_fields(
   T qv[5];
 #pragma unroll
   for (int k = 0; k < 5; k++) {
-    const double v = q_in[k * d.n + idx];
+    const QIn v = q_in[k * d.n + idx];
     nbad += !isfinite(v);
     qv[k] = (T)v;
   }

@@ -448,13 +448,42 @@ class Engine final : public EngineBase {
   // Device-side address of a page-locked (pinned) host array, which the
   // kernels can read in place over the host link, or nullptr for any other
   // memory (pageable host memory goes through a staging copy instead).
-  static const double* mapped_host(const double* p) {
+  template <class V>
+  static const V* mapped_host(const V* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
-    return a.type == cudaMemoryTypeHost ? static_cast<const double*>(a.devicePointer) : nullptr;
+    return a.type == cudaMemoryTypeHost ? static_cast<const V*>(a.devicePointer) : nullptr;
+  }
+
+  // Q from float32 (pinned: read in place; else through the staging
+  // buffer), rho = rho0, u = 0
+  nlc_status set_fields_f32(int i, const float* Q5) override {
+    InstHost<T, G>& I = inst_[i];
+    nlc_status s;
+    if ((s = ensure_staging(I))) return s;
+    const int64_t n = I.d.n;
+    cudaStream_t st = args_.stream;
+    const float* qs = mapped_host(Q5);
+    if (!qs) {
+      float* stage = reinterpret_cast<float*>(I.stage);  // 9 n doubles >= 5 n floats
+      NLC_CK(cudaMemcpyAsync(stage, Q5, sizeof(float) * 5 * n, cudaMemcpyHostToDevice, st));
+      qs = stage;
+    }
+    NLC_CK(cudaMemsetAsync(bad_, 0, sizeof(unsigned long long), st));
+    k_set_fields<Lat, T, G, float><<<grid1(n), 256, 0, st>>>(
+        qs, nullptr, nullptr, I.q[cur_], I.g[cur_], I.d, args_.params[i].rho0, bad_);
+    NLC_CK_LAUNCH("k_set_fields");
+    unsigned long long nbad = 0;
+    NLC_CK(cudaMemcpyAsync(&nbad, bad_, sizeof(nbad), cudaMemcpyDeviceToHost, st));
+    NLC_CK(cudaStreamSynchronize(st));
+    if (nbad) {
+      err = "nlc_set_fields_f32: " + std::to_string(nbad) + " non-finite input values";
+      return NLC_EUNSTABLE;
+    }
+    return NLC_OK;
   }
 
   nlc_status set_fields(int i, const double* Q5, const double* rho,

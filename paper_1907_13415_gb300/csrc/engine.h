@@ -91,6 +91,8 @@ struct EngineBase {
   virtual nlc_status step(int64_t n, int schedule) = 0;
   virtual nlc_status set_fields(int inst, const double* Q5, const double* rho,
                                 const double* u) = 0;
+  // Q from float32, rho = rho0, u = 0
+  virtual nlc_status set_fields_f32(int inst, const float* Q5) = 0;
   virtual nlc_status get_fields(int inst, double* Q5, double* rho, double* u) = 0;
   virtual nlc_status get_populations(int inst, double* f) = 0;
   virtual nlc_status observables(int inst, nlc_obs* out, double* s_profile) = 0;

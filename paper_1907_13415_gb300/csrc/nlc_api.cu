@@ -293,6 +293,16 @@ nlc_status nlc_set_fields(nlc_ctx* ctx, int32_t inst, const double* Q5,
   return NLC_OK;
 }
 
+nlc_status nlc_set_fields_f32(nlc_ctx* ctx, int32_t inst, const float* Q5) {
+  if (!ctx) return NLC_EINVAL;
+  if (bad_inst(ctx, inst)) return fail(ctx, NLC_EINVAL, "instance out of range");
+  if (!Q5) return fail(ctx, NLC_EINVAL, "Q5 is NULL");
+  nlc_status st = ctx->eng->set_fields_f32(inst, Q5);
+  if (st != NLC_OK) return fail(ctx, st, ctx->eng->err);
+  ctx->steps[inst] = 0;
+  return NLC_OK;
+}
+
 nlc_status nlc_get_fields(nlc_ctx* ctx, int32_t inst, double* Q5, double* rho,
                           double* u) {
   if (!ctx) return NLC_EINVAL;

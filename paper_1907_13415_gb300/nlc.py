@@ -112,6 +112,7 @@ def load(build_if_missing=True):
         "nlc_get_chunk": ([P, I32, P], I32),
         "nlc_autotune": ([P, I32, ctypes.POINTER(nlc_tune)], I32),
         "nlc_set_fields": ([P, I32, P, P, P], I32),
+        "nlc_set_fields_f32": ([P, I32, P], I32),
         "nlc_get_fields": ([P, I32, P, P, P], I32),
         "nlc_get_populations": ([P, I32, P], I32),
         "nlc_step": ([P, I64], I32),
@@ -140,7 +141,7 @@ def load(build_if_missing=True):
 def exported_symbols():
     return ["nlc_create", "nlc_create_batch", "nlc_count", "nlc_set_graph", "nlc_set_check",
             "nlc_set_params", "nlc_set_mrt", "nlc_set_stencil",
-            "nlc_set_schedule", "nlc_set_fields",
+            "nlc_set_schedule", "nlc_set_fields", "nlc_set_fields_f32",
             "nlc_get_fields", "nlc_get_populations", "nlc_step",
             "nlc_observables", "nlc_last_error", "nlc_destroy",
             "nlc_lattice_velocities", "nlc_version", "nlc_set_timing",
@@ -157,6 +158,13 @@ def _check(ctx, status):
 
 def _ptr(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _f32(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {shape}, got {a.shape}")
+    return a
 
 
 def _f64(a, shape):
@@ -250,6 +258,10 @@ def nlc_autotune(ctx, trial_steps):
 
 def nlc_set_fields(ctx, inst, Q5, rho=None, u=None):
     _check(ctx, load().nlc_set_fields(ctx, inst, _ptr(Q5), _ptr(rho), _ptr(u)))
+
+
+def nlc_set_fields_f32(ctx, inst, Q5):
+    _check(ctx, load().nlc_set_fields_f32(ctx, inst, _ptr(Q5)))
 
 
 def nlc_get_fields(ctx, inst, Q5=None, rho=None, u=None):
@@ -389,6 +401,9 @@ class Batch:
         nlc_set_fields(self.ctx, i, _f64(Q5, (5,) + sh), _f64(rho, sh),
                        _f64(u, (3,) + sh))
 
+    def set_fields_f32(self, i, Q5):
+        nlc_set_fields_f32(self.ctx, i, _f32(Q5, (5,) + self.shapes[i]))
+
     def get_fields(self, i):
         sh = self.shapes[i]
         Q5, rho, u = np.empty((5,) + sh), np.empty(sh), np.empty((3,) + sh)
@@ -463,6 +478,11 @@ class Simulation:
         sh = self.shape
         nlc_set_fields(self.ctx, 0, _f64(Q5, (5,) + sh), _f64(rho, sh),
                        _f64(u, (3,) + sh))
+
+    def set_fields_f32(self, Q5):
+        """Q in float32 (a float32 array is passed as is, pinned memory
+        included), the fluid at rest with rho = rho0."""
+        nlc_set_fields_f32(self.ctx, 0, _f32(Q5, (5,) + self.shape))
 
     def get_fields(self):
         sh = self.shape

@@ -134,3 +134,38 @@ def test_pinned_host_inputs_are_read_in_place(precision):
     assert ei.value.status == -4
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "fp32", "fp32_qf64"])
+@pytest.mark.parametrize("pin", [False, True], ids=["pageable", "pinned"])
+def test_float32_q_input_equals_the_float64_entry(precision, pin):
+    """nlc_set_fields_f32 (Q in float32, rho0 and rest) gives the state that
+    nlc_set_fields gives for the same values in float64, bit for bit, also
+    after steps; a non-finite value is refused."""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    w = wl.sphere_256().with_(shape=(9, 12, 34), size=4.0, noise=1e-3, seed=57)
+    Q32 = w.initial_q5().astype(np.float32)
+    if pin:
+        t = torch.empty(Q32.shape, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = Q32
+        src = t.numpy()
+    else:
+        src = Q32
+    a, b = make(w, precision), make(w, precision)
+    a.set_fields(Q32.astype(np.float64))
+    b.set_fields_f32(src)
+    for x, y in zip(a.get_fields(), b.get_fields()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    a.step(3)
+    b.step(3)
+    assert np.array_equal(a.get_fields()[0], b.get_fields()[0])
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    bad = Q32.copy()
+    bad[4, 2, 3, 5] = np.inf
+    with pytest.raises(nlc.NlcError) as ei:
+        b.set_fields_f32(bad)
+    assert ei.value.status == -4
+    a.close()
+    b.close()
