@@ -280,12 +280,14 @@ NLC_API nlc_status nlc_autotune(nlc_ctx* ctx, int32_t trial_steps, nlc_tune* out
 NLC_API nlc_status nlc_set_fields(nlc_ctx* ctx, int32_t inst, const double* Q5,
                           const double* rho, const double* u);
 
-/* The same with Q given in float32 (same layout) and the fluid at rest with
- * rho = rho0 (the populations w_i rho0), for contexts whose state is
- * float32 (NLC_FP32): half the host bytes of nlc_set_fields.  The values are
- * stored as given; in a context with float64 Q they are widened exactly.
- * Synchronises the stream.  Errors: NLC_EINVAL (null Q5, inst out of
- * range), NLC_EUNSTABLE (a non-finite input value), NLC_ECUDA. */
+/* The same with Q given in float32 (same layout, caller-owned, pinned arrays
+ * read in place) and the fluid at rest with rho = rho0, the initial state of
+ * Sec. 2 (populations f_i^eq(rho0, 0) = w_i rho0), for contexts whose state
+ * is float32 (NLC_FP32): half the host bytes of nlc_set_fields.  The values
+ * are stored as given; in a context with float64 Q they are widened
+ * exactly.  The lattice's step counter restarts at 0.  Synchronises the
+ * stream.  Errors: NLC_EINVAL (null Q5, inst out of range), NLC_EUNSTABLE (a
+ * non-finite input value; the state is then undefined), NLC_ECUDA. */
 NLC_API nlc_status nlc_set_fields_f32(nlc_ctx* ctx, int32_t inst, const float* Q5);
 
 /* Copies the current Q, rho and u (u of Eq. 6, including F/2) to host
