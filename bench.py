@@ -61,8 +61,8 @@ def alg_bytes(precision):
 # on; reported as null once those sources change.
 NCU_TRAFFIC = {
     # 256 x 256 x 64 capture (4,194,304 cells), see profiles/
-    "fused_lb": ((421.122304e6 + 333.341696e6) / 4194304, "eea08e94377f3966"),
-    "fused_be": ((153.862144e6 + 60.773120e6) / 4194304, "eea08e94377f3966"),
+    "fused_lb": ((420.338688e6 + 333.701888e6) / 4194304, "f00c6583920b7b38"),
+    "fused_be": ((153.916672e6 + 60.967424e6) / 4194304, "f00c6583920b7b38"),
 }
 
 KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",

@@ -780,12 +780,12 @@ __device__ __forceinline__ void stencil_adv(const T* __restrict__ c, const T* __
                                             const T* __restrict__ pp, int o, int row, int comp,
                                             const T u[3], T q[5], T adv[5], T lap[5]) {
   constexpr int DIM = Lat::DIM;
-  const T uh0 = u[0], uh1 = u[1], uh2 = u[2];
+  const T u0 = u[0], u1 = u[1], u2 = u[2];
   // FP32: components (0, 1) and (2, 3) as packed pairs (same operations in
   // the same order as the scalar form, lane by lane)
   constexpr int KP = (std::is_same<T, float>::value && !ISO) ? 4 : 0;
   if constexpr (KP == 4) {
-    const float2 a0 = bc(uh0), a1 = bc(uh1), a2 = bc(uh2);
+    const float2 a0 = bc(u0), a1 = bc(u1), a2 = bc(u2);
 #pragma unroll
     for (int k = 0; k < 4; k += 2) {
       const float* F0 = c + k * comp;
@@ -818,8 +818,8 @@ __device__ __forceinline__ void stencil_adv(const T* __restrict__ c, const T* __
       T d2[3];
       q[k] = c[ok];
       lattice_stencil<Lat, T>(at, q[k], d2, lap[k]);
-      T a = fma_(uh0, d2[0], uh1 * d2[1]);
-      if (DIM == 3) a = fma_(uh2, d2[2], a);
+      T a = fma_(u0, d2[0], u1 * d2[1]);
+      if (DIM == 3) a = fma_(u2, d2[2], a);
       adv[k] = a;
       continue;
     }
@@ -828,12 +828,12 @@ __device__ __forceinline__ void stencil_adv(const T* __restrict__ c, const T* __
             xm = F[o - 1];
     const T yp = F[o + row], ym = F[o - row];
     q[k] = v;
-    T a = fma_(uh0, xp - xm, uh1 * (yp - ym));
+    T a = fma_(u0, xp - xm, u1 * (yp - ym));
     T zp = T(0), zm = T(0);
     if (DIM == 3) {
       zp = (pp + k * comp)[o];
       zm = (m + k * comp)[o];
-      a = fma_(uh2, zp - zm, a);
+      a = fma_(u2, zp - zm, a);
     }
     adv[k] = a;
     lap[k] = lap_points<T, DIM>(v, xp, xm, yp, ym, zp, zm);
