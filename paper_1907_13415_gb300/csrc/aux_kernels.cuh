@@ -150,13 +150,13 @@ constexpr int OBS_SLOTS = 9;
 
 // Running sum of float32 terms as the unevaluated pair hi + lo: every
 // addition is made exact by Knuth's TwoSum, its rounding error collected in
-// lo, so a thread's sum over its cells keeps about 48 significant bits at
-// float32 speed (GB300 runs float64 arithmetic at a small fraction of its
+// lo, so a thread's sum over its cells keeps roughly twice the float32
+// precision at float32 speed (GB300 runs float64 arithmetic at a small fraction of its
 // float32 rate); the pair is read out in float64 for the block and grid
 // sums.
 struct AccFF {
   float hi = 0.0f, lo = 0.0f;
-  __device__ __forceinline__ void add(float v) {
+  __host__ __device__ __forceinline__ void add(float v) {
     const float s = hi + v;
     const float bp = s - hi;
     const float err = (hi - (s - bp)) + (v - bp);
@@ -164,21 +164,21 @@ struct AccFF {
     lo += err;
   }
   // a b, exactly: the fused multiply-add gives the product's rounding error
-  __device__ __forceinline__ void add_prod(float a, float b) {
+  __host__ __device__ __forceinline__ void add_prod(float a, float b) {
     const float pr = a * b;
     const float e = fmaf(a, b, -pr);
     add(pr);
     lo += e;
   }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+  __host__ __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 // plain float64 running sum (float64 state)
 struct AccD {
   double v = 0.0;
-  __device__ __forceinline__ void add(double x) { v += x; }
-  __device__ __forceinline__ void add_prod(double a, double b) { v += a * b; }
-  __device__ __forceinline__ double value() const { return v; }
+  __host__ __device__ __forceinline__ void add(double x) { v += x; }
+  __host__ __device__ __forceinline__ void add_prod(double a, double b) { v += a * b; }
+  __host__ __device__ __forceinline__ double value() const { return v; }
 };
 
 template <class T>

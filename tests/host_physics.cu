@@ -13,6 +13,7 @@ inline std::complex<double> fma_(std::complex<double> a, std::complex<double> b,
 
 #include "../paper_1907_13415_gb300/csrc/lattice.cuh"
 #include "../paper_1907_13415_gb300/csrc/physics.cuh"
+#include "../paper_1907_13415_gb300/csrc/aux_kernels.cuh"
 
 using namespace nlc;
 
@@ -25,6 +26,20 @@ static Par<double> par(const double* p) {
 }
 
 extern "C" {
+// the float-float running sum of the observables over v[0..n) (and of the
+// products a_i b_i with add_prod), read out in float64
+double hp_accff_sum(const float* v, int n) {
+  AccFF a;
+  for (int i = 0; i < n; i++) a.add(v[i]);
+  return a.value();
+}
+double hp_accff_dot(const float* x, const float* y, int n) {
+  AccFF a;
+  for (int i = 0; i < n; i++) a.add_prod(x[i], y[i]);
+  return a.value();
+}
+// the FP32 gradient contraction of the stress (packed pairs)
+float hp_grad_dot_f32(const float* A5, const float* B5) { return grad_dot(A5, B5); }
 void hp_molecular_field(const double* q5, const double* lap5, const double* p, double* h5) {
   molecular_field<double>(q5, lap5, par(p), h5);
 }

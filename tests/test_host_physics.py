@@ -231,3 +231,55 @@ def test_pointwise_adjoints_dot_product(hp, k):
         lhs = ob @ jv
         rhs = ib @ v + pb[0] * vp[2] + pb[1] * vp[1] + pb[2] * vp[3]
         assert lhs == pytest.approx(rhs, rel=1e-11, abs=1e-13)
+
+
+def test_float_float_sums_of_the_observables_are_nearly_exact(hp):
+    """The observables' per-thread running sums (AccFF: Knuth's TwoSum on
+    float32, read out in float64) against the exact sum (math.fsum) of the
+    same float32 terms: within 2^-40 of the sum of magnitudes over a
+    million terms of mixed sign and magnitude (a thread of the observables
+    kernels sums tens of terms), where a plain float32 sum is off by three
+    orders more; products by add_prod likewise (exact float32 products in
+    float64)."""
+    import math
+    rng = np.random.default_rng(71)
+    n = 1 << 20
+    v = (rng.standard_normal(n) * 10.0 ** rng.integers(-4, 3, n)).astype(np.float32)
+    w = (1.0 + 1e-3 * rng.standard_normal(n)).astype(np.float32)
+    hp.hp_accff_sum.restype = ctypes.c_double
+    hp.hp_accff_sum.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    hp.hp_accff_dot.restype = ctypes.c_double
+    hp.hp_accff_dot.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    exact = math.fsum(v.astype(np.float64))
+    mag = float(np.abs(v.astype(np.float64)).sum())
+    got = hp.hp_accff_sum(P(v), n)
+    assert abs(got - exact) < 2.0 ** -40 * mag
+    naive = np.float32(0)
+    for x in v[:65536]:
+        naive += x
+    ex16 = math.fsum(v[:65536].astype(np.float64))
+    assert abs(float(naive) - ex16) > 1e3 * abs(hp.hp_accff_sum(P(v), 65536) - ex16)
+    prods = v.astype(np.float64) * w.astype(np.float64)  # exact in float64
+    exact_dot = math.fsum(prods)
+    got_dot = hp.hp_accff_dot(P(v), P(w), n)
+    assert abs(got_dot - exact_dot) < 2.0 ** -40 * float(np.abs(prods).sum())
+
+
+def test_fp32_gradient_contraction_is_the_full_tensor_contraction(hp):
+    """grad_dot in float32 (packed pairs) against d_a Q : d_b Q summed over
+    all nine entries of the full tensors in float64 (Qzz = -Qxx - Qyy)."""
+    hp.hp_grad_dot_f32.restype = ctypes.c_float
+    hp.hp_grad_dot_f32.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    rng = np.random.default_rng(73)
+
+    def full(q):
+        return np.array([[q[0], q[1], q[2]], [q[1], q[3], q[4]],
+                         [q[2], q[4], -q[0] - q[3]]])
+
+    for _ in range(200):
+        A = rng.standard_normal(5).astype(np.float32)
+        B = rng.standard_normal(5).astype(np.float32)
+        ref = float(np.sum(full(A.astype(np.float64)) * full(B.astype(np.float64))))
+        got = hp.hp_grad_dot_f32(P(A), P(B))
+        scale = float(np.sum(np.abs(full(A.astype(np.float64)) * full(B.astype(np.float64)))))
+        assert abs(got - ref) < 1e-6 * scale
