@@ -61,15 +61,18 @@ def alg_bytes(precision):
 # on; reported as null once those sources change.
 NCU_TRAFFIC = {
     # 256 x 256 x 64 capture (4,194,304 cells), see profiles/
-    "fused_lb": ((420.338688e6 + 333.701888e6) / 4194304, "f00c6583920b7b38"),
-    "fused_be": ((153.916672e6 + 60.967424e6) / 4194304, "f00c6583920b7b38"),
+    "fused_lb": ((420.338688e6 + 333.701888e6) / 4194304, "4b7fe77f9531ef39"),
+    "fused_be": ((153.916672e6 + 60.967424e6) / 4194304, "4b7fe77f9531ef39"),
 }
 
 KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",
                   "paper_1907_13415_gb300/csrc/physics.cuh",
                   "paper_1907_13415_gb300/csrc/step_unfused.cuh",
                   "paper_1907_13415_gb300/csrc/lattice.cuh",
-                  "paper_1907_13415_gb300/csrc/common.cuh"]
+                  "paper_1907_13415_gb300/csrc/common.cuh",
+                  "paper_1907_13415_gb300/csrc/packed.cuh",
+                  "paper_1907_13415_gb300/csrc/tma.cuh",
+                  "paper_1907_13415_gb300/csrc/aux_kernels.cuh"]
 
 
 def source_hash():
