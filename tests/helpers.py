@@ -5,6 +5,16 @@ from paper_1907_13415_gb300 import workloads as wl
 
 EPS32 = np.finfo(np.float32).eps  # 1.19e-7
 
+#: parameter sets of the parity tests.  At tau = 1 the BGK collision keeps
+#: nothing of the incoming populations ((1 - 1/tau) f = 0); tau = 0.8 and the
+#: paper's own set (Sec. 2: tau = 1.5, K = 0.04, Gamma = 0.34) exercise that
+#: part of the collision and of its adjoint.
+PARAM_SETS = {
+    "tau1": dict(wl.BASE_PARAMS),
+    "tau0.8": dict(wl.BASE_PARAMS, tau=0.8),
+    "paper": dict(wl.PAPER_PARAMS),
+}
+
 
 def fp32_tolerance(steps):
     """Normwise relative bound for FP32 storage and arithmetic against the

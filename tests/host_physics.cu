@@ -68,6 +68,46 @@ int hp_collide(int lattice, double* g, double rho, const double* u, const double
   collide_bgk<LatD3Q19, double>(g, rho, uu, FF, pp);
   return 19;
 }
+}  // extern "C"
+
+// the FP32 kernels' moments and BGK + source collision on packed opposite
+// pairs (packed.cuh) for deviations g in the library's velocity order
+// (rho0 = 1): g is replaced by the post-collision deviations, rho and u
+// (Eq. 6, with F/2) are returned in ru[0..3]
+template <class Lat>
+static void lb_pairs_f32(float* g, const float* F, const double* p, float* ru) {
+  constexpr int NP = (Lat::Q - 1) / 2;
+  Par<float> pf;
+  pf.A0 = float(p[0]); pf.K = float(p[1]); pf.gamma = float(p[2]); pf.Gamma = float(p[3]);
+  pf.xi = float(p[4]); pf.tau = float(p[5]); pf.rho0 = 1.0f;
+  derive(pf);
+  float g0 = g[0];
+  float2 gp[NP];
+  for (int q = 0; q < NP; q++) {
+    const int i = pair_first<Lat>(q);
+    gp[q] = make_float2(g[i], g[Lat::opp(i)]);
+  }
+  float rho, drho, u[3];
+  moments_pairs<Lat>(g0, gp, F, pf.rho0, rho, drho, u);
+  collide_bgk_pairs<Lat>(g0, gp, rho, drho, u, F, pf.inv_tau, pf.guo);
+  g[0] = g0;
+  for (int q = 0; q < NP; q++) {
+    const int i = pair_first<Lat>(q);
+    g[i] = gp[q].x;
+    g[Lat::opp(i)] = gp[q].y;
+  }
+  ru[0] = rho;
+  for (int a = 0; a < 3; a++) ru[1 + a] = u[a];
+}
+extern "C" {
+int hp_lb_pairs_f32(int lattice, float* g, const float* F, const double* p, float* ru) {
+  if (lattice == 0) {
+    lb_pairs_f32<LatD2Q9>(g, F, p, ru);
+    return 9;
+  }
+  lb_pairs_f32<LatD3Q19>(g, F, p, ru);
+  return 19;
+}
 // MRT collision with the source term on deviations g (rho0 = 1); a[k] are
 // the per-moment coefficients s_k / |v_k|^2 (filled here from rates s_k)
 int hp_collide_mrt(int lattice, double* g, double rho, const double* u, const double* F,

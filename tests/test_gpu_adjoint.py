@@ -13,6 +13,8 @@ import pytest
 
 from paper_1907_13415_gb300 import workloads as wl
 
+from helpers import PARAM_SETS
+
 pytestmark = pytest.mark.gpu
 
 LOSS = (7.5, 1.0, 50.0)  # target radius, w_radius, w_velocity
@@ -31,10 +33,10 @@ def stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def droplet(lattice, shape):
+def droplet(lattice, shape, pset="tau1"):
     base = wl.adjoint_disc_128() if lattice == wl.D2Q9 else wl.sphere_256()
     r = 0.25 * min(s for s in shape if s > 1)
-    p = dict(wl.BASE_PARAMS, gamma=2.70)
+    p = dict(PARAM_SETS[pset], gamma=2.70)
     return base.with_(shape=shape, size=r, noise=1e-4, seed=41, params=p,
                       director=(0.8, 0.6, 0.0))
 
@@ -66,11 +68,12 @@ def gpu_adjoint(w, steps, ckpt, precision):
     return g, obs
 
 
+@pytest.mark.parametrize("pset", ["tau1", "tau0.8", "paper"])
 @pytest.mark.parametrize("lattice,shape,steps,ckpt",
                          [(wl.D2Q9, (1, 32, 32), 60, 16),
                           (wl.D3Q19, (10, 12, 14), 20, 7)])
-def test_fp64_adjoint_matches_complex_step_oracle(orc_cs, lattice, shape, steps, ckpt):
-    w = droplet(lattice, shape)
+def test_fp64_adjoint_matches_complex_step_oracle(orc_cs, lattice, shape, steps, ckpt, pset):
+    w = droplet(lattice, shape, pset)
     g, obs = gpu_adjoint(w, steps, ckpt, precision=0)
     L, dg = oracle_loss_derivative(orc_cs, w, steps, dparam=2)
     assert g["loss"] == pytest.approx(L, rel=1e-10)
@@ -87,8 +90,9 @@ def test_fp64_adjoint_matches_complex_step_oracle(orc_cs, lattice, shape, steps,
         assert np.sum(g["dQ0"] * v) == pytest.approx(dv, rel=1e-8)
 
 
-def test_fp32_adjoint_matches_oracle_within_bound(orc_cs):
-    w = droplet(wl.D2Q9, (1, 32, 32))
+@pytest.mark.parametrize("pset", ["tau1", "paper"])
+def test_fp32_adjoint_matches_oracle_within_bound(orc_cs, pset):
+    w = droplet(wl.D2Q9, (1, 32, 32), pset)
     g, _ = gpu_adjoint(w, 60, 16, precision=1)
     for idx, key in ((2, "dgamma"), (1, "dK"), (3, "dGamma")):
         _, d = oracle_loss_derivative(orc_cs, w, 60, dparam=idx)

@@ -25,12 +25,13 @@ def stream():
 
 def sweep_members():
     """Uneven flat-interface lattices across gamma (the temperature-sweep
-    recipe at parity size)."""
+    recipe at parity size), each member with its own relaxation time (the
+    paper's tau = 1.5 among them, Sec. 2)."""
     out = []
-    for i, (lx, ly, g) in enumerate([(64, 8, 2.62), (40, 16, 2.70),
-                                     (97, 3, 2.75), (33, 9, 2.80),
-                                     (1, 1, 2.7)]):
-        p = dict(wl.BASE_PARAMS, gamma=g)
+    for i, (lx, ly, g, tau) in enumerate([(64, 8, 2.62, 1.0), (40, 16, 2.70, 1.5),
+                                          (97, 3, 2.75, 0.8), (33, 9, 2.80, 1.2),
+                                          (1, 1, 2.7, 1.5)]):
+        p = dict(wl.BASE_PARAMS, gamma=g, tau=tau)
         out.append(wl.Workload(f"m{i}", wl.D2Q9, (1, ly, lx), p, 0, "slab",
                                max(1, lx // 2), (0.2, 0.9, 0.1), 1e-3, 20 + i))
     return out
@@ -60,7 +61,7 @@ def test_batch_d3q19_fp64_matches_oracle(orc):
     base = wl.sphere_256()
     ws = [base.with_(shape=(9, 10, 33), size=3.5, noise=1e-3, seed=31),
           base.with_(shape=(5, 17, 20), size=3.0, noise=1e-3, seed=32,
-                     params=dict(base.params, gamma=2.68))]
+                     params=dict(base.params, gamma=2.68, tau=1.5))]
     b = nlc.Batch(wl.D3Q19, [w.shape for w in ws], [w.params for w in ws],
                   precision=nlc.NLC_FP64, stream=stream())
     for i, w in enumerate(ws):

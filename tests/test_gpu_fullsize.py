@@ -23,7 +23,7 @@ import pytest
 
 from paper_1907_13415_gb300 import workloads as wl
 
-from helpers import fp32_tolerance, perm_to_oracle
+from helpers import PARAM_SETS, fp32_tolerance, perm_to_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -60,10 +60,15 @@ def sample_cells(w, chunk_bounds):
     return cells
 
 
-def test_sampled_cells_match_oracle_at_full_size(orc):
+@pytest.mark.parametrize("pset", ["tau1", "paper"])
+def test_sampled_cells_match_oracle_at_full_size(orc, pset):
+    """With the workload's parameters (tau = 1) and with the paper's
+    (tau = 1.5, K = 0.04, Gamma = 0.34; Sec. 2), where the collision keeps
+    a third of the incoming populations."""
     import torch
     from paper_1907_13415_gb300 import nlc
     w = wl.sphere_256()
+    w = w.with_(params=dict(PARAM_SETS[pset], gamma=w.params["gamma"]))
     nz, ny, nx = w.shape
     sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
                          stream=torch.cuda.current_stream().cuda_stream)
@@ -137,12 +142,13 @@ def run_gpu_steps(w, steps, precision):
     return Q, f, obs
 
 
-@pytest.mark.parametrize("delta", [0.0, 0.005])
-def test_disc_256_fp32_matches_oracle_in_full(orc, delta):
+@pytest.mark.parametrize("delta,pset", [(0.0, "tau1"), (0.005, "tau1"), (0.0, "paper")])
+def test_disc_256_fp32_matches_oracle_in_full(orc, delta, pset):
     """The circular droplet (256^2 D2Q9, R = 32) at its full size in the FP32
     bulk form, every cell against the FP64 oracle, with the FP64 drift of
-    mass and radius."""
+    mass and radius (also with the paper's parameters, tau = 1.5)."""
     w = wl.disc_256(delta)
+    w = w.with_(params=dict(PARAM_SETS[pset], gamma=w.params["gamma"]))
     steps = 50
     Q, f, obs = run_gpu_steps(w, steps, precision=1)
     p = wl.param_vector(w.params)
@@ -188,15 +194,19 @@ def test_sweep_64_members_match_oracle(orc):
     b.close()
 
 
-def test_adjoint_workload_in_full_matches_central_differences():
+@pytest.mark.parametrize("pset", ["tau1", "paper"])
+def test_adjoint_workload_in_full_matches_central_differences(pset):
     """The adjoint workload at its full size (128^2 D2Q9 disc, 2000 steps,
     checkpoints every 100): the FP64 adjoint's dL/dgamma against central
     differences (h = 1e-6) of the FP64 forward run, and the FP32 adjoint
     within 2% of the FP64 one.  (The oracle's own derivative, by complex
-    step, is the check at smaller sizes.)"""
+    step, is the check at smaller sizes.)  Also with the paper's parameters
+    (tau = 1.5), where the adjoint of the collision carries a third of each
+    population's adjoint back."""
     import torch
     from paper_1907_13415_gb300 import nlc
     w = wl.adjoint_disc_128()
+    w = w.with_(params=dict(PARAM_SETS[pset], gamma=w.params["gamma"]))
     steps, ckpt, target = w.steps, w.extra["ckpt_every"], w.extra["target_radius"]
     st = torch.cuda.current_stream().cuda_stream
 

@@ -10,7 +10,7 @@ import pytest
 
 from paper_1907_13415_gb300 import workloads as wl
 
-from helpers import fp32_tolerance, perm_to_oracle, rel, run_gpu, run_oracle
+from helpers import PARAM_SETS, fp32_tolerance, perm_to_oracle, rel, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -31,18 +31,22 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def workload(lattice, shape, kind="slab"):
+def workload(lattice, shape, kind="slab", pset="tau1"):
     base = wl.flat_128x8() if lattice == wl.D2Q9 else wl.sphere_256()
     nz, ny, nx = shape
+    p = dict(PARAM_SETS[pset], gamma=base.params["gamma"])
     if kind == "slab":
         w = base.with_(lattice=lattice, shape=shape, geometry="slab",
                        size=max(1, nx // 2), director=(0.3, 0.9, 0.3),
-                       noise=1e-3, seed=7)
+                       noise=1e-3, seed=7, params=p)
     else:
         r = 0.3 * min(s for s in shape if s > 1) if max(shape) > 1 else 1
         w = base.with_(lattice=lattice, shape=shape, geometry="ball", size=r,
-                       director=(0.6, 0.0, 0.8), noise=1e-3, seed=8)
+                       director=(0.6, 0.0, 0.8), noise=1e-3, seed=8, params=p)
     return w
+
+
+PSETS = list(PARAM_SETS)
 
 
 def compare(orc, g, o, lattice, tol):
@@ -55,31 +59,34 @@ def compare(orc, g, o, lattice, tol):
     assert np.abs(g["u"] - o["u"]).max() < tol
 
 
+@pytest.mark.parametrize("pset", PSETS)
 @pytest.mark.parametrize("schedule", [0, 1], ids=["fused", "unfused"])
 @pytest.mark.parametrize("shape", D2_SHAPES, ids=lambda s: "x".join(map(str, s[::-1])))
-def test_d2q9_fp64_matches_oracle(orc, shape, schedule):
-    w = workload(wl.D2Q9, shape)
+def test_d2q9_fp64_matches_oracle(orc, shape, schedule, pset):
+    w = workload(wl.D2Q9, shape, pset=pset)
     steps = 60
     g = run_gpu(w, steps, precision=0, schedule=schedule)
     o = run_oracle(orc, w, steps)
     compare(orc, g, o, wl.D2Q9, FP64_TOL)
 
 
+@pytest.mark.parametrize("pset", PSETS)
 @pytest.mark.parametrize("schedule", [0, 1], ids=["fused", "unfused"])
 @pytest.mark.parametrize("shape", D3_SHAPES, ids=lambda s: "x".join(map(str, s[::-1])))
-def test_d3q19_fp64_matches_oracle(orc, shape, schedule):
-    w = workload(wl.D3Q19, shape, kind="ball")
+def test_d3q19_fp64_matches_oracle(orc, shape, schedule, pset):
+    w = workload(wl.D3Q19, shape, kind="ball", pset=pset)
     steps = 12
     g = run_gpu(w, steps, precision=0, schedule=schedule)
     o = run_oracle(orc, w, steps)
     compare(orc, g, o, wl.D3Q19, FP64_TOL)
 
 
+@pytest.mark.parametrize("pset", PSETS)
 @pytest.mark.parametrize("lattice,shape", [(wl.D2Q9, (1, 24, 64)),
                                            (wl.D2Q9, (1, 11, 37)),
                                            (wl.D3Q19, (20, 10, 40))])
-def test_fp32_matches_oracle_within_bound(orc, lattice, shape):
-    w = workload(lattice, shape, kind="ball")
+def test_fp32_matches_oracle_within_bound(orc, lattice, shape, pset):
+    w = workload(lattice, shape, kind="ball", pset=pset)
     steps = 40
     g = run_gpu(w, steps, precision=1)
     o = run_oracle(orc, w, steps)
@@ -89,9 +96,12 @@ def test_fp32_matches_oracle_within_bound(orc, lattice, shape):
     assert rel(g["f"], o["f"][perm]) < tol
 
 
-def test_flat_interface_2000_steps_fp64(orc):
-    """The flat-interface workload (128x8 D2Q9, 2000 steps, FP64) in full."""
+@pytest.mark.parametrize("pset", ["tau1", "paper"])
+def test_flat_interface_2000_steps_fp64(orc, pset):
+    """The flat-interface workload (128x8 D2Q9, 2000 steps, FP64) in full,
+    with its own parameters and with the paper's (Sec. 2)."""
     w = wl.flat_128x8()
+    w = w.with_(params=dict(PARAM_SETS[pset], gamma=w.params["gamma"]))
     g = run_gpu(w, w.steps, precision=0)
     o = run_oracle(orc, w, w.steps)
     compare(orc, g, o, wl.D2Q9, FP64_TOL)
@@ -99,10 +109,11 @@ def test_flat_interface_2000_steps_fp64(orc):
     assert rel(g["obs"]["s_profile"], o["obs"]["s_profile"]) < FP64_TOL
 
 
+@pytest.mark.parametrize("pset", ["tau1", "paper"])
 @pytest.mark.parametrize("lattice,shape", [(wl.D2Q9, (1, 40, 50)),
                                            (wl.D3Q19, (9, 10, 12))])
-def test_observables_match_oracle(orc, lattice, shape):
-    w = workload(lattice, shape, kind="ball")
+def test_observables_match_oracle(orc, lattice, shape, pset):
+    w = workload(lattice, shape, kind="ball", pset=pset)
     g = run_gpu(w, 30, precision=0)
     o = run_oracle(orc, w, 30)
     go, oo = g["obs"], o["obs"]
@@ -146,8 +157,9 @@ def test_nonfinite_input_is_rejected():
     sim.close()
 
 
-def test_fused_and_unfused_agree_fp32():
-    w = workload(wl.D3Q19, (20, 17, 45), kind="ball")
+@pytest.mark.parametrize("pset", ["tau1", "paper"])
+def test_fused_and_unfused_agree_fp32(pset):
+    w = workload(wl.D3Q19, (20, 17, 45), kind="ball", pset=pset)
     a = run_gpu(w, 10, precision=1, schedule=0)
     b = run_gpu(w, 10, precision=1, schedule=1)
     assert rel(a["Q"], b["Q"]) < 1e-6

@@ -31,6 +31,8 @@ def hp(tmp_path_factory):
     lib.hp_collide_mrt.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]
+    lib.hp_lb_pairs_f32.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]
     lib.hp_corotation.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                   ctypes.c_void_p]
     return lib
@@ -143,6 +145,52 @@ def test_collision_with_source(hp, orc, lattice):
         S = orc.guo_point(lattice, p[5], u, F)
         ref = f - (f - feq) / p[5] + S
         assert np.allclose(g + w, ref[perm], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+@pytest.mark.parametrize("tau", [0.8, 1.5, "random"])
+def test_packed_fp32_collision_matches_oracle(hp, orc, lattice, tau):
+    """The FP32 kernels' moments and collision on packed opposite pairs
+    (packed.cuh: moments_pairs, collide_bgk_pairs) against the oracle's
+    equilibrium and source term, f* = f - (f - feq)/tau + S_i with rho and u
+    of Eq. 6 (u with F/2), at tau != 1, where the (1 - 1/tau) f part of the
+    collision is not zero (tau = 1.5 is the paper's value, Sec. 2)."""
+    q = 9 if lattice == 0 else 19
+    d = 2 if lattice == 0 else 3
+    c = np.zeros((q, 3), dtype=np.int32)
+    w = np.zeros(q)
+    hp.hp_lattice(lattice, P(c), P(w))
+    rng = np.random.default_rng(21 + lattice)
+    worst = 0.0
+    for _ in range(40):
+        p = params(rng)
+        p[5] = rng.uniform(0.6, 2.0) if tau == "random" else tau
+        rho = 1 + 0.05 * rng.normal()
+        u0 = np.zeros(3)
+        u0[:d] = rng.normal(scale=0.05, size=d)
+        F = np.zeros(3)
+        F[:d] = rng.normal(scale=1e-3, size=d)
+        co, _ = orc.lattice(lattice)
+        perm = [int(np.where((co == cv).all(axis=1))[0][0]) for cv in c]
+        f = orc.equilibrium_point(lattice, rho, u0)[perm] + rng.normal(scale=2e-3, size=q)
+        g32 = (f - w).astype(np.float32)
+        f = g32.astype(np.float64) + w          # the FP32 input, exactly
+        F32 = F.astype(np.float32)
+        Fd = F32.astype(np.float64)
+        ru = np.zeros(4, dtype=np.float32)
+        hp.hp_lb_pairs_f32(lattice, P(g32), P(F32), P(p), P(ru))
+        rho_ref = f.sum()
+        u_ref = (c.T.astype(np.float64) @ f + Fd / 2) / rho_ref
+        feq = orc.equilibrium_point(lattice, rho_ref, u_ref)[perm]
+        S = orc.guo_point(lattice, p[5], u_ref, Fd)[perm]
+        ref = f - (f - feq) / p[5] + S
+        gref = ref - w
+        assert ru[0] == pytest.approx(rho_ref, rel=1e-6)
+        assert np.allclose(ru[1:], u_ref, rtol=0, atol=1e-6 * np.abs(u_ref).max())
+        err = np.abs(g32 - gref).max() / np.abs(gref).max()
+        worst = max(worst, err)
+    # a few float32 roundings of terms of the size of the deviations
+    assert worst < 2e-6
 
 
 @pytest.mark.parametrize("lattice", [0, 1])
