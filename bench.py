@@ -202,7 +202,7 @@ def whole_job_rate(cells_per_rank, steps, elapsed_ms, ws):
 
 def oracle_sample_rate(w, steps, shape=None):
     """Time the FP64 CPU oracle on a bounded sample of the workload.  Returns
-    (MLUPS, threads, description)."""
+    (MLUPS, threads, description, (f, Q) after the steps)."""
     import oracle
     from paper_1907_13415_gb300 import workloads as wl
     cores = os.cpu_count() or 1
@@ -214,12 +214,12 @@ def oracle_sample_rate(w, steps, shape=None):
     p = wl.param_vector(ws.params)
     threads = orc.set_threads(0)
     t0 = time.perf_counter()
-    orc.step(ws.lattice, p, f, Q, steps)
+    state = orc.step(ws.lattice, p, f, Q, steps)
     dt = time.perf_counter() - t0
     nz, ny, nx = ws.shape
     desc = (f"{steps} step(s) of the oracle on a {nx}x{ny}x{nz} D3Q19 lattice "
             f"with the droplet recipe, FP64, OpenMP")
-    return nx * ny * nz * steps / dt / 1e6, threads, desc
+    return nx * ny * nz * steps / dt / 1e6, threads, desc, state
 
 
 def oracle_single_thread_rate(w):
@@ -265,6 +265,62 @@ def baseline_shape(w):
     if mem_available_gb() > 2 * need_gb:
         return w.shape
     return (max(8, nz // 8), ny, nx)
+
+
+ACC_STEPS = 2  # steps of the accuracy comparison with the oracle
+ACC_HALF = 9   # half-width of the periodic box around a sampled cell
+
+
+def accuracy_full(orc, w, gpu, state):
+    """Normwise max |dQ| / max |Q| and max |df| / max |f| over the whole
+    lattice, and the drift of mass and radius, of the GPU state after
+    ACC_STEPS steps against the oracle's."""
+    from paper_1907_13415_gb300 import workloads as wl
+    Qg, fg, og, perm = gpu
+    fo, Qo = state
+    p = wl.param_vector(w.params)
+    oo = orc.observables(w.lattice, p, fo, Qo)
+    dq = float(np.abs(Qg - Qo).max() / np.abs(Qo).max())
+    df = float(np.abs(fg - fo[perm]).max() / np.abs(fo).max())
+    return {"steps": ACC_STEPS, "cells": "all",
+            "max_dQ_rel": dq, "max_df_rel": df,
+            "radius_gpu": og["radius"], "radius_oracle": float(oo["radius"]),
+            "radius_drift": abs(og["radius"] - float(oo["radius"])),
+            "mass_rel_drift": abs(og["mass"] - float(oo["mass"])) / float(oo["mass"]),
+            "max_u_gpu": og["max_u"], "max_u_oracle": float(oo["max_u"])}
+
+
+def accuracy_sampled(orc, w, Q0, gpu, ncells=12):
+    """The same on sampled cells when the host cannot hold the oracle's
+    full lattice: a cell's state after ACC_STEPS steps depends only on
+    inputs within 4 ACC_STEPS cells, so the oracle on a periodic box of
+    half-width ACC_HALF cut around the cell gives its exact result."""
+    from paper_1907_13415_gb300 import workloads as wl
+    Qg, fg, og, perm = gpu
+    nz, ny, nx = w.shape
+    c = (nx - 1) / 2.0
+    cells = []
+    for d in (np.array([1, 0, 0]), np.array([0, 1, 0]), np.array([0, 0, 1])):
+        for rad in (w.size - 1.0, w.size, w.size + 1.0, 0.5 * w.size):
+            q = np.rint(c + rad * d).astype(int)
+            cells.append((int(q[2]), int(q[1]), int(q[0])))
+    cells = cells[:ncells]
+    p = wl.param_vector(w.params)
+    box = 2 * ACC_HALF + 1
+    dq = df = 0.0
+    for (cz, cy, cx) in cells:
+        iz = np.arange(cz - ACC_HALF, cz + ACC_HALF + 1) % nz
+        iy = np.arange(cy - ACC_HALF, cy + ACC_HALF + 1) % ny
+        ix = np.arange(cx - ACC_HALF, cx + ACC_HALF + 1) % nx
+        Qb = Q0[:, iz][:, :, iy][:, :, :, ix].copy()
+        fo, Qo = orc.step(w.lattice, p, orc.init_equilibrium(w.lattice, (box,) * 3), Qb,
+                          ACC_STEPS)
+        h = ACC_HALF
+        dq = max(dq, float(np.abs(Qg[:, cz, cy, cx] - Qo[:, h, h, h]).max()))
+        df = max(df, float(np.abs(fg[:, cz, cy, cx] - fo[perm][:, h, h, h]).max()))
+    return {"steps": ACC_STEPS, "cells": f"{len(cells)} sampled (interface and bulk)",
+            "max_dQ_rel": dq / float(np.abs(Q0).max()),
+            "max_df_rel": df / float(np.abs(fg).max())}
 
 
 def workload_config(args, w, ws):
@@ -379,29 +435,46 @@ def run_ours(args, w):
     value, t_max = whole_job_rate(cells, args.steps, elapsed_ms, ws)
     launches = sum(n for _, n in kt.values())
 
-    # roofline of the dominant kernel
+    # roofline of the step (the pair of fused kernels that makes one time
+    # step): algorithmic bytes 2 (q + 5) words per lattice update over the
+    # device time of a step, against the measured HBM copy bandwidth; the
+    # per-kernel figures sit under "kernels"
     peak, peak_src = hbm_peak()
-    dom = max(kt, key=lambda k: kt[k][0])
-    dom_ms, dom_n = kt[dom]
-    per_launch_s = dom_ms / max(dom_n, 1) * 1e-3
     step_bytes, kern_bytes = alg_bytes(args.precision)
-    alg = kern_bytes.get(dom, step_bytes) * cells
-    achieved = alg / per_launch_s / 1e9
-    tr = NCU_TRAFFIC.get(dom)
-    # the ncu figures were taken on the FP32 default configuration
-    traffic = (tr[0] * cells if tr and tr[1] == source_hash() and args.precision == "fp32"
-               and not args.mrt else None)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "kernel": dom, "peak_source": peak_src,
-                "alg_bytes_per_lup": kern_bytes.get(dom, step_bytes)}
     step_s = t_max / args.steps * 1e-3
-    step_roofline = {"alg_bytes_per_lup": step_bytes,
-                     "achieved": step_bytes * cells / step_s / 1e9,
-                     "frac": step_bytes * cells / step_s / 1e9 / peak}
-    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
-                   "share": v[0] / max(sum(x[0] for x in kt.values()), 1e-30)}
-               for k, v in kt.items() if v[1]}
+    src_ok = source_hash()
+    ncu_ok = args.precision == "fp32" and not args.mrt
+    kernels = {}
+    ktot = max(sum(x[0] for x in kt.values()), 1e-30)
+    for k, (ms, n) in kt.items():
+        if not n:
+            continue
+        ab = kern_bytes.get(k)
+        ent = {"ms_per_launch": ms / n, "launches": n, "share": ms / ktot}
+        if ab is not None:
+            ach = ab * cells / (ms / n * 1e-3) / 1e9
+            ent.update({"alg_bytes_per_lup": ab, "achieved_gbs": ach, "frac": ach / peak})
+            tr = NCU_TRAFFIC.get(k)
+            if tr and tr[1] == src_ok and ncu_ok:
+                ent["ncu_bytes_per_lup"] = tr[0]
+                ent["ncu_gbs"] = tr[0] * cells / (ms / n * 1e-3) / 1e9
+                ent["ncu_frac"] = ent["ncu_gbs"] / peak
+        kernels[k] = ent
+    step_traffic = None
+    if ncu_ok and all(NCU_TRAFFIC.get(k, (0, ""))[1] == src_ok for k in kern_bytes):
+        step_traffic = sum(NCU_TRAFFIC[k][0] for k in kern_bytes) * cells
+    achieved = step_bytes * cells / step_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": step_traffic,
+                "kernel": "step (fused_lb + fused_be)", "peak_source": peak_src,
+                "alg_bytes_per_lup": step_bytes,
+                "numerator": (f"{step_bytes} B/LUP x {cells} cells (read + write of the "
+                              f"{Q3} populations and 5 Q components) / device time of "
+                              f"one step (ms_per_step)"),
+                "denominator": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src} copy bandwidth)",
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per LUP "
+                                   "of both kernels (256x256x64 capture) x cells"
+                                   if step_traffic else None)}
 
     # end to end through the public API with host buffers: upload Q from
     # pinned host memory (float32 for a float32 state, nlc_set_fields_f32;
@@ -433,18 +506,54 @@ def run_ours(args, w):
                "steps": args.e2e_steps,
                "what": ("nlc_set_fields_f32" if f32_in else "nlc_set_fields") +
                        "(Q from pinned host) + nlc_step(1) + nlc_observables() per step"}
+    # accuracy against the FP64 oracle, outside the timed region: the state
+    # ACC_STEPS steps after the initial fields, in the launch configuration
+    # timed above
+    gpu_state = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_accuracy:
+        sim.set_fields(Q0)
+        sim.step(ACC_STEPS)
+        Qg, _, _ = sim.get_fields()
+        fg = sim.get_populations()
+        og = sim.observables()
+        c_g, _ = nlc.nlc_lattice_velocities(w.lattice)
+        gpu_state = (Qg, fg, og, c_g)
     nlc_chunk = sim.chunk()
     sim.close()
 
     cpu = None
+    accuracy = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
         shape = baseline_shape(w)
-        rate, cores, desc = oracle_sample_rate(w, 1, shape)
+        # the timed oracle sample is ACC_STEPS steps, so that on the full
+        # lattice its result is also the accuracy reference
+        rate, cores, desc, state = oracle_sample_rate(w, ACC_STEPS, shape)
         rate1, desc1 = oracle_single_thread_rate(w)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": desc,
                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
                                  "sample": desc1}}
+        if gpu_state is not None:
+            orc = oracle.get()
+            c_o, _ = orc.lattice(w.lattice)
+            perm = [int(np.where((c_o == cv).all(axis=1))[0][0]) for cv in gpu_state[3]]
+            gpu = gpu_state[:3] + (perm,)
+            del gpu_state
+            if tuple(shape) == tuple(w.shape):
+                accuracy = accuracy_full(orc, w, gpu, state)
+            else:
+                accuracy = accuracy_sampled(orc, w, Q0, gpu)
+            accuracy["reference"] = "FP64 CPU oracle"
+        del state
+
+    # the other two figures the metric names, on their own workloads:
+    # adjoint/forward time (128^2 droplet, 2000 steps, checkpoints every 100)
+    # and the batched temperature sweep against sequential contexts
+    adjoint = sweep = None
+    if rank == 0 and ws == 1 and not args.no_extras:
+        adjoint = adjoint_figures(args)
+        sweep = sweep_figures(args)
 
     if rank == 0:
         nz, ny, nx = w.shape
@@ -456,8 +565,9 @@ def run_ours(args, w):
             "data": "synthetic",
             "config": workload_config(args, w, ws),
             "tuning": {"chunk": nlc_chunk[0], "taper": nlc_chunk[1], "autotune": tune},
-            "roofline": roofline, "step_roofline": step_roofline,
+            "roofline": roofline,
             "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "accuracy": accuracy, "adjoint": adjoint, "sweep": sweep,
             "gpu_launches": launches, "clocks": clocks,
             "kernel_source": source_hash(),
         }
@@ -468,11 +578,11 @@ def run_ours(args, w):
     return 0
 
 
-def run_sweep(args):
+def sweep_figures(args):
     """Batched temperature sweep: 64 flat-interface D2Q9 lattices of uneven
     extents (gamma over [2.60, 2.80]) advanced by the same launches and
     replayed as CUDA graphs, against the same lattices stepped one context
-    after another."""
+    after another.  Returns the figures as a dict."""
     import torch
     from paper_1907_13415_gb300 import nlc
     from paper_1907_13415_gb300 import workloads as wl
@@ -528,29 +638,39 @@ def run_sweep(args):
         s.close()
     v_b = cells * args.steps / (t_batch * 1e-3) / 1e6
     v_s = cells * args.steps / (t_seq * 1e-3) / 1e6
+    return {"workload": "sweep_64 flat interfaces, D2Q9, Lx in {256..2048}, "
+                        "Ly in {8,16,64}, gamma in [2.60, 2.80], FP32",
+            "instances": len(ws), "cells": cells, "steps": args.steps,
+            "graph_steps": args.graph_steps,
+            "batched": {"value": v_b, "unit": UNIT, "ms_per_step": t_batch / args.steps},
+            "sequential": {"value": v_s, "unit": UNIT, "ms_per_step": t_seq / args.steps,
+                           "launches_per_step": 2 * len(ws)},
+            "tuning": {"batched": tune_b, "chunk": args.chunk, "taper": args.taper},
+            "batched_over_sequential": t_seq / t_batch}
+
+
+def run_sweep(args):
+    f = sweep_figures(args)
     out = {"metric": "MLUPS, batched temperature sweep vs sequential contexts",
-           "value": v_b, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": t_batch / args.steps,
-           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "sweep_64 flat interfaces, D2Q9, "
-                                  "Lx in {256..2048}, Ly in {8,16,64}, "
-                                  "gamma in [2.60, 2.80]",
-                      "instances": len(ws), "cells": cells,
-                      "graph_steps": args.graph_steps},
-           "tuning": {"batched": tune_b, "chunk": args.chunk, "taper": args.taper},
-           "sequential": {"value": v_s, "unit": UNIT,
-                          "ms_per_step": t_seq / args.steps,
-                          "launches_per_step": 2 * len(ws)},
-           "batched_over_sequential": t_seq / t_batch}
+           "value": f["batched"]["value"], "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": f["batched"]["ms_per_step"], "higher_is_better": True,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f["workload"], "instances": f["instances"],
+                      "cells": f["cells"], "graph_steps": f["graph_steps"]},
+           "tuning": f["tuning"], "sequential": f["sequential"],
+           "batched_over_sequential": f["batched_over_sequential"]}
     print(json.dumps(out), flush=True)
     return 0
 
 
-def run_adjoint(args):
+def adjoint_figures(args):
     """Adjoint cost: the 128x128 D2Q9 droplet (R = 24, gamma = 2.70),
     2000 steps with checkpoints every 100, FP32.  Ratio of one nlc_adjoint
     call (its forward sweep, the recomputation and the reverse sweep) to one
-    plain forward run of the same steps."""
+    plain forward run of the same steps, and to the same forward run
+    replayed as CUDA graphs of ckpt_every steps (the library's fastest
+    forward).  Returns the figures as a dict."""
     import torch
     from paper_1907_13415_gb300 import nlc
     from paper_1907_13415_gb300 import workloads as wl
@@ -587,12 +707,21 @@ def run_adjoint(args):
     ta = min(r[0] for r in runs)
     g = runs[0][1]
     sim.close()
-    out = {"metric": "adjoint/forward time", "value": ta / tf, "unit": "ratio",
-           "higher_is_better": False, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": w.name, "steps": steps, "ckpt_every": ckpt},
-           "forward_s": tf, "adjoint_s": ta,
-           "forward_graph_s": tfg, "ratio_vs_graph_forward": ta / tfg,
-           "gradient": {k: g[k] for k in ("loss", "radius", "dgamma", "dK", "dGamma")}}
+    return {"workload": w.name, "steps": steps, "ckpt_every": ckpt, "dtype": "f32",
+            "forward_s": tf, "adjoint_s": ta, "forward_graph_s": tfg,
+            "ratio_vs_forward": ta / tf, "ratio_vs_graph_forward": ta / tfg,
+            "timer": "host wall clock around each call, stream synchronised, best of 3",
+            "gradient": {k: g[k] for k in ("loss", "radius", "dgamma", "dK", "dGamma")}}
+
+
+def run_adjoint(args):
+    f = adjoint_figures(args)
+    out = {"metric": "adjoint/forward time", "value": f["ratio_vs_forward"],
+           "unit": "ratio", "higher_is_better": False, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": f["workload"], "steps": f["steps"],
+                      "ckpt_every": f["ckpt_every"]}}
+    out.update({k: v for k, v in f.items() if k not in ("workload", "steps", "ckpt_every")})
     print(json.dumps(out), flush=True)
     return 0
 
@@ -606,6 +735,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the comparison with the oracle after the timed region")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint and batched-sweep figures of the default line")
     ap.add_argument("--shape", default=None,
                     help="nz,ny,nx of a smaller lattice with the same recipe "
                          "(profiling captures); the reported workload is "

@@ -224,6 +224,19 @@ NLC_API nlc_status nlc_set_params(nlc_ctx* ctx, int32_t inst, const nlc_params* 
  * and the step, when it finds any; 0 (default) never checks. */
 NLC_API nlc_status nlc_set_check(nlc_ctx* ctx, int32_t every);
 
+/* Budget, in nanoseconds of the GPU's global timer, of every wait at a
+ * grid-wide barrier of this context's persistent kernels (the segment
+ * kernels of nlc_adjoint; the paper has no counterpart: it is the failure
+ * detection of a kernel whose blocks wait on one another).  A wait that runs
+ * out makes the kernel record the fault and return, and the call that
+ * launched it fails with NLC_ETIMEOUT; the fault is cleared once reported
+ * and the context stays usable (its state is that of the last completed
+ * call, except for the adjoint's own work arrays).  ns < 0 restores the
+ * default, 200 ms; 0 makes any wait that does not find the barrier already
+ * complete run out (a test of the path).  Waits on tile copies inside the
+ * step kernels keep their own fixed 200 ms bound. */
+NLC_API nlc_status nlc_set_wait_budget(nlc_ctx* ctx, int64_t ns);
+
 /* Selects the kernel schedule (NLC_SCHED_*) for later nlc_step calls. */
 NLC_API nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule);
 
@@ -378,9 +391,12 @@ NLC_API nlc_status nlc_adjoint(nlc_ctx* ctx, const nlc_loss* loss, int64_t nstep
  * nx*ny*nz <= NLC_STATIC_MAX_CELLS, nx <= NLC_STATIC_MAX_NX and
  * (nx + 8)(ny + 4)(nz + 4) <= 262144 on D3Q19 ((nx + 8)(ny + 4) on D2Q9,
  * nx + 8 rounded up to a multiple of 4); larger lattices get NLC_EINVAL.
- * The first call on a device looks up that block's device address; make it
- * before any stream capture.  Calls share the block: calls that overlap on
- * the GPU race.  Queued on stream; synchronises it. */
+ * The first call on a device looks up that block's device address.  Queued
+ * on stream, and ends by copying the totals to the host and synchronising
+ * the stream: it cannot run inside a stream capture, and a capturing stream
+ * gets NLC_EINVAL.  A launch error left pending by earlier work of the
+ * calling thread is cleared on entry.  Calls share the block: calls that
+ * overlap on the GPU race. */
 #define NLC_STATIC_MAX_CELLS 65536
 #define NLC_STATIC_MAX_NX 4096
 NLC_API nlc_status nlc_observables_static(const nlc_grid* grid, const nlc_params* params,

@@ -12,8 +12,9 @@
 // barrier instead of a kernel boundary, so one launch replaces 4 (record) or
 // 5 (reverse) launches per step.  The kernels are launched cooperatively,
 // which guarantees that every block is resident, and each barrier wait is
-// bounded in wall-clock time like the mbarrier waits (tma.cuh): a wait that
-// runs out records DEV_ERR_GRID_TIMEOUT and the block returns.
+// bounded in wall-clock time by the context's wait budget (SegArgs::wait_ns,
+// nlc_set_wait_budget; 200 ms by default): a wait that runs out records
+// DEV_ERR_GRID_TIMEOUT and the block returns.
 //
 // Parameter adjoints are accumulated per thread in FP64 over all cells and
 // steps the thread handles (a fixed cell-to-thread map, so the order is
@@ -44,8 +45,10 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
 // its arrival with release semantics and polls the counter with acquire
 // semantics until every block of this generation has arrived (the counter
 // is cumulative: generation g completes at (g + 1) gridDim.x).  The poll is
-// bounded; returns false in every thread of the block if it ran out.
-__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen, unsigned* err) {
+// bounded by wait_ns nanoseconds of %globaltimer; returns false in every
+// thread of the block if it ran out.
+__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen, unsigned* err,
+                                          uint64_t wait_ns) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
@@ -54,7 +57,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen, unsigne
     if (ld_acquire_gpu(&b->arrived) < target) {
       const uint64_t t0 = global_ns();
       while (ld_acquire_gpu(&b->arrived) < target) {
-        if (global_ns() - t0 > kWaitNs) {
+        if (global_ns() - t0 > wait_ns) {
           ok = 0;
           atomicExch(err, DEV_ERR_GRID_TIMEOUT);
           break;
@@ -88,6 +91,7 @@ struct SegArgs {
   double* acc;  // [gridDim.x][3], added to
   GridBarrier* bar;
   unsigned* err;
+  uint64_t wait_ns;  // budget of each grid-barrier wait
 };
 
 template <class Lat, class T>
@@ -121,14 +125,14 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_record(SegArgs<T> a) {
   for (int j = 0; j < a.len; j++) {
     const Field<T> Q = S.q(j), U = S.u(j), QP = S.qp(j);
     NLC_FOR_CELLS(d) stress_at<Lat, T>(Q, S.pi(j), d, p, false, idx, x, y, z);
-    if (!grid_sync(a.bar, gen, a.err)) return;
+    if (!grid_sync(a.bar, gen, a.err, a.wait_ns)) return;
     NLC_FOR_CELLS(d)
     lb_at<Lat, T>(S.g(j), S.g(j + 1), S.pi(j), U, d, p, nullptr, false, idx, x, y, z);
-    if (!grid_sync(a.bar, gen, a.err)) return;
+    if (!grid_sync(a.bar, gen, a.err, a.wait_ns)) return;
     NLC_FOR_CELLS(d) predict_at<Lat, T>(Q, U, QP, a.r1, d, p, false, idx, x, y, z);
-    if (!grid_sync(a.bar, gen, a.err)) return;
+    if (!grid_sync(a.bar, gen, a.err, a.wait_ns)) return;
     NLC_FOR_CELLS(d) correct_at<Lat, T>(Q, QP, a.r1, U, S.q(j + 1), d, p, false, idx, x, y, z);
-    if (!grid_sync(a.bar, gen, a.err)) return;
+    if (!grid_sync(a.bar, gen, a.err, a.wait_ns)) return;
   }
 }
 
@@ -155,25 +159,25 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_reverse(SegArgs<T> a) {
       adj_be2_at<Lat, T>(QP, U, lQn, a.lQP, a.lUa, a.lGv, d, p, pb, idx, x, y, z);
       take(pb);
     }
-    if (!(ok = grid_sync(a.bar, gen, a.err))) break;
+    if (!(ok = grid_sync(a.bar, gen, a.err, a.wait_ns))) break;
     NLC_FOR_CELLS(d) {
       ParBar<T> pb{T(0), T(0), T(0)};
       adj_be1_at<Lat, T>(Q, U, lQn, a.lQP, lQo, a.lUa, a.lGv, d, p, pb, idx, x, y, z);
       take(pb);
     }
-    if (!(ok = grid_sync(a.bar, gen, a.err))) break;
+    if (!(ok = grid_sync(a.bar, gen, a.err, a.wait_ns))) break;
     NLC_FOR_CELLS(d)
     adj_lb_at<Lat, T>(S.g(j), S.pi(j), a.lG[lc], a.lUa, a.lGv, a.lG[lc ^ 1], a.lF, d, p,
                       T(0), idx, x, y, z);
-    if (!(ok = grid_sync(a.bar, gen, a.err))) break;
+    if (!(ok = grid_sync(a.bar, gen, a.err, a.wait_ns))) break;
     NLC_FOR_CELLS(d) {
       ParBar<T> pb{T(0), T(0), T(0)};
       adj_stress_at<Lat, T>(Q, a.lF, lQo, a.lDq, a.lLap, d, p, pb, idx, x, y, z);
       take(pb);
     }
-    if (!(ok = grid_sync(a.bar, gen, a.err))) break;
+    if (!(ok = grid_sync(a.bar, gen, a.err, a.wait_ns))) break;
     NLC_FOR_CELLS(d) adj_stencil_at<Lat, T>(a.lDq, a.lLap, lQo, d, idx, x, y, z);
-    if (!(ok = grid_sync(a.bar, gen, a.err))) break;
+    if (!(ok = grid_sync(a.bar, gen, a.err, a.wait_ns))) break;
     lc ^= 1;
   }
   if (!ok) return;

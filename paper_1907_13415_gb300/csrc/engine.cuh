@@ -12,6 +12,7 @@
 #include "adjoint_segment.cuh"
 #include "aux_kernels.cuh"
 #include "engine.h"
+#include "obs_finish.h"
 #include "step_fused.cuh"
 #include "step_unfused.cuh"
 
@@ -748,26 +749,7 @@ class Engine final : public EngineBase {
     NLC_CK(cudaMemcpyAsync(prof.data(), I.prof, sizeof(double) * d.nx, cudaMemcpyDeviceToHost, st));
     NLC_CK(cudaStreamSynchronize(st));
     if ((s = device_error())) return s;
-    out->mass = tot[0];
-    out->mom[0] = tot[1];
-    out->mom[1] = tot[2];
-    out->mom[2] = tot[3];
-    out->s_area = tot[4];
-    out->free_energy = tot[5];
-    out->nonfinite = (int64_t)tot[6];
-    out->u_l2 = std::sqrt(tot[7]);
-    out->max_u = tot[8];
-    out->radius = (DIM == 2 || d.nz == 1) ? std::sqrt(tot[4] / M_PI)
-                                          : std::cbrt(3.0 * tot[4] / (4.0 * M_PI));
-    const double half = s_ref / 2.0;
-    out->x_iface = -1.0;
-    for (int x = 0; x < d.nx; x++) {
-      const double a = prof[x], b = prof[(x + 1) % d.nx];
-      if (a >= half && b < half) {
-        out->x_iface = x + (a - half) / (a - b);
-        break;
-      }
-    }
+    obs_from_totals(tot, prof.data(), d.nx, DIM == 2 || d.nz == 1, s_ref, out);
     if (s_profile)
       for (int x = 0; x < d.nx; x++) s_profile[x] = prof[x];
     return NLC_OK;
@@ -799,15 +781,17 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
-  // device-side error word (bounded waits that ran out); read after a sync
+  // device-side error word (bounded waits that ran out); read after a
+  // sync, and cleared once reported, so that the context can run again
   nlc_status device_error() {
     unsigned e = 0;
     NLC_CK(cudaMemcpy(&e, derr_, sizeof(e), cudaMemcpyDeviceToHost));
     if (e != DEV_ERR_NONE) {
       err = e == DEV_ERR_GRID_TIMEOUT
-                ? "a bounded grid-barrier wait ran out inside an adjoint segment kernel"
+                ? "a bounded grid-barrier wait ran out inside a persistent kernel"
                 : "a bounded wait on a tile copy ran out inside a step kernel (code " +
                       std::to_string(e) + ")";
+      NLC_CK(cudaMemset(derr_, 0, sizeof(unsigned)));
       return NLC_ETIMEOUT;
     }
     return NLC_OK;
@@ -936,6 +920,7 @@ class Engine final : public EngineBase {
     a.lLap = I.lLap;
     a.acc = I.acc + (size_t)3 * 3 * grid1(I.d.n);
     a.err = derr_;
+    a.wait_ns = wait_ns;
     return a;
   }
 

@@ -72,6 +72,9 @@ struct EngineBase {
   virtual ~EngineBase() = default;
   KernelTimer timer;
   int graph_steps = 0;  // >0: whole chunks of this many steps replay a CUDA graph
+  // budget in nanoseconds of every grid-barrier wait of the persistent
+  // kernels (a wait that runs out ends the call with NLC_ETIMEOUT)
+  uint64_t wait_ns = 200ull * 1000 * 1000;
   virtual int count() const = 0;
   // number of non-finite stored values of each lattice (syncs); first bad
   // lattice in *bad (-1 if none)

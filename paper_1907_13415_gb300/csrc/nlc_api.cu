@@ -347,6 +347,12 @@ nlc_status nlc_set_check(nlc_ctx* ctx, int32_t every) {
   return NLC_OK;
 }
 
+nlc_status nlc_set_wait_budget(nlc_ctx* ctx, int64_t ns) {
+  if (!ctx) return NLC_EINVAL;
+  ctx->eng->wait_ns = ns < 0 ? 200ull * 1000 * 1000 : (uint64_t)ns;
+  return NLC_OK;
+}
+
 nlc_status nlc_observables(nlc_ctx* ctx, int32_t inst, nlc_obs* out,
                            double* s_profile) {
   if (!ctx) return NLC_EINVAL;

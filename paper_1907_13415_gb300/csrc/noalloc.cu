@@ -11,11 +11,13 @@
 // the stress, rho and u, the reduction partials and the S profile) in
 // file-scope __device__ arrays of fixed size, which every GPU that loads the
 // library holds until the process exits.  The first call on a device looks
-// up the arrays' device addresses with cudaGetSymbolAddress; make that first
-// call before any stream capture.  Every call shares the arrays: two calls
-// whose work overlaps on the GPU (different streams or threads) race and
-// give undefined results.  Nothing here needs clearing between calls: each
-// call overwrites every scratch value it later reads.
+// up the arrays' device addresses with cudaGetSymbolAddress.  Every call
+// ends by copying the totals to the host and synchronising the stream, so
+// the entry point cannot run inside a stream capture; it refuses a
+// capturing stream with NLC_EINVAL.  Every call shares the arrays: two
+// calls whose work overlaps on the GPU (different streams or threads) race
+// and give undefined results.  Nothing here needs clearing between calls:
+// each call overwrites every scratch value it later reads.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -25,6 +27,7 @@
 #include "aux_kernels.cuh"
 #include "common.cuh"
 #include "lattice.cuh"
+#include "obs_finish.h"
 #include "physics.cuh"
 #include "step_unfused.cuh"
 
@@ -106,26 +109,7 @@ nlc_status run(const Dims& d, const Par<double>& p, const double* f, const doubl
           cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return NLC_ECUDA;
-  out->mass = tot[0];
-  out->mom[0] = tot[1];
-  out->mom[1] = tot[2];
-  out->mom[2] = tot[3];
-  out->s_area = tot[4];
-  out->free_energy = tot[5];
-  out->nonfinite = (int64_t)tot[6];
-  out->u_l2 = std::sqrt(tot[7]);
-  out->max_u = tot[8];
-  out->radius = (DIM == 2 || d.nz == 1) ? std::sqrt(tot[4] / M_PI)
-                                        : std::cbrt(3.0 * tot[4] / (4.0 * M_PI));
-  const double half = s_ref / 2.0;
-  out->x_iface = -1.0;
-  for (int x = 0; x < d.nx; x++) {
-    const double a = hprof[x], b = hprof[(x + 1) % d.nx];
-    if (a >= half && b < half) {
-      out->x_iface = x + (a - half) / (a - b);
-      break;
-    }
-  }
+  obs_from_totals(tot, hprof, d.nx, DIM == 2 || d.nz == 1, s_ref, out);
   out->step = 0;
   return NLC_OK;
 }
@@ -147,6 +131,15 @@ extern "C" NLC_API nlc_status nlc_observables_static(const nlc_grid* grid,
   const Layout L = make_layout(d, grid->lattice == NLC_D3Q19);
   // sizes beyond the fixed scratch are refused (no fallback allocation)
   if (d.n > kMaxCells || d.nx > kMaxNx || L.comp > kMaxPadded) return NLC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the call ends with a copy to the host and a stream synchronisation,
+  // which a stream capture cannot hold
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return NLC_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone) return NLC_EINVAL;
+  // a launch error left pending by earlier work of the calling thread is
+  // cleared here, so that it is not reported as this call's failure
+  (void)cudaGetLastError();
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return NLC_ECUDA;
   if (!g_scratch_ptr[dev]) {
@@ -166,7 +159,6 @@ extern "C" NLC_API nlc_status nlc_observables_static(const nlc_grid* grid,
   p.tau = params->tau;
   p.rho0 = params->rho0;
   derive(p);
-  cudaStream_t st = (cudaStream_t)stream;
   return grid->lattice == NLC_D2Q9
              ? run<LatD2Q9>(d, p, f, Q5, st, g_scratch_ptr[dev], out)
              : run<LatD3Q19>(d, p, f, Q5, st, g_scratch_ptr[dev], out);

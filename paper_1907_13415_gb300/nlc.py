@@ -104,6 +104,7 @@ def load(build_if_missing=True):
         "nlc_count": ([P], I32),
         "nlc_set_graph": ([P, I32], I32),
         "nlc_set_check": ([P, I32], I32),
+        "nlc_set_wait_budget": ([P, I64], I32),
         "nlc_set_params": ([P, I32, ctypes.POINTER(nlc_params)], I32),
         "nlc_set_mrt": ([P, I32, P, I32], I32),
         "nlc_set_stencil": ([P, I32], I32),
@@ -147,7 +148,7 @@ def exported_symbols():
             "nlc_lattice_velocities", "nlc_version", "nlc_set_timing",
             "nlc_get_timing", "nlc_timing_name", "nlc_save", "nlc_load",
             "nlc_adjoint", "nlc_observables_static", "nlc_set_chunk",
-            "nlc_get_chunk", "nlc_autotune"]
+            "nlc_get_chunk", "nlc_autotune", "nlc_set_wait_budget"]
 
 
 def _check(ctx, status):
@@ -229,6 +230,10 @@ def nlc_set_stencil(ctx, kind):
 
 def nlc_set_check(ctx, every):
     _check(ctx, load().nlc_set_check(ctx, int(every)))
+
+
+def nlc_set_wait_budget(ctx, ns):
+    _check(ctx, load().nlc_set_wait_budget(ctx, int(ns)))
 
 
 def nlc_set_graph(ctx, steps):
@@ -534,6 +539,9 @@ class Simulation:
 
     def set_params(self, params):
         nlc_set_params(self.ctx, 0, params)
+
+    def set_wait_budget(self, ns):
+        nlc_set_wait_budget(self.ctx, ns)
 
     def adjoint(self, target_radius, w_radius, w_velocity, nsteps, ckpt_every,
                 want_dQ0=True):

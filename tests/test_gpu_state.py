@@ -169,3 +169,36 @@ def test_float32_q_input_equals_the_float64_entry(precision, pin):
     assert ei.value.status == -4
     a.close()
     b.close()
+
+
+def test_grid_barrier_wait_runs_out_and_context_recovers():
+    """A wait budget of 0 makes the adjoint's cooperative segment kernels give
+    up at their first grid-wide barrier that is not already complete (no
+    tile copy is in flight there): the call fails with NLC_ETIMEOUT and
+    every block returns.  With the budget restored the same context steps
+    and differentiates exactly as a fresh one."""
+    from paper_1907_13415_gb300 import nlc
+    w = wl.adjoint_disc_128().with_(shape=(1, 24, 40), size=7.0)
+    loss = (7.0, 1.0, 1.0)
+    a = make(w, 0)
+    a.set_fields(w.initial_q5())
+    a.set_wait_budget(0)
+    with pytest.raises(nlc.NlcError) as ei:
+        a.adjoint(*loss, nsteps=12, ckpt_every=4)
+    assert ei.value.status == -5
+    assert "grid-barrier" in nlc.nlc_last_error(a.ctx)
+    a.set_wait_budget(-1)
+    a.set_fields(w.initial_q5())
+    a.step(9)
+    ga = a.adjoint(*loss, nsteps=12, ckpt_every=4)
+    b = make(w, 0)
+    b.set_fields(w.initial_q5())
+    b.step(9)
+    gb = b.adjoint(*loss, nsteps=12, ckpt_every=4)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    assert np.array_equal(a.get_fields()[0], b.get_fields()[0])
+    for k in ("loss", "dgamma", "dK", "dGamma"):
+        assert ga[k] == gb[k], k
+    assert np.array_equal(ga["dQ0"], gb["dQ0"])
+    a.close()
+    b.close()

@@ -28,7 +28,7 @@ def _cuda():
 
 @pytest.mark.parametrize("lattice,shape", [(wl.D2Q9, (1, 40, 64)),
                                            (wl.D3Q19, (10, 12, 14))])
-def test_static_observables_equal_context_observables(lattice, shape):
+def test_static_observables_equal_context_observables(orc, lattice, shape):
     import torch
     from paper_1907_13415_gb300 import nlc
     base = wl.disc_256() if lattice == wl.D2Q9 else wl.sphere_256()
@@ -56,6 +56,16 @@ def test_static_observables_equal_context_observables(lattice, shape):
             assert abs(got[k] - ref[k]) < TOL * np.prod(shape), k
         assert abs(got["x_iface"] - ref["x_iface"]) < 1e-9
         assert got["nonfinite"] == 0
+    # and, independently of the library's other entry point, against the
+    # oracle's observables of the same populations and Q
+    from helpers import perm_to_oracle
+    perm = perm_to_oracle(orc, lattice)
+    fo = np.empty_like(f)
+    fo[perm] = f
+    oo = orc.observables(lattice, wl.param_vector(w.params), fo, Q)
+    for k in ("mass", "s_area", "radius", "free_energy", "max_u"):
+        assert got[k] == pytest.approx(float(oo[k]), rel=TOL), k
+    assert abs(got["x_iface"] - float(oo["x_iface"])) < 1e-9
 
 
 def test_static_observables_refuse_lattices_beyond_the_scratch():
@@ -72,3 +82,23 @@ def test_static_observables_refuse_lattices_beyond_the_scratch():
     with pytest.raises(nlc.NlcError):
         nlc.nlc_observables_static(grid, wl.BASE_PARAMS, f_d.data_ptr(),
                                    f_d.data_ptr(), stream)
+
+
+def test_static_observables_refuse_a_capturing_stream():
+    """The call ends with a copy to the host and a stream synchronisation,
+    which no stream capture can hold: a capturing stream is refused before
+    any work is queued."""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    f_d = torch.zeros(9 * 64, dtype=torch.float64, device="cuda")
+    q_d = torch.zeros(5 * 64, dtype=torch.float64, device="cuda")
+    grid = nlc.nlc_grid(8, 8, 1, nlc.NLC_D2Q9, nlc.NLC_FP64)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    status = None
+    with torch.cuda.graph(g, stream=s):
+        q_d.add_(0.0)  # the capture holds one kernel
+        status = nlc.load().nlc_observables_static(
+            grid, nlc._params(wl.BASE_PARAMS), f_d.data_ptr(), q_d.data_ptr(),
+            s.cuda_stream, nlc.nlc_obs())
+    assert status == -1
