@@ -615,6 +615,16 @@ def sweep_figures(args):
 
     b.step(max(args.warmup, args.graph_steps))
     t_batch = timed(b.step, args.steps)
+    # the same batch as cooperative launches of the persistent kernel, each
+    # advancing persist_steps steps (inside the same graphs)
+    t_pers = None
+    if args.persist_steps > 0:
+        for i, w in enumerate(ws):
+            b.set_fields(i, w.initial_q5())
+        b.set_persistent(args.persist_steps)
+        b.step(max(args.warmup, args.graph_steps))
+        t_pers = timed(b.step, args.steps)
+        b.set_persistent(0)
     b.close()
     sims = []
     for w in ws:
@@ -642,11 +652,20 @@ def sweep_figures(args):
                         "Ly in {8,16,64}, gamma in [2.60, 2.80], FP32",
             "instances": len(ws), "cells": cells, "steps": args.steps,
             "graph_steps": args.graph_steps,
-            "batched": {"value": v_b, "unit": UNIT, "ms_per_step": t_batch / args.steps},
+            "batched": {"value": v_b, "unit": UNIT, "ms_per_step": t_batch / args.steps,
+                        "form": "two kernels per step, graphs of graph_steps steps"},
+            "persistent": (None if t_pers is None else
+                           {"value": cells * args.steps / (t_pers * 1e-3) / 1e6, "unit": UNIT,
+                            "ms_per_step": t_pers / args.steps,
+                            "persist_steps": args.persist_steps,
+                            "form": "one cooperative launch per persist_steps steps, "
+                                    "inside the same graphs",
+                            "over_two_kernel_form": t_batch / t_pers}),
             "sequential": {"value": v_s, "unit": UNIT, "ms_per_step": t_seq / args.steps,
                            "launches_per_step": 2 * len(ws)},
             "tuning": {"batched": tune_b, "chunk": args.chunk, "taper": args.taper},
-            "batched_over_sequential": t_seq / t_batch}
+            "batched_over_sequential": t_seq / t_batch,
+            "persistent_over_sequential": None if t_pers is None else t_seq / t_pers}
 
 
 def run_sweep(args):
@@ -755,6 +774,9 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=0,
                     help="steps of the adjoint workload (default: its own 2000)")
     ap.add_argument("--graph-steps", type=int, default=50)
+    ap.add_argument("--persist-steps", type=int, default=50,
+                    help="sweep: steps per cooperative launch of the persistent kernel "
+                         "(0: skip that arm)")
     ap.add_argument("--chunk", type=int, default=-1,
                     help="z planes per block of the fused kernels: -1 autotune "
                          "(default), 0 the library default, N fixed")

@@ -176,6 +176,19 @@ NLC_API int32_t nlc_count(const nlc_ctx* ctx);
  * Not used while timing is enabled. */
 NLC_API nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps);
 
+/* steps > 0: nlc_step runs the fused schedule as cooperative launches of
+ * one persistent kernel, each advancing every lattice of the context by up
+ * to `steps` time steps (the paper has no counterpart; for batched sweeps of
+ * many small lattices, where launch gaps dominate).  Its blocks stay
+ * resident and take the tiles of the joint tile list one by one, with a
+ * grid-wide barrier, bounded by the wait budget (nlc_set_wait_budget),
+ * between the lb and Beris-Edwards phases of each step; the results equal
+ * the two-kernel form bit for bit.  Combines with nlc_set_graph (a graph
+ * then holds the cooperative launches).  0 (default): two kernel launches
+ * per step.  The MRT collision and devices without cooperative launch keep
+ * the two-kernel form.  Errors: NLC_EINVAL (steps < 0). */
+NLC_API nlc_status nlc_set_persistent(nlc_ctx* ctx, int32_t steps);
+
 /* Finite-difference stencils of the context (every lattice).
  * NLC_STENCIL_STANDARD (default): central first derivatives and the
  * 2d+1-point Laplacian (Sec. 1.2.2, second order).  NLC_STENCIL_ISOTROPIC:
@@ -351,7 +364,7 @@ NLC_API nlc_status nlc_set_timing(nlc_ctx* ctx, int32_t enable);
  * total_ms[k] milliseconds and launches[k] launch counts (arrays of at least
  * max_kernels entries; either may be NULL).  *n_kernels (may be NULL) gets
  * NLC_N_KERNELS.  Synchronises the stream. */
-#define NLC_N_KERNELS 7
+#define NLC_N_KERNELS 8
 NLC_API nlc_status nlc_get_timing(nlc_ctx* ctx, int32_t max_kernels,
                                   double* total_ms, int64_t* launches,
                                   int32_t* n_kernels);

@@ -10,6 +10,7 @@
 
 #include "adjoint.cuh"
 #include "adjoint_segment.cuh"
+#include "adjoint_tiled.cuh"
 #include "aux_kernels.cuh"
 #include "engine.h"
 #include "obs_finish.h"
@@ -114,6 +115,9 @@ struct InstHost {
   int64_t rec_len = 0;
   GridBarrier* bar = nullptr;  // [0], [1]: record kernels; [2]: reverse kernel
   int seg_grid = 0;            // blocks of the cooperative launches (0: not available)
+  // single-plane lattices: the reverse sweep as owned tiles with recomputed
+  // halos (adjoint_tiled.cuh), tiles_x x tiles_y blocks; 0: not used
+  int rev_tiles_x = 0, rev_grid = 0;
 };
 
 // T: arithmetic and the Q, u fields; G: storage of the populations (float
@@ -386,6 +390,8 @@ class Engine final : public EngineBase {
     return NLC_OK;
   }
 
+  void invalidate_graphs() override { drop_graphs(); }
+
   void drop_graphs() {
     for (int c = 0; c < 2; c++)
       if (graph_[c]) {
@@ -431,6 +437,12 @@ class Engine final : public EngineBase {
             "unfused schedule";
       return NLC_EUNSUPPORTED;
     }
+    // the persistent kernel's occupancy and counters are set up here, not
+    // inside a stream capture (no allocation may happen there)
+    if (persistent_steps > 0 && !any_mrt_) {
+      int grid;
+      if ((s = persist_grid(&grid))) return s;
+    }
     // whole chunks of steps replay a captured CUDA graph (not while timing)
     if (graph_steps > 0 && !timer.on) {
       while (n >= graph_steps) {
@@ -440,8 +452,58 @@ class Engine final : public EngineBase {
         n -= graph_steps;
       }
     }
+    return fused_launches(n, args_.stream);
+  }
+
+  // n fused steps launched on st: two kernels per step, or cooperative
+  // launches of the persistent kernel of up to persistent_steps steps each
+  nlc_status fused_launches(int64_t n, cudaStream_t st) {
+    nlc_status s;
+    int grid = 0;
+    if (persistent_steps > 0 && !any_mrt_ && (s = persist_grid(&grid))) return s;
+    if (grid > 0) {
+      while (n > 0) {
+        const int m = (int)std::min<int64_t>(n, persistent_steps);
+        if ((s = step_persistent(st, m, grid))) return s;
+        n -= m;
+      }
+      return NLC_OK;
+    }
     for (int64_t k = 0; k < n; k++)
-      if ((s = step_fused(args_.stream))) return s;
+      if ((s = step_fused(st))) return s;
+    return NLC_OK;
+  }
+
+  // blocks of the persistent kernel (0: not available on this device)
+  nlc_status persist_grid(int* grid) {
+    const int v = (iso_ ? 2 : 0) + (ix32_ ? 1 : 0);
+    if (pgrid_max_[v] < 0)
+      pgrid_max_[v] = persistent_grid_max<Lat, T, G>(iso_, ix32_);
+    if (pgrid_max_[v] > 0 && !pbar_) {
+      nlc_status s;
+      if ((s = alloc(&pbar_, 1)) || (s = alloc(&pclaim_, 1))) return s;
+    }
+    *grid = std::min(pgrid_max_[v], ntiles_);
+    return NLC_OK;
+  }
+
+  // m steps of every lattice in one cooperative launch
+  nlc_status step_persistent(cudaStream_t st, int m, int grid) {
+    NLC_CK(cudaMemsetAsync(pbar_, 0, sizeof(GridBarrier), st));
+    NLC_CK(cudaMemsetAsync(pclaim_, 0, sizeof(unsigned), st));
+    const int e0 = mark();
+    PersistArgs pa{pbar_, pclaim_, wait_ns};
+    cudaError_t e = launch_fused_persistent<Lat, T, G>(insts_dev_, qmaps_dev_, umaps_dev_,
+                                                       tiles_dev_, ntiles_, cur_, m, derr_, pa,
+                                                       grid, st, iso_, ix32_);
+    if (e != cudaSuccess) {
+      err = std::string("persistent step kernel: ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      return NLC_ECUDA;
+    }
+    const int e1 = mark();
+    if (timer.on) timer.span(KID_PERSIST, e0, e1);
+    if (m & 1) cur_ ^= 1;
     return NLC_OK;
   }
 
@@ -868,6 +930,33 @@ class Engine final : public EngineBase {
     return sms * std::min(nb1, nb2);
   }
 
+  // Single-plane lattices reverse each segment as owned 16 x 16 tiles with
+  // recomputed halos (one grid barrier per step) when every tile's block
+  // can be resident and the parameter-adjoint slots of the segment kernel
+  // cover them; NLC_ADJ_TILED=0 keeps the one-cell-per-thread kernel.
+  nlc_status plan_tiled_reverse(InstHost<T, G>& I) {
+    I.rev_tiles_x = I.rev_grid = 0;
+    if constexpr (DIM == 2) {
+      const char* env = std::getenv("NLC_ADJ_TILED");
+      if (env && env[0] == '0') return NLC_OK;
+      const int tx = (I.d.nx + ATX - 1) / ATX, ty = (I.d.ny + ATY - 1) / ATY;
+      const int64_t want = (int64_t)tx * ty;
+      if (I.seg_grid <= 0 || want > I.seg_grid) return NLC_OK;
+      const size_t bytes = sizeof(AdjTile<T>);
+      NLC_CK(cudaFuncSetAttribute(k_seg_reverse_tiled<Lat, T>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      int dev = 0, sms = 0, nb = 0;
+      NLC_CK(cudaGetDevice(&dev));
+      NLC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      NLC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_reverse_tiled<Lat, T>, ABA,
+                                                           bytes));
+      if ((int64_t)nb * sms < want) return NLC_OK;
+      I.rev_tiles_x = tx;
+      I.rev_grid = (int)want;
+    }
+    return NLC_OK;
+  }
+
   // record slots (two sets) for segments of up to len steps
   nlc_status ensure_segment(InstHost<T, G>& I, int64_t len) {
     nlc_status s;
@@ -875,6 +964,7 @@ class Engine final : public EngineBase {
       if ((s = alloc(&I.bar, 3))) return s;
       const int64_t want = (I.d.n + SEG_THREADS - 1) / SEG_THREADS;
       I.seg_grid = (int)std::min<int64_t>(seg_grid_max(), want);
+      if ((s = plan_tiled_reverse(I))) return s;
     }
     if (I.seg_grid <= 0 || I.rec_len >= len) return NLC_OK;
     const int64_t n = I.d.n, comp = I.L.comp;
@@ -948,6 +1038,16 @@ class Engine final : public EngineBase {
     a.bar = I.bar + 2;
     void* args[] = {&a};
     NLC_CK(cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st));
+    if constexpr (DIM == 2) {
+      if (I.rev_grid > 0) {
+        int tiles_x = I.rev_tiles_x;
+        void* targs[] = {&a, &tiles_x};
+        NLC_CK(cudaLaunchCooperativeKernel((const void*)k_seg_reverse_tiled<Lat, T>,
+                                           dim3(I.rev_grid), dim3(ABA), targs,
+                                           sizeof(AdjTile<T>), st));
+        return NLC_OK;
+      }
+    }
     NLC_CK(cudaLaunchCooperativeKernel((const void*)k_seg_reverse<Lat, T>, dim3(I.seg_grid),
                                        dim3(SEG_THREADS), args, 0, st));
     return NLC_OK;
@@ -1113,7 +1213,7 @@ class Engine final : public EngineBase {
     cur_ = c;
     NLC_CK(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
     nlc_status s = NLC_OK;
-    for (int k = 0; k < len && s == NLC_OK; k++) s = step_fused(cap_stream_);
+    s = fused_launches(len, cap_stream_);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap_stream_, &g);
     cur_ = saved;
@@ -1136,7 +1236,8 @@ class Engine final : public EngineBase {
 
   // captures graph_steps fused steps starting from buffer parity c
   nlc_status ensure_graph(int c) {
-    if (graph_[c] && graph_len_[c] == graph_steps) return NLC_OK;
+    if (graph_[c] && graph_len_[c] == graph_steps && graph_pers_[c] == persistent_steps)
+      return NLC_OK;
     if (graph_[c]) {
       cudaGraphExecDestroy(graph_[c]);
       graph_[c] = nullptr;
@@ -1144,6 +1245,7 @@ class Engine final : public EngineBase {
     nlc_status s = capture_steps(c, graph_steps, &graph_[c]);
     if (s) return s;
     graph_len_[c] = graph_steps;
+    graph_pers_[c] = persistent_steps;
     return NLC_OK;
   }
 
@@ -1176,6 +1278,10 @@ class Engine final : public EngineBase {
   bool ix32_ = false;                     // Q n < 2^32 on every lattice (pop_off)
   cudaEvent_t seg_ev_[5] = {};
   int graph_len_[2] = {0, 0};
+  int graph_pers_[2] = {0, 0};           // persistent_steps the graphs hold
+  int pgrid_max_[4] = {-1, -1, -1, -1};  // persistent blocks per (iso, ix32)
+  GridBarrier* pbar_ = nullptr;          // persistent kernel's grid barrier
+  unsigned* pclaim_ = nullptr;           // and its tile counter
 };
 
 template <class Lat, class T, class G = T>

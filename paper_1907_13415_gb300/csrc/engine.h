@@ -14,7 +14,7 @@ namespace nlc {
 
 // kernel ids of the timing log (names in nlc_timing_name)
 enum KernelId { KID_FUSED_LB = 0, KID_FUSED_BE, KID_STRESS, KID_LB, KID_PREDICT,
-                KID_CORRECT, KID_ADJOINT, KID_COUNT };
+                KID_CORRECT, KID_ADJOINT, KID_PERSIST, KID_COUNT };
 
 // CUDA events recorded around kernel launches while timing is on.
 class KernelTimer {
@@ -75,7 +75,12 @@ struct EngineBase {
   // budget in nanoseconds of every grid-barrier wait of the persistent
   // kernels (a wait that runs out ends the call with NLC_ETIMEOUT)
   uint64_t wait_ns = 200ull * 1000 * 1000;
+  // >0: fused steps run as cooperative launches of the persistent kernel,
+  // each advancing up to this many steps (nlc_set_persistent)
+  int persistent_steps = 0;
   virtual int count() const = 0;
+  // drops the captured step graphs (after a change of how steps launch)
+  virtual void invalidate_graphs() = 0;
   // number of non-finite stored values of each lattice (syncs); first bad
   // lattice in *bad (-1 if none)
   virtual nlc_status check_finite(int* bad) = 0;

@@ -200,6 +200,14 @@ nlc_status nlc_set_graph(nlc_ctx* ctx, int32_t steps) {
   return NLC_OK;
 }
 
+nlc_status nlc_set_persistent(nlc_ctx* ctx, int32_t steps) {
+  if (!ctx) return NLC_EINVAL;
+  if (steps < 0) return fail(ctx, NLC_EINVAL, "negative persistent step count");
+  if (steps != ctx->eng->persistent_steps) ctx->eng->invalidate_graphs();
+  ctx->eng->persistent_steps = steps;
+  return NLC_OK;
+}
+
 int32_t nlc_count(const nlc_ctx* ctx) { return ctx ? (int32_t)ctx->grids.size() : -1; }
 
 nlc_status nlc_set_schedule(nlc_ctx* ctx, int32_t schedule) {
@@ -500,7 +508,8 @@ nlc_status nlc_get_timing(nlc_ctx* ctx, int32_t max_kernels, double* total_ms,
 
 const char* nlc_timing_name(int32_t k) {
   static const char* names[nlc::KID_COUNT] = {
-      "fused_lb", "fused_be", "stress", "lb", "predict", "correct", "adjoint_step"};
+      "fused_lb", "fused_be", "stress", "lb", "predict", "correct", "adjoint_step",
+      "fused_persistent"};
   return (k >= 0 && k < nlc::KID_COUNT) ? names[k] : "?";
 }
 

@@ -36,6 +36,7 @@
 #include "aux_kernels.cuh"
 #include "chunks.h"
 #include "common.cuh"
+#include "grid_sync.cuh"
 #include "lattice.cuh"
 #include "packed.cuh"
 #include "physics.cuh"
@@ -297,12 +298,18 @@ __device__ __forceinline__ size_t pop_off(int i, unsigned n, unsigned o) {
 // of aux_kernels.cuh: rho and u of Eq. 6 in the cell phase, the Q terms of
 // the tile's cells in the ring phase), summed per block into
 // obs_partial[block][OBS_SLOTS]; nothing is stored.
-template <class Lat, class T, class G, bool MRT, bool ISO, bool IX32, bool OBS = false>
-__global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
-    k_fused_lb(const InstDev<T, G>* __restrict__ insts,
-               const CUtensorMap* __restrict__ qmaps,
-               const TileRef* __restrict__ tiles, int cur,
-               unsigned* __restrict__ err, double* __restrict__ obs_partial) {
+// PERSIST: called repeatedly by the blocks of the persistent kernel, which
+// rewrites the populations it reads within one launch: the pulls then go
+// through L2 only (ld.global.cg) instead of the read-only path.
+// Returns false when a bounded wait ran out (the error word is set and the
+// block's copies are drained).
+template <class Lat, class T, class G, bool MRT, bool ISO, bool IX32, bool OBS = false,
+          bool PERSIST = false>
+__device__ __forceinline__ bool fused_lb_tile(const TileRef tile,
+                                              const InstDev<T, G>* __restrict__ insts,
+                                              const CUtensorMap* __restrict__ qmaps, int cur,
+                                              unsigned* __restrict__ err,
+                                              double* __restrict__ obs_partial) {
   using C = LbCfg<Lat, T>;
   constexpr int DIM = Lat::DIM;
   constexpr int NPI = C::NPI;
@@ -311,7 +318,6 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
   auto sQ = [&](int slot) { return reinterpret_cast<T*>(smem + slot * C::q_slot); };
   auto sP = [&](int slot) { return reinterpret_cast<T*>(smem + C::off_p + slot * C::p_slot); };
 
-  const TileRef tile = tiles[blockIdx.x];
   const InstDev<T, G>& I = insts[tile.inst];
   const Dims d = I.d;
   const Par<T> p = I.p;
@@ -434,7 +440,10 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     auto ld = [&](int i) {
       const unsigned off = (unsigned)(plane[Lat::c(i, 2) + 1] + rowy[Lat::c(i, 1) + 1] +
                                       colx[Lat::c(i, 0) + 1]);
-      return T(__ldg(gin + pop_off<IX32>(i, n32, off)));
+      if constexpr (PERSIST)
+        return T(__ldcg(gin + pop_off<IX32>(i, n32, off)));
+      else
+        return T(__ldg(gin + pop_off<IX32>(i, n32, off)));
     };
     if constexpr (kPacked) {
       gn.g0 = ld(0);
@@ -598,7 +607,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
       }
       if (__syncthreads_or(late)) {
         abort_block();
-        return;
+        return false;
       }
       lb_cell(0, t & 1);
       if (t + 1 < nt) {
@@ -618,7 +627,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
                                sP(pslot(z0 - 1)), p);
     if (__syncthreads_or(late)) {
       abort_block();
-      return;
+      return false;
     }
     if (tid == 0) issue(z0 + 2);
     wait(z0 + 1);
@@ -663,7 +672,7 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
       }
       if (__syncthreads_or(late)) {
         abort_block();
-        return;
+        return false;
       }
       if (tid >= NT)
         force_plane(z);
@@ -677,7 +686,23 @@ __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     __shared__ double s_obs[32];
     obs_block_out<T>(oacc, onbad, oumax, s_obs, obs_partial);
   }
+  // every copy issued was waited on: retire the barriers, so that the
+  // block's next tile (persistent kernel) can initialise them again
+  __syncthreads();
+  if (tid == 0)
+    for (int s = 0; s < C::NSQ; s++) mbar_inval(&bars[s]);
   (void)NPI;
+  return true;
+}
+
+template <class Lat, class T, class G, bool MRT, bool ISO, bool IX32, bool OBS = false>
+__global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
+    k_fused_lb(const InstDev<T, G>* __restrict__ insts,
+               const CUtensorMap* __restrict__ qmaps,
+               const TileRef* __restrict__ tiles, int cur,
+               unsigned* __restrict__ err, double* __restrict__ obs_partial) {
+  (void)fused_lb_tile<Lat, T, G, MRT, ISO, IX32, OBS>(tiles[blockIdx.x], insts, qmaps, cur, err,
+                                                      obs_partial);
 }
 
 
@@ -840,13 +865,14 @@ __device__ __forceinline__ void stencil_adv(const T* __restrict__ c, const T* __
   }
 }
 
+// Returns false when a bounded wait ran out (the error word is set and the
+// block's copies are drained).
 template <class Lat, class T, class G, bool ISO>
-__global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
-    k_fused_be(const InstDev<T, G>* __restrict__ insts,
-               const CUtensorMap* __restrict__ qmaps,
-               const CUtensorMap* __restrict__ umaps,
-               const TileRef* __restrict__ tiles, int cur,
-               unsigned* __restrict__ err) {
+__device__ __forceinline__ bool fused_be_tile(const TileRef tile,
+                                              const InstDev<T, G>* __restrict__ insts,
+                                              const CUtensorMap* __restrict__ qmaps,
+                                              const CUtensorMap* __restrict__ umaps, int cur,
+                                              unsigned* __restrict__ err) {
   using C = BeCfg<Lat, T>;
   constexpr int DIM = Lat::DIM;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -856,7 +882,6 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
   auto sU = [&](int s) { return reinterpret_cast<T*>(smem + C::off_u + s * C::u_slot); };
   auto sQP = [&](int s) { return reinterpret_cast<T*>(smem + C::off_p + s * C::p_slot); };
 
-  const TileRef tile = tiles[blockIdx.x];
   const InstDev<T, G>& I = insts[tile.inst];
   const Dims d = I.d;
   const Par<T> p = I.p;
@@ -997,7 +1022,7 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
       if (tid < C::RING_T) predict(tid, sq, sq, sq, sq, sq, sq, t & 1);
       if (__syncthreads_or(late)) {
         abort_block();
-        return;
+        return false;
       }
       set_tile(y0 + FTY * t);
       correct(0, sq, sq, sq, sq, t & 1, t & 1, t & 1);
@@ -1014,7 +1039,7 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
     if (tid < C::RING_T) predict(tid, 1, 0, 2, 1, 0, 2, 0);  // plane z0-1
     if (__syncthreads_or(late)) {
       abort_block();
-      return;
+      return false;
     }
     wait(3, 3);
     if (tid < C::RING_T) predict(tid, 2, 1, 3, 2, 1, 3, 1);  // plane z0
@@ -1030,13 +1055,91 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
       if (tid < C::RING_T) predict(tid, sq1, sq, sq2, su1, su, su2, sp1);  // plane z+1
       if (__syncthreads_or(late)) {
         abort_block();
-        return;
+        return false;
       }
       correct(z, sq, su, slot_add<NU>(su, NU - 1), su1, sp, slot_add<NP>(sp, NP - 1), sp1);
       sq = sq1;
       su = su1;
       sp = sp1;
     }
+  }
+  // every copy issued was waited on: retire the barriers (see fused_lb_tile)
+  __syncthreads();
+  if (tid == 0)
+    for (int s = 0; s < C::NSQ + C::NSU; s++) mbar_inval(&qbar[s]);
+  return true;
+}
+
+template <class Lat, class T, class G, bool ISO>
+__global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
+    k_fused_be(const InstDev<T, G>* __restrict__ insts,
+               const CUtensorMap* __restrict__ qmaps,
+               const CUtensorMap* __restrict__ umaps,
+               const TileRef* __restrict__ tiles, int cur,
+               unsigned* __restrict__ err) {
+  (void)fused_be_tile<Lat, T, G, ISO>(tiles[blockIdx.x], insts, qmaps, umaps, cur, err);
+}
+
+// ---------------------------------------------------------------------------
+// persistent form: several steps in one cooperative launch
+// ---------------------------------------------------------------------------
+// Every block stays resident (cooperative launch) and runs nsteps steps: in
+// each, the lb phase and then the Beris-Edwards phase hand the tiles of the
+// joint tile list out one by one from a running counter (a block takes the
+// next tile when it has finished its last, so uneven tiles balance), and a
+// grid-wide barrier (grid_sync.cuh, bounded by wait_ns) separates the
+// phases.  Phase k of the launch (k = 2 step + 0 for lb, + 1 for
+// Beris-Edwards) owns the counter values [k (ntiles + G), (k + 1)(ntiles + G)),
+// G = gridDim.x: every block ends its phase with exactly one claim past the
+// tile list.  The tiles compute exactly what the two kernels compute.
+struct PersistArgs {
+  GridBarrier* bar;
+  unsigned* claim;   // zeroed before each launch
+  uint64_t wait_ns;
+};
+
+template <class Lat, class T>
+struct PersistCfg {
+  static constexpr int THREADS = LbCfg<Lat, T>::THREADS;
+  static_assert(THREADS == BeCfg<Lat, T>::THREADS, "one block shape for both phases");
+  static constexpr size_t bytes =
+      LbCfg<Lat, T>::bytes > BeCfg<Lat, T>::bytes ? LbCfg<Lat, T>::bytes : BeCfg<Lat, T>::bytes;
+  static constexpr int MINB = LbCfg<Lat, T>::MINB;
+};
+
+template <class Lat, class T, class G, bool ISO, bool IX32>
+__global__ void __launch_bounds__(PersistCfg<Lat, T>::THREADS, PersistCfg<Lat, T>::MINB)
+    k_fused_persistent(const InstDev<T, G>* __restrict__ insts,
+                       const CUtensorMap* __restrict__ qmaps,
+                       const CUtensorMap* __restrict__ umaps,
+                       const TileRef* __restrict__ tiles, int ntiles, int cur0, int nsteps,
+                       unsigned* __restrict__ err, PersistArgs pa) {
+  __shared__ int s_tile;
+  unsigned gen = 0;
+  const unsigned per_phase = (unsigned)ntiles + gridDim.x;
+  int cur = cur0;
+  for (int step = 0; step < nsteps; step++) {
+#pragma unroll 1
+    for (int ph = 0; ph < 2; ph++) {
+      const unsigned base = (unsigned)(2 * step + ph) * per_phase;
+      while (true) {
+        if (threadIdx.x == 0) s_tile = (int)(atomicAdd(pa.claim, 1u) - base);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();  // every thread has read s_tile before the next claim
+        if (t >= ntiles) break;
+        const bool ok =
+            ph == 0 ? fused_lb_tile<Lat, T, G, false, ISO, IX32, false, true>(
+                          tiles[t], insts, qmaps, cur, err, nullptr)
+                    : fused_be_tile<Lat, T, G, ISO>(tiles[t], insts, qmaps, umaps, cur, err);
+        if (!ok) return;
+      }
+      // the phase's global writes are read by TMA copies after the barrier
+      fence_proxy_async_global();
+      if (!grid_sync(pa.bar, gen, err, pa.wait_ns)) return;
+      fence_proxy_async_global();
+    }
+    cur ^= 1;
   }
 }
 
@@ -1167,6 +1270,51 @@ cudaError_t launch_fused_be(const InstDev<T, G>* insts, const CUtensorMap* qmaps
                             int cur, unsigned* err, cudaStream_t st, bool iso) {
   return iso ? launch_fused_be_as<Lat, T, G, true>(insts, qmaps, umaps, tiles, ntiles, cur, err, st)
              : launch_fused_be_as<Lat, T, G, false>(insts, qmaps, umaps, tiles, ntiles, cur, err, st);
+}
+
+// Blocks of a cooperative launch of the persistent kernel: every block must
+// be resident, so at most the SM count times the blocks per SM that fit
+// (0 if the device cannot launch cooperatively).
+template <class Lat, class T, class G>
+int persistent_grid_max(bool iso, bool ix32) {
+  int dev = 0, sms = 0, coop = 0, nb = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+    return 0;
+  auto occ = [&](auto kernel) {
+    static unsigned long long configured = 0;
+    if (set_smem(kernel, PersistCfg<Lat, T>::bytes, &configured) != cudaSuccess) return -1;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+               &nb, kernel, PersistCfg<Lat, T>::THREADS, PersistCfg<Lat, T>::bytes) ==
+                   cudaSuccess
+               ? nb
+               : -1;
+  };
+  int r;
+  if (iso)
+    r = occ(k_fused_persistent<Lat, T, G, true, false>);
+  else
+    r = ix32 ? occ(k_fused_persistent<Lat, T, G, false, true>)
+             : occ(k_fused_persistent<Lat, T, G, false, false>);
+  return r > 0 ? r * sms : 0;
+}
+
+// nsteps steps of every lattice of the tile list in one cooperative launch
+// of `grid` blocks (at most persistent_grid_max); pa.claim and pa.bar must
+// be zero (the caller clears them on the stream first)
+template <class Lat, class T, class G>
+cudaError_t launch_fused_persistent(const InstDev<T, G>* insts, const CUtensorMap* qmaps,
+                                    const CUtensorMap* umaps, const TileRef* tiles, int ntiles,
+                                    int cur, int nsteps, unsigned* err, PersistArgs pa, int grid,
+                                    cudaStream_t st, bool iso, bool ix32) {
+  void* args[] = {(void*)&insts, (void*)&qmaps, (void*)&umaps, (void*)&tiles, (void*)&ntiles,
+                  (void*)&cur, (void*)&nsteps, (void*)&err, (void*)&pa};
+  const void* k = iso ? (const void*)k_fused_persistent<Lat, T, G, true, false>
+                      : (ix32 ? (const void*)k_fused_persistent<Lat, T, G, false, true>
+                              : (const void*)k_fused_persistent<Lat, T, G, false, false>);
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(PersistCfg<Lat, T>::THREADS), args,
+                                     PersistCfg<Lat, T>::bytes, st);
 }
 
 }  // namespace nlc

@@ -105,6 +105,7 @@ def load(build_if_missing=True):
         "nlc_set_graph": ([P, I32], I32),
         "nlc_set_check": ([P, I32], I32),
         "nlc_set_wait_budget": ([P, I64], I32),
+        "nlc_set_persistent": ([P, I32], I32),
         "nlc_set_params": ([P, I32, ctypes.POINTER(nlc_params)], I32),
         "nlc_set_mrt": ([P, I32, P, I32], I32),
         "nlc_set_stencil": ([P, I32], I32),
@@ -148,7 +149,8 @@ def exported_symbols():
             "nlc_lattice_velocities", "nlc_version", "nlc_set_timing",
             "nlc_get_timing", "nlc_timing_name", "nlc_save", "nlc_load",
             "nlc_adjoint", "nlc_observables_static", "nlc_set_chunk",
-            "nlc_get_chunk", "nlc_autotune", "nlc_set_wait_budget"]
+            "nlc_get_chunk", "nlc_autotune", "nlc_set_wait_budget",
+            "nlc_set_persistent"]
 
 
 def _check(ctx, status):
@@ -234,6 +236,10 @@ def nlc_set_check(ctx, every):
 
 def nlc_set_wait_budget(ctx, ns):
     _check(ctx, load().nlc_set_wait_budget(ctx, int(ns)))
+
+
+def nlc_set_persistent(ctx, steps):
+    _check(ctx, load().nlc_set_persistent(ctx, int(steps)))
 
 
 def nlc_set_graph(ctx, steps):
@@ -381,7 +387,7 @@ class Batch:
     shapes: list of (nz, ny, nx); params: list of parameter dicts."""
 
     def __init__(self, lattice, shapes, params, precision=NLC_FP32,
-                 stream=None, graph_steps=0):
+                 stream=None, graph_steps=0, persistent_steps=0):
         self.lattice = lattice
         self.q = 9 if lattice == NLC_D2Q9 else 19
         self.shapes = [tuple(s) for s in shapes]
@@ -391,6 +397,8 @@ class Batch:
                                     stream)
         if graph_steps:
             nlc_set_graph(self.ctx, graph_steps)
+        if persistent_steps:
+            nlc_set_persistent(self.ctx, persistent_steps)
 
     def __len__(self):
         return len(self.shapes)
@@ -422,6 +430,9 @@ class Batch:
 
     def step(self, n=1):
         nlc_step(self.ctx, n)
+
+    def set_persistent(self, steps):
+        nlc_set_persistent(self.ctx, steps)
 
     def set_chunk(self, chunk, taper=False):
         nlc_set_chunk(self.ctx, chunk, taper)
@@ -536,6 +547,9 @@ class Simulation:
 
     def set_graph(self, steps):
         nlc_set_graph(self.ctx, steps)
+
+    def set_persistent(self, steps):
+        nlc_set_persistent(self.ctx, steps)
 
     def set_params(self, params):
         nlc_set_params(self.ctx, 0, params)

@@ -120,3 +120,90 @@ def test_batch_rejects_mixed_lattices():
     grids = [nlc.nlc_grid(8, 8, 1, nlc.NLC_D2Q9, 1), nlc.nlc_grid(8, 8, 4, nlc.NLC_D3Q19, 1)]
     with pytest.raises(nlc.NlcError):
         nlc.nlc_create_batch(grids, [p, p], stream())
+
+
+@pytest.mark.parametrize("persist,graph", [(1, 0), (7, 0), (4, 10)])
+def test_persistent_kernel_is_bitwise_identical_d2q9(persist, graph):
+    """The persistent form (cooperative launches of several steps, tiles
+    handed out one by one, grid barriers between the phases) gives exactly
+    the two-kernel steps, alone and inside captured graphs, on lattices of
+    uneven sizes and relaxation times."""
+    from paper_1907_13415_gb300 import nlc
+    ws = sweep_members()
+    out = []
+    for k, g in ((0, 0), (persist, graph)):
+        b = nlc.Batch(wl.D2Q9, [w.shape for w in ws], [w.params for w in ws],
+                      precision=nlc.NLC_FP32, stream=stream(), graph_steps=g,
+                      persistent_steps=k)
+        for i, w in enumerate(ws):
+            b.set_fields(i, w.initial_q5())
+        b.step(23)
+        b.step(10)
+        out.append([(b.get_populations(i), b.get_fields(i)[0]) for i in range(len(ws))])
+        b.close()
+    for (fa, qa), (fb, qb) in zip(out[0], out[1]):
+        assert np.array_equal(fa, fb) and np.array_equal(qa, qb)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_persistent_kernel_d3q19_matches_oracle(orc, precision):
+    """Two D3Q19 lattices of different extents and tau in one persistent
+    launch per 4 steps: bitwise the two-kernel result, and the oracle's
+    within the FP64 / FP32 bounds."""
+    from paper_1907_13415_gb300 import nlc
+    from helpers import fp32_tolerance
+    base = wl.sphere_256()
+    ws = [base.with_(shape=(9, 10, 33), size=3.5, noise=1e-3, seed=31),
+          base.with_(shape=(21, 17, 20), size=3.0, noise=1e-3, seed=32,
+                     params=dict(base.params, gamma=2.68, tau=1.5))]
+    res = []
+    for k in (0, 4):
+        b = nlc.Batch(wl.D3Q19, [w.shape for w in ws], [w.params for w in ws],
+                      precision=precision, stream=stream(), persistent_steps=k)
+        b.set_chunk(8, False)
+        for i, w in enumerate(ws):
+            b.set_fields(i, w.initial_q5())
+        b.step(9)
+        res.append([(b.get_populations(i), b.get_fields(i)[0]) for i in range(len(ws))])
+        b.close()
+    perm = perm_to_oracle(orc, wl.D3Q19)
+    tol = 1e-12 if precision == 0 else fp32_tolerance(9)
+    for i, w in enumerate(ws):
+        assert np.array_equal(res[0][i][0], res[1][i][0])
+        assert np.array_equal(res[0][i][1], res[1][i][1])
+        o = run_oracle(orc, w, 9)
+        assert rel(res[1][i][1], o["Q"]) < tol, i
+        assert rel(res[1][i][0], o["f"][perm]) < tol, i
+
+
+def test_persistent_kernel_barrier_runs_out_and_recovers():
+    """A wait budget of 0 makes the persistent kernel's blocks give up at a
+    grid barrier that is not already complete (no tile copy is in flight
+    there): NLC_ETIMEOUT, and with the budget restored the context steps
+    exactly like a fresh one."""
+    from paper_1907_13415_gb300 import nlc
+    ws = sweep_members()[:3]
+
+    def fresh():
+        b = nlc.Batch(wl.D2Q9, [w.shape for w in ws], [w.params for w in ws],
+                      precision=nlc.NLC_FP32, stream=stream(), persistent_steps=5)
+        for i, w in enumerate(ws):
+            b.set_fields(i, w.initial_q5())
+        return b
+
+    a = fresh()
+    nlc.nlc_set_wait_budget(a.ctx, 0)
+    with pytest.raises(nlc.NlcError) as ei:
+        a.step(10)
+        a.observables(0)  # the error is reported at the next synchronising call
+    assert ei.value.status == -5
+    nlc.nlc_set_wait_budget(a.ctx, -1)
+    for i, w in enumerate(ws):
+        a.set_fields(i, w.initial_q5())
+    a.step(10)
+    b = fresh()
+    b.step(10)
+    for i in range(len(ws)):
+        assert np.array_equal(a.get_populations(i), b.get_populations(i))
+    a.close()
+    b.close()

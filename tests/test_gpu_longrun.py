@@ -1,0 +1,79 @@
+"""Long-horizon FP32 drift against the FP64 oracle: the circular droplet
+(256^2 D2Q9, R = 32, gamma = 2.70 + delta) for its full 20000 steps in the
+FP32 bulk form with FP64 reductions, against the oracle run of the same
+problem; max |dQ| (normwise), the radius and max |u| (the spurious velocity,
+Sec. 2.2) compared every 2000 steps.
+
+The oracle needs minutes of host time per case (1.3 G lattice updates), so
+these run only with NLC_LONG=1; with NLC_LONG_OUT set, each case appends its
+figures as one JSON line to that file.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1907_13415_gb300 import workloads as wl
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("NLC_LONG") != "1",
+                                 reason="long run (minutes of oracle time): NLC_LONG=1")]
+
+EVERY = 2000
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("delta", [0.0, 0.002, 0.005])
+def test_disc_256_fp32_20000_steps_against_oracle(orc, delta):
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    w = wl.disc_256(delta)
+    steps = w.steps
+    p = wl.param_vector(w.params)
+    sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                         stream=torch.cuda.current_stream().cuda_stream)
+    sim.set_graph(50)
+    Q0 = w.initial_q5()
+    sim.set_fields(Q0)
+    f = orc.init_equilibrium(w.lattice, w.shape)
+    Q = Q0
+    rows = []
+    done = 0
+    while done < steps:
+        sim.step(EVERY)
+        f, Q = orc.step(w.lattice, p, f, Q, EVERY)
+        done += EVERY
+        og = sim.observables()
+        oo = orc.observables(w.lattice, p, f, Q)
+        Qg, _, _ = sim.get_fields()
+        rows.append({"step": done,
+                     "max_dQ_rel": float(np.abs(Qg - Q).max() / np.abs(Q).max()),
+                     "radius_gpu": og["radius"], "radius_oracle": float(oo["radius"]),
+                     "max_u_gpu": og["max_u"], "max_u_oracle": float(oo["max_u"])})
+    sim.close()
+    dR = max(abs(r["radius_gpu"] - r["radius_oracle"]) for r in rows)
+    dQ = max(r["max_dQ_rel"] for r in rows)
+    du = max(abs(r["max_u_gpu"] - r["max_u_oracle"]) / r["max_u_oracle"] for r in rows)
+    summary = {"case": w.name, "steps": steps, "precision": "fp32",
+               "reference": "FP64 CPU oracle", "max_dQ_rel": dQ,
+               "radius_drift_max": dR, "max_u_rel_diff_max": du,
+               "radius_final_gpu": rows[-1]["radius_gpu"],
+               "radius_final_oracle": rows[-1]["radius_oracle"],
+               "trace": rows}
+    out = os.environ.get("NLC_LONG_OUT")
+    if out:
+        with open(out, "a") as fh:
+            fh.write(json.dumps(summary) + "\n")
+    # FP32 storage and arithmetic over 20000 relaxational steps: the radius
+    # stays within a thousandth of a cell, Q within 1e-3 normwise
+    assert dR < 1e-3
+    assert dQ < 1e-3
+    assert du < 1e-2
