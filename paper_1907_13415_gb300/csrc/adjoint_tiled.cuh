@@ -4,8 +4,8 @@
 // The five stages of a reverse step (adjoint.cuh) each gather the previous
 // stage's output from the neighbouring cells, so the one-cell-per-thread
 // segment kernel (adjoint_segment.cuh) needs a grid-wide barrier after
-// every stage.  Here a block owns a 16 x 16 tile and keeps the stage
-// outputs of a 24 x 24 box around it in shared memory: stage s is computed
+// every stage.  Here a block owns a 16 x 8 tile and keeps the stage
+// outputs of a 24 x 16 box around it in shared memory: stage s is computed
 // on every box cell within Chebyshev distance r_s of the tile
 // (r = 4, 3, 2, 1, 0 for the corrector, predictor, lb, stress and stencil
 // adjoints), which is exactly the support the next stage's gather reads.
@@ -24,10 +24,14 @@
 
 namespace nlc {
 
-constexpr int ATX = 16, ATY = 16;                   // owned tile
+// The tile trades recomputation (the box holds 3 times the tile's cells)
+// against the number of blocks: 16 x 8 tiles put one block on each of 128
+// SMs for a 128^2 lattice (16 x 16 tiles: 64 blocks doing 1.65 times the
+// work each, slower).
+constexpr int ATX = 16, ATY = 8;                    // owned tile
 constexpr int AHALO = 4;                            // halo of the box
 constexpr int ABW = ATX + 2 * AHALO;                // box width (24)
-constexpr int ABH = ATY + 2 * AHALO;                // box height (24)
+constexpr int ABH = ATY + 2 * AHALO;                // box height (16)
 constexpr int ABA = ABW * ABH;                      // box cells = threads per block
 
 // stage outputs on the box, [component][box cell]
@@ -77,9 +81,12 @@ __device__ __forceinline__ void rhs_gather_box(const Field<T>& U, const T* __res
 }
 
 // Reverse sweep of the segment recorded in a (as k_seg_reverse), one block
-// per owned tile of a tiles_x-wide grid of tiles; cooperative launch.
+// per owned tile of a tiles_x-wide grid of tiles; cooperative launch.  At
+// most 96 registers per thread, so that a block of the record kernel of the
+// previous segment (k_seg_record_tiled, at most 72 registers per thread),
+// which runs at the same time on another stream, fits beside it on an SM.
 template <class Lat, class T>
-__global__ void __launch_bounds__(ABA, 1) k_seg_reverse_tiled(SegArgs<T> a, int tiles_x) {
+__global__ void __maxnreg__(96) k_seg_reverse_tiled(SegArgs<T> a, int tiles_x) {
   static_assert(Lat::DIM == 2, "single-plane lattices");
   constexpr int DIM = 2;
   extern __shared__ __align__(16) unsigned char adj_smem[];
@@ -243,6 +250,142 @@ __global__ void __launch_bounds__(ABA, 1) k_seg_reverse_tiled(SegArgs<T> a, int 
     a.acc[3 * blockIdx.x + 0] += g0;
     a.acc[3 * blockIdx.x + 1] += g1;
     a.acc[3 * blockIdx.x + 2] += g2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// record of a segment on the same tiles
+// ---------------------------------------------------------------------------
+// The forward recomputation of a segment (as k_seg_record: the stress, lb,
+// predictor and corrector stages of step_unfused.cuh, keeping Pi, u, Q^P
+// and the next state in the record slots) with the intermediates of a step
+// in shared memory on the tile's box: the stress on r <= 3, the lb update
+// (u) on r <= 2, the predictor (Q^P) on r <= 1, the corrector on the tile,
+// one grid barrier per step.  Records are written for the owned cells
+// (with the periodic images of the padded fields).
+template <class T>
+struct RecTile {
+  T pi[4][ABA];  // stress                (r <= 3)
+  T u[2][ABA];   // velocity of Eq. 6     (r <= 2)
+  T qp[5][ABA];  // predictor Q^P         (r <= 1)
+};
+
+template <class Lat, class T>
+__global__ void __maxnreg__(72) k_seg_record_tiled(SegArgs<T> a, int tiles_x) {
+  static_assert(Lat::DIM == 2, "single-plane lattices");
+  constexpr int DIM = 2;
+  extern __shared__ __align__(16) unsigned char rec_smem[];
+  RecTile<T>& S = *reinterpret_cast<RecTile<T>*>(rec_smem);
+  const SegSlots<Lat, T> R{a};
+  const Dims d = a.d;
+  const Par<T> p = a.p;
+  const int t = threadIdx.x;
+  const int lx = t % ABW - AHALO, ly = t / ABW - AHALO;
+  const int x0 = (int)(blockIdx.x % (unsigned)tiles_x) * ATX;
+  const int y0 = (int)(blockIdx.x / (unsigned)tiles_x) * ATY;
+  const int x = pmod(x0 + lx, d.nx), y = pmod(y0 + ly, d.ny);
+  const int64_t idx = cell_of(d, x, y, 0);
+  const int r = max(max(max(-lx, lx - (ATX - 1)), max(-ly, ly - (ATY - 1))), 0);
+  const bool own = r == 0 && x0 + lx < d.nx && y0 + ly < d.ny;
+  // u and its gradient (u_stencil) from the box
+  auto u_box = [&](T u[3], T G[3][3]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      if (c < DIM) {
+        u[c] = S.u[c][t];
+        G[c][0] = (S.u[c][t + 1] - S.u[c][t - 1]) / T(2);
+        G[c][1] = (S.u[c][t + ABW] - S.u[c][t - ABW]) / T(2);
+        G[c][2] = T(0);
+      } else {
+        u[c] = T(0);
+        G[c][0] = G[c][1] = G[c][2] = T(0);
+      }
+    }
+  };
+  unsigned gen = 0;
+  for (int j = 0; j < a.len; j++) {
+    const Field<T> Q = R.q(j), U = R.u(j), QP = R.qp(j), Qn = R.q(j + 1);
+    T r1[5];
+    // 1. stress (stress_at)
+    if (r <= 3) {
+      T q[5], dq[3][5], lap[5], h[5], P[3][3];
+      q_stencil<T, DIM>(Q, x, y, 0, q, dq, lap);
+      molecular_field(q, lap, p, h);
+      stress<T, DIM>(q, h, dq, p, P);
+#pragma unroll
+      for (int c = 0; c < DIM; c++)
+#pragma unroll
+        for (int b = 0; b < DIM; b++) {
+          S.pi[c * DIM + b][t] = P[c][b];
+          if (own) R.pi(j)[(c * DIM + b) * d.n + idx] = P[c][b];
+        }
+    }
+    __syncthreads();
+    // 2. lb update (lb_at, BGK)
+    if (r <= 2) {
+      T F[3], g[Lat::Q], rho, u[3];
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        T s = T(0);
+        if (c < DIM) {
+#pragma unroll
+          for (int b = 0; b < DIM; b++) {
+            const int e = b == 0 ? 1 : ABW;
+            s += (S.pi[c * DIM + b][t + e] - S.pi[c * DIM + b][t - e]) / T(2);
+          }
+        }
+        F[c] = s;
+      }
+      pull<Lat, T>(R.g(j), d, x, y, 0, g);
+      moments<Lat, T>(g, F, p, rho, u);
+      collide_bgk<Lat, T>(g, rho, u, F, p);
+#pragma unroll
+      for (int c = 0; c < DIM; c++) S.u[c][t] = u[c];
+      if (own) {
+        T* gout = R.g(j + 1);
+#pragma unroll
+        for (int i = 0; i < Lat::Q; i++) gout[(int64_t)i * d.n + idx] = g[i];
+        store_with_images<T, DIM, DIM>(U, d, x, y, 0, u);
+      }
+    }
+    __syncthreads();
+    // 3. predictor (predict_at)
+    if (r <= 1) {
+      T q[5], dq[3][5], lap[5], u[3], G[3][3], qp[5];
+      q_stencil<T, DIM>(Q, x, y, 0, q, dq, lap);
+      u_box(u, G);
+      be_rhs<T, DIM>(q, dq, lap, u, G, p, r1);
+#pragma unroll
+      for (int k = 0; k < 5; k++) {
+        qp[k] = q[k] + r1[k];
+        S.qp[k][t] = qp[k];
+      }
+      if (own) store_with_images<T, 5, DIM>(QP, d, x, y, 0, qp);
+    }
+    __syncthreads();
+    // 4. corrector (correct_at) on the owned cells
+    if (own) {
+      T qp[5], dq[3][5], lap[5], u[3], G[3][3], r2[5], out[5];
+#pragma unroll
+      for (int k = 0; k < 5; k++) {
+        const T v = S.qp[k][t];
+        const T xp = S.qp[k][t + 1], xm = S.qp[k][t - 1];
+        const T yp = S.qp[k][t + ABW], ym = S.qp[k][t - ABW];
+        qp[k] = v;
+        dq[0][k] = (xp - xm) / T(2);
+        dq[1][k] = (yp - ym) / T(2);
+        dq[2][k] = T(0);
+        lap[k] = (xp + xm - T(2) * v) + (yp + ym - T(2) * v);
+      }
+      u_box(u, G);
+      be_rhs<T, DIM>(qp, dq, lap, u, G, p, r2);
+#pragma unroll
+      for (int k = 0; k < 5; k++) out[k] = Q.at(k, x, y, 0) + (r1[k] + r2[k]) / T(2);
+      store_with_images<T, 5, DIM>(Qn, d, x, y, 0, out);
+    }
+    // the step's records are complete everywhere before the next step
+    // reads them around every tile
+    if (!grid_sync(a.bar, gen, a.err, a.wait_ns)) return;
   }
 }
 

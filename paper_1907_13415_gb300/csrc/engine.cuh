@@ -118,6 +118,7 @@ struct InstHost {
   // single-plane lattices: the reverse sweep as owned tiles with recomputed
   // halos (adjoint_tiled.cuh), tiles_x x tiles_y blocks; 0: not used
   int rev_tiles_x = 0, rev_grid = 0;
+  int acc_slots = 0;  // parameter-adjoint slots of the segment kernels
 };
 
 // T: arithmetic and the Q, u fields; G: storage of the populations (float
@@ -481,7 +482,7 @@ class Engine final : public EngineBase {
       pgrid_max_[v] = persistent_grid_max<Lat, T, G>(iso_, ix32_);
     if (pgrid_max_[v] > 0 && !pbar_) {
       nlc_status s;
-      if ((s = alloc(&pbar_, 1)) || (s = alloc(&pclaim_, 1))) return s;
+      if ((s = alloc(&pbar_, 1))) return s;
     }
     *grid = std::min(pgrid_max_[v], ntiles_);
     return NLC_OK;
@@ -490,9 +491,8 @@ class Engine final : public EngineBase {
   // m steps of every lattice in one cooperative launch
   nlc_status step_persistent(cudaStream_t st, int m, int grid) {
     NLC_CK(cudaMemsetAsync(pbar_, 0, sizeof(GridBarrier), st));
-    NLC_CK(cudaMemsetAsync(pclaim_, 0, sizeof(unsigned), st));
     const int e0 = mark();
-    PersistArgs pa{pbar_, pclaim_, wait_ns};
+    PersistArgs pa{pbar_, wait_ns};
     cudaError_t e = launch_fused_persistent<Lat, T, G>(insts_dev_, qmaps_dev_, umaps_dev_,
                                                        tiles_dev_, ntiles_, cur_, m, derr_, pa,
                                                        grid, st, iso_, ix32_);
@@ -696,10 +696,20 @@ class Engine final : public EngineBase {
       err = "TMA tensor maps unavailable; the adjoint needs the fused step";
       return NLC_EUNSUPPORTED;
     }
-    // forward sweep, keeping the state at the start of every segment
+    // forward sweep, keeping the state at the start of every segment; the
+    // record of the last segment, which the backward sweep needs first, runs
+    // on the side stream from its checkpoint while the forward sweep
+    // finishes that segment
     for (int64_t k = 0; k < nseg; k++) {
       if ((s = state_out(I, I.ck + k * S))) return s;
       const int64_t len = std::min<int64_t>(ckpt_every, nsteps - k * ckpt_every);
+      if (k == nseg - 1) {
+        NLC_CK(cudaEventRecord(seg_ev_[0], st));
+        NLC_CK(cudaStreamWaitEvent(side_stream_, seg_ev_[0], 0));
+        const int b = (int)(k & 1);
+        if ((s = segment_record(I, b, I.ck + k * S, (int)len, side_stream_))) return s;
+        NLC_CK(cudaEventRecord(seg_ev_[1 + b], side_stream_));
+      }
       if ((s = fused_steps(len))) return s;
     }
     if ((s = state_out(I, I.ck + nseg * S))) return s;  // final state
@@ -716,7 +726,7 @@ class Engine final : public EngineBase {
     out->u_l2 = obs.u_l2;
     out->loss = loss->w_radius * (R - loss->target_radius) * (R - loss->target_radius) +
                 loss->w_velocity * obs.u_l2;
-    NLC_CK(cudaMemsetAsync(I.acc, 0, sizeof(double) * 3 * (3 * grid1(n) + I.seg_grid), st));
+    NLC_CK(cudaMemsetAsync(I.acc, 0, sizeof(double) * 3 * (3 * grid1(n) + I.acc_slots), st));
     int lc = 0;  // lQ[lc], lG[lc] hold the adjoint of the current state
     {
       const unsigned gb = grid1(n);
@@ -733,7 +743,7 @@ class Engine final : public EngineBase {
     if ((s = segments_backward(I, nsteps, ckpt_every, nseg, S, lc))) return s;
     // gradients: every block slot of every kernel, summed in a fixed order
     const unsigned gb = grid1(n);
-    std::vector<double> acc((size_t)3 * (3 * gb + I.seg_grid));
+    std::vector<double> acc((size_t)3 * (3 * gb + I.acc_slots));
     NLC_CK(cudaMemcpyAsync(acc.data(), I.acc, sizeof(double) * acc.size(),
                            cudaMemcpyDeviceToHost, st));
     if (dQ0) {
@@ -930,10 +940,10 @@ class Engine final : public EngineBase {
     return sms * std::min(nb1, nb2);
   }
 
-  // Single-plane lattices reverse each segment as owned 16 x 16 tiles with
-  // recomputed halos (one grid barrier per step) when every tile's block
-  // can be resident and the parameter-adjoint slots of the segment kernel
-  // cover them; NLC_ADJ_TILED=0 keeps the one-cell-per-thread kernel.
+  // Single-plane lattices record and reverse each segment as owned 16 x 8
+  // tiles with recomputed halos (one grid barrier per step,
+  // adjoint_tiled.cuh) when every tile's block can be resident;
+  // NLC_ADJ_TILED=0 keeps the one-cell-per-thread segment kernels.
   nlc_status plan_tiled_reverse(InstHost<T, G>& I) {
     I.rev_tiles_x = I.rev_grid = 0;
     if constexpr (DIM == 2) {
@@ -941,7 +951,7 @@ class Engine final : public EngineBase {
       if (env && env[0] == '0') return NLC_OK;
       const int tx = (I.d.nx + ATX - 1) / ATX, ty = (I.d.ny + ATY - 1) / ATY;
       const int64_t want = (int64_t)tx * ty;
-      if (I.seg_grid <= 0 || want > I.seg_grid) return NLC_OK;
+      if (I.seg_grid <= 0 || want > seg_grid_max()) return NLC_OK;
       const size_t bytes = sizeof(AdjTile<T>);
       NLC_CK(cudaFuncSetAttribute(k_seg_reverse_tiled<Lat, T>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -951,8 +961,12 @@ class Engine final : public EngineBase {
       NLC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_reverse_tiled<Lat, T>, ABA,
                                                            bytes));
       if ((int64_t)nb * sms < want) return NLC_OK;
+      NLC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_record_tiled<Lat, T>, ABA,
+                                                           sizeof(RecTile<T>)));
+      if ((int64_t)nb * sms < want) return NLC_OK;
       I.rev_tiles_x = tx;
       I.rev_grid = (int)want;
+      I.acc_slots = std::max(I.seg_grid, I.rev_grid);
     }
     return NLC_OK;
   }
@@ -964,6 +978,7 @@ class Engine final : public EngineBase {
       if ((s = alloc(&I.bar, 3))) return s;
       const int64_t want = (I.d.n + SEG_THREADS - 1) / SEG_THREADS;
       I.seg_grid = (int)std::min<int64_t>(seg_grid_max(), want);
+      I.acc_slots = I.seg_grid;
       if ((s = plan_tiled_reverse(I))) return s;
     }
     if (I.seg_grid <= 0 || I.rec_len >= len) return NLC_OK;
@@ -1026,6 +1041,16 @@ class Engine final : public EngineBase {
     a.bar = I.bar + b;
     void* args[] = {&a};
     NLC_CK(cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), ss));
+    if constexpr (DIM == 2) {
+      if (I.rev_grid > 0) {
+        int tiles_x = I.rev_tiles_x;
+        void* targs[] = {&a, &tiles_x};
+        NLC_CK(cudaLaunchCooperativeKernel((const void*)k_seg_record_tiled<Lat, T>,
+                                           dim3(I.rev_grid), dim3(ABA), targs,
+                                           sizeof(RecTile<T>), ss));
+        return NLC_OK;
+      }
+    }
     NLC_CK(cudaLaunchCooperativeKernel((const void*)k_seg_record<Lat, T>, dim3(I.seg_grid),
                                        dim3(SEG_THREADS), args, 0, ss));
     return NLC_OK;
@@ -1054,7 +1079,8 @@ class Engine final : public EngineBase {
   }
 
   // All segments, last to first: the record of segment k-1 runs on the side
-  // stream while segment k reverses on the main stream.  Record set k % 2
+  // stream while segment k reverses on the main stream (the record of the
+  // last segment was queued by the forward sweep).  Record set k % 2
   // is rewritten only after the reverse that read it (segment k+2) is done.
   nlc_status segments_backward(InstHost<T, G>& I, int64_t nsteps, int ckpt_every, int64_t nseg,
                                int64_t S, int& lc) {
@@ -1066,12 +1092,8 @@ class Engine final : public EngineBase {
     };
     nlc_status s;
     const int e0 = mark();
-    NLC_CK(cudaEventRecord(ev_main, st));  // checkpoints and seed are done
-    NLC_CK(cudaStreamWaitEvent(ss, ev_main, 0));
-    if ((s = segment_record(I, (int)((nseg - 1) & 1), I.ck + (nseg - 1) * S, seg_len(nseg - 1),
-                            ss)))
-      return s;
-    NLC_CK(cudaEventRecord(ev_rec[(nseg - 1) & 1], ss));
+    // the record of the last segment was queued on the side stream during
+    // the forward sweep (event ev_rec[(nseg - 1) & 1])
     for (int64_t k = nseg - 1; k >= 0; k--) {
       const int b = (int)(k & 1);
       NLC_CK(cudaStreamWaitEvent(st, ev_rec[b], 0));
@@ -1281,7 +1303,6 @@ class Engine final : public EngineBase {
   int graph_pers_[2] = {0, 0};           // persistent_steps the graphs hold
   int pgrid_max_[4] = {-1, -1, -1, -1};  // persistent blocks per (iso, ix32)
   GridBarrier* pbar_ = nullptr;          // persistent kernel's grid barrier
-  unsigned* pclaim_ = nullptr;           // and its tile counter
 };
 
 template <class Lat, class T, class G = T>

@@ -1084,17 +1084,16 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
 // persistent form: several steps in one cooperative launch
 // ---------------------------------------------------------------------------
 // Every block stays resident (cooperative launch) and runs nsteps steps: in
-// each, the lb phase and then the Beris-Edwards phase hand the tiles of the
-// joint tile list out one by one from a running counter (a block takes the
-// next tile when it has finished its last, so uneven tiles balance), and a
-// grid-wide barrier (grid_sync.cuh, bounded by wait_ns) separates the
-// phases.  Phase k of the launch (k = 2 step + 0 for lb, + 1 for
-// Beris-Edwards) owns the counter values [k (ntiles + G), (k + 1)(ntiles + G)),
-// G = gridDim.x: every block ends its phase with exactly one claim past the
-// tile list.  The tiles compute exactly what the two kernels compute.
+// each, the lb phase and then the Beris-Edwards phase work through the
+// tiles of the joint tile list, block b taking tiles b, b + G, b + 2G, ...
+// (G = gridDim.x; the list is ordered so that neighbouring tiles run
+// together), and a grid-wide barrier (grid_sync.cuh, bounded by wait_ns)
+// separates the phases.  The tiles compute exactly what the two kernels
+// compute.  (Handing the tiles out one by one from an atomic counter, to
+// balance uneven tiles, was measured slower: each claim costs a round trip
+// to L2 and two block barriers.)
 struct PersistArgs {
   GridBarrier* bar;
-  unsigned* claim;   // zeroed before each launch
   uint64_t wait_ns;
 };
 
@@ -1114,20 +1113,12 @@ __global__ void __launch_bounds__(PersistCfg<Lat, T>::THREADS, PersistCfg<Lat, T
                        const CUtensorMap* __restrict__ umaps,
                        const TileRef* __restrict__ tiles, int ntiles, int cur0, int nsteps,
                        unsigned* __restrict__ err, PersistArgs pa) {
-  __shared__ int s_tile;
   unsigned gen = 0;
-  const unsigned per_phase = (unsigned)ntiles + gridDim.x;
   int cur = cur0;
   for (int step = 0; step < nsteps; step++) {
 #pragma unroll 1
     for (int ph = 0; ph < 2; ph++) {
-      const unsigned base = (unsigned)(2 * step + ph) * per_phase;
-      while (true) {
-        if (threadIdx.x == 0) s_tile = (int)(atomicAdd(pa.claim, 1u) - base);
-        __syncthreads();
-        const int t = s_tile;
-        __syncthreads();  // every thread has read s_tile before the next claim
-        if (t >= ntiles) break;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const bool ok =
             ph == 0 ? fused_lb_tile<Lat, T, G, false, ISO, IX32, false, true>(
                           tiles[t], insts, qmaps, cur, err, nullptr)
@@ -1301,8 +1292,8 @@ int persistent_grid_max(bool iso, bool ix32) {
 }
 
 // nsteps steps of every lattice of the tile list in one cooperative launch
-// of `grid` blocks (at most persistent_grid_max); pa.claim and pa.bar must
-// be zero (the caller clears them on the stream first)
+// of `grid` blocks (at most persistent_grid_max); pa.bar must be zero (the
+// caller clears it on the stream first)
 template <class Lat, class T, class G>
 cudaError_t launch_fused_persistent(const InstDev<T, G>* insts, const CUtensorMap* qmaps,
                                     const CUtensorMap* umaps, const TileRef* tiles, int ntiles,
