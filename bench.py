@@ -61,8 +61,8 @@ def alg_bytes(precision):
 # on; reported as null once those sources change.
 NCU_TRAFFIC = {
     # 256 x 256 x 64 capture (4,194,304 cells), see profiles/
-    "fused_lb": ((430.178816e6 + 333.204480e6) / 4194304, "8fff1de26aa98f9e"),
-    "fused_be": ((155.735040e6 + 61.262592e6) / 4194304, "8fff1de26aa98f9e"),
+    "fused_lb": ((430.056192e6 + 333.870080e6) / 4194304, "33ba9dc08b931c2c"),
+    "fused_be": ((155.835648e6 + 61.252096e6) / 4194304, "33ba9dc08b931c2c"),
 }
 
 KERNEL_SOURCES = ["paper_1907_13415_gb300/csrc/step_fused.cuh",
@@ -410,6 +410,8 @@ def run_ours(args, w):
         tune = sim.autotune(args.tune_steps)
     else:
         sim.set_chunk(args.chunk, args.taper)
+    if args.persist > 0:
+        sim.set_persistent(args.persist)
 
     # warm-up
     sim.step(args.warmup)
@@ -423,8 +425,12 @@ def run_ours(args, w):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        for _ in range(args.steps):
-            sim.step(1)
+        if args.persist > 0:
+            # the persistent form: cooperative launches of args.persist steps
+            sim.step(args.steps)
+        else:
+            for _ in range(args.steps):
+                sim.step(1)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier(ws)
@@ -564,7 +570,8 @@ def run_ours(args, w):
             "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic",
             "config": workload_config(args, w, ws),
-            "tuning": {"chunk": nlc_chunk[0], "taper": nlc_chunk[1], "autotune": tune},
+            "tuning": {"chunk": nlc_chunk[0], "taper": nlc_chunk[1], "autotune": tune,
+                       "persistent_steps": args.persist},
             "roofline": roofline,
             "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "accuracy": accuracy, "adjoint": adjoint, "sweep": sweep,
@@ -783,6 +790,9 @@ def main():
                     help="sweep64: batched vs sequential temperature sweep")
     ap.add_argument("--adjoint-steps", type=int, default=0,
                     help="steps of the adjoint workload (default: its own 2000)")
+    ap.add_argument("--persist", type=int, default=0,
+                    help="sphere256: run the step as cooperative launches of the persistent "
+                         "kernel, this many steps each (0: two kernels per step)")
     ap.add_argument("--adjoint-once", action="store_true",
                     help="adjoint128: one nlc_adjoint call, no timing (launch lists)")
     ap.add_argument("--graph-steps", type=int, default=50)

@@ -3,9 +3,9 @@
 The oracle's complex-step twin gives the exact (to rounding) derivative of
 the droplet loss L = w_R (R - R_target)^2 + w_u |u|_2 after T steps with
 respect to gamma, K, Gamma and any direction of the initial Q field.  The
-FP64 adjoint must agree to 1e-8 relative; the FP32 adjoint to 2e-2 (the
-loss gradient is a difference of O(1) terms accumulated over T steps in
-single precision).  FP64 central finite differences of the GPU forward run
+FP64 adjoint must agree to 1e-8 relative; the FP32 adjoint to 1e-4 (the
+loss gradient is accumulated over T steps in single precision; measured
+errors are below 2e-6 here).  FP64 central finite differences of the GPU forward run
 (h = 1e-6) are checked as well.
 """
 import numpy as np
@@ -96,10 +96,10 @@ def test_fp32_adjoint_matches_oracle_within_bound(orc_cs, pset):
     g, _ = gpu_adjoint(w, 60, 16, precision=1)
     for idx, key in ((2, "dgamma"), (1, "dK"), (3, "dGamma")):
         _, d = oracle_loss_derivative(orc_cs, w, 60, dparam=idx)
-        assert g[key] == pytest.approx(d, rel=2e-2), key
+        assert g[key] == pytest.approx(d, rel=1e-4), key
     v = np.random.default_rng(6).normal(size=(5,) + w.shape)
     _, dv = oracle_loss_derivative(orc_cs, w, 60, dQ=v)
-    assert np.sum(g["dQ0"] * v) == pytest.approx(dv, rel=2e-2)
+    assert np.sum(g["dQ0"] * v) == pytest.approx(dv, rel=1e-4)
 
 
 def test_fp64_adjoint_matches_central_differences():

@@ -199,7 +199,7 @@ def test_adjoint_workload_in_full_matches_central_differences(pset):
     """The adjoint workload at its full size (128^2 D2Q9 disc, 2000 steps,
     checkpoints every 100): the FP64 adjoint's dL/dgamma against central
     differences (h = 1e-6) of the FP64 forward run, and the FP32 adjoint
-    within 2% of the FP64 one.  (The oracle's own derivative, by complex
+    within 1e-4 of the FP64 one (measured: below 1e-5).  (The oracle's own derivative, by complex
     step, is the check at smaller sizes.)  Also with the paper's parameters
     (tau = 1.5), where the adjoint of the collision carries a third of each
     population's adjoint back."""
@@ -231,4 +231,4 @@ def test_adjoint_workload_in_full_matches_central_differences(pset):
     fd = (Ls[0] - Ls[1]) / (2 * h)
     assert g64["dgamma"] == pytest.approx(fd, rel=1e-5)
     for k in ("dgamma", "dK", "dGamma"):
-        assert g32[k] == pytest.approx(g64[k], rel=2e-2), k
+        assert g32[k] == pytest.approx(g64[k], rel=1e-4), k
