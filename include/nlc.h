@@ -306,8 +306,9 @@ NLC_API nlc_status nlc_autotune(nlc_ctx* ctx, int32_t trial_steps, nlc_tune* out
 NLC_API nlc_status nlc_set_fields(nlc_ctx* ctx, int32_t inst, const double* Q5,
                           const double* rho, const double* u);
 
-/* The same with Q given in float32 (same layout, caller-owned, pinned arrays
- * read in place) and the fluid at rest with rho = rho0, the initial state of
+/* The same with Q given in float32 (same layout, caller-owned; pinned host
+ * arrays and device arrays are read in place, pageable host arrays go
+ * through a staging copy) and the fluid at rest with rho = rho0, the initial state of
  * Sec. 2 (populations f_i^eq(rho0, 0) = w_i rho0), for contexts whose state
  * is float32 (NLC_FP32): half the host bytes of nlc_set_fields.  The values
  * are stored as given; in a context with float64 Q they are widened

@@ -13,6 +13,7 @@
 #include "adjoint_tiled.cuh"
 #include "aux_kernels.cuh"
 #include "engine.h"
+#include "nvtx_range.h"
 #include "obs_finish.h"
 #include "step_fused.cuh"
 #include "step_unfused.cuh"
@@ -511,6 +512,17 @@ class Engine final : public EngineBase {
   // Device-side address of a page-locked (pinned) host array, which the
   // kernels can read in place over the host link, or nullptr for any other
   // memory (pageable host memory goes through a staging copy instead).
+  // true for memory the device can read directly (device or managed)
+  template <class V>
+  static bool device_array(const V* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  }
+
   template <class V>
   static const V* mapped_host(const V* p) {
     cudaPointerAttributes a;
@@ -529,7 +541,9 @@ class Engine final : public EngineBase {
     if ((s = ensure_staging(I))) return s;
     const int64_t n = I.d.n;
     cudaStream_t st = args_.stream;
-    const float* qs = mapped_host(Q5);
+    // device arrays are read in place too (a caller that uploads the next
+    // state on its own copy stream while the current one is stepped)
+    const float* qs = device_array(Q5) ? Q5 : mapped_host(Q5);
     if (!qs) {
       float* stage = reinterpret_cast<float*>(I.stage);  // 9 n doubles >= 5 n floats
       NLC_CK(cudaMemcpyAsync(stage, Q5, sizeof(float) * 5 * n, cudaMemcpyHostToDevice, st));
@@ -696,21 +710,24 @@ class Engine final : public EngineBase {
       err = "TMA tensor maps unavailable; the adjoint needs the fused step";
       return NLC_EUNSUPPORTED;
     }
-    // forward sweep, keeping the state at the start of every segment; the
-    // record of the last segment, which the backward sweep needs first, runs
-    // on the side stream from its checkpoint while the forward sweep
-    // finishes that segment
-    for (int64_t k = 0; k < nseg; k++) {
-      if ((s = state_out(I, I.ck + k * S))) return s;
-      const int64_t len = std::min<int64_t>(ckpt_every, nsteps - k * ckpt_every);
-      if (k == nseg - 1) {
-        NLC_CK(cudaEventRecord(seg_ev_[0], st));
-        NLC_CK(cudaStreamWaitEvent(side_stream_, seg_ev_[0], 0));
-        const int b = (int)(k & 1);
-        if ((s = segment_record(I, b, I.ck + k * S, (int)len, side_stream_))) return s;
-        NLC_CK(cudaEventRecord(seg_ev_[1 + b], side_stream_));
+    {
+      NvtxRange nvtx_fwd("adjoint: forward sweep");
+      // forward sweep, keeping the state at the start of every segment; the
+      // record of the last segment, which the backward sweep needs first, runs
+      // on the side stream from its checkpoint while the forward sweep
+      // finishes that segment
+      for (int64_t k = 0; k < nseg; k++) {
+        if ((s = state_out(I, I.ck + k * S))) return s;
+        const int64_t len = std::min<int64_t>(ckpt_every, nsteps - k * ckpt_every);
+        if (k == nseg - 1) {
+          NLC_CK(cudaEventRecord(seg_ev_[0], st));
+          NLC_CK(cudaStreamWaitEvent(side_stream_, seg_ev_[0], 0));
+          const int b = (int)(k & 1);
+          if ((s = segment_record(I, b, I.ck + k * S, (int)len, side_stream_))) return s;
+          NLC_CK(cudaEventRecord(seg_ev_[1 + b], side_stream_));
+        }
+        if ((s = fused_steps(len))) return s;
       }
-      if ((s = fused_steps(len))) return s;
     }
     if ((s = state_out(I, I.ck + nseg * S))) return s;  // final state
     // loss and its seed on the final state
@@ -740,7 +757,10 @@ class Engine final : public EngineBase {
       NLC_CK_LAUNCH("adjoint seed");
     }
     // backward sweep, segment by segment (adjoint_segment.cuh)
-    if ((s = segments_backward(I, nsteps, ckpt_every, nseg, S, lc))) return s;
+    {
+      NvtxRange nvtx_bwd("adjoint: backward segments");
+      if ((s = segments_backward(I, nsteps, ckpt_every, nseg, S, lc))) return s;
+    }
     // gradients: every block slot of every kernel, summed in a fixed order
     const unsigned gb = grid1(n);
     std::vector<double> acc((size_t)3 * (3 * gb + I.acc_slots));

@@ -17,6 +17,9 @@
 #include "engine.h"
 #include "lattice.cuh"
 #include "tune_cache.h"
+#include "nvtx_range.h"
+
+using nlc::NvtxRange;
 
 static_assert(nlc::KID_COUNT == NLC_N_KERNELS, "kernel id table out of sync");
 
@@ -256,6 +259,7 @@ static std::string tune_key(const nlc_ctx* ctx) {
 }
 
 nlc_status nlc_autotune(nlc_ctx* ctx, int32_t trial_steps, nlc_tune* out) {
+  NvtxRange nvtx_range("nlc_autotune");
   if (!ctx) return NLC_EINVAL;
   if (trial_steps < 1) return fail(ctx, NLC_EINVAL, "trial_steps must be at least 1");
   nlc_tune res{};
@@ -292,6 +296,7 @@ static bool bad_inst(const nlc_ctx* ctx, int32_t inst) {
 
 nlc_status nlc_set_fields(nlc_ctx* ctx, int32_t inst, const double* Q5,
                           const double* rho, const double* u) {
+  NvtxRange nvtx_range("nlc_set_fields");
   if (!ctx) return NLC_EINVAL;
   if (bad_inst(ctx, inst)) return fail(ctx, NLC_EINVAL, "instance out of range");
   if (!Q5) return fail(ctx, NLC_EINVAL, "Q5 is NULL");
@@ -302,6 +307,7 @@ nlc_status nlc_set_fields(nlc_ctx* ctx, int32_t inst, const double* Q5,
 }
 
 nlc_status nlc_set_fields_f32(nlc_ctx* ctx, int32_t inst, const float* Q5) {
+  NvtxRange nvtx_range("nlc_set_fields_f32");
   if (!ctx) return NLC_EINVAL;
   if (bad_inst(ctx, inst)) return fail(ctx, NLC_EINVAL, "instance out of range");
   if (!Q5) return fail(ctx, NLC_EINVAL, "Q5 is NULL");
@@ -328,6 +334,7 @@ nlc_status nlc_get_populations(nlc_ctx* ctx, int32_t inst, double* f) {
 }
 
 nlc_status nlc_step(nlc_ctx* ctx, int64_t n) {
+  NvtxRange nvtx_range("nlc_step");
   if (!ctx) return NLC_EINVAL;
   if (n < 0) return fail(ctx, NLC_EINVAL, "negative step count");
   const int64_t chunk = ctx->check_every > 0 ? ctx->check_every : n;
@@ -363,6 +370,7 @@ nlc_status nlc_set_wait_budget(nlc_ctx* ctx, int64_t ns) {
 
 nlc_status nlc_observables(nlc_ctx* ctx, int32_t inst, nlc_obs* out,
                            double* s_profile) {
+  NvtxRange nvtx_range("nlc_observables");
   if (!ctx) return NLC_EINVAL;
   if (bad_inst(ctx, inst)) return fail(ctx, NLC_EINVAL, "instance out of range");
   if (!out) return fail(ctx, NLC_EINVAL, "out is NULL");
@@ -472,6 +480,7 @@ nlc_status nlc_load(nlc_ctx* ctx, const void* buf, size_t len) {
 
 nlc_status nlc_adjoint(nlc_ctx* ctx, const nlc_loss* loss, int64_t nsteps,
                        int32_t ckpt_every, nlc_grad* out, double* dQ0) {
+  NvtxRange nvtx_range("nlc_adjoint");
   if (!ctx) return NLC_EINVAL;
   if (!loss || !out) return fail(ctx, NLC_EINVAL, "loss or out is NULL");
   if (nsteps < 1 || ckpt_every < 1) return fail(ctx, NLC_EINVAL, "nsteps and ckpt_every must be >= 1");

@@ -272,7 +272,10 @@ def nlc_set_fields(ctx, inst, Q5, rho=None, u=None):
 
 
 def nlc_set_fields_f32(ctx, inst, Q5):
-    _check(ctx, load().nlc_set_fields_f32(ctx, inst, _ptr(Q5)))
+    """Q5: a float32 numpy array (host), or the integer address of a float32
+    device array of the same layout (read in place)."""
+    ptr = ctypes.c_void_p(Q5) if isinstance(Q5, int) else _ptr(Q5)
+    _check(ctx, load().nlc_set_fields_f32(ctx, inst, ptr))
 
 
 def nlc_get_fields(ctx, inst, Q5=None, rho=None, u=None):
@@ -497,8 +500,12 @@ class Simulation:
 
     def set_fields_f32(self, Q5):
         """Q in float32 (a float32 array is passed as is, pinned memory
-        included), the fluid at rest with rho = rho0."""
-        nlc_set_fields_f32(self.ctx, 0, _f32(Q5, (5,) + self.shape))
+        included; an integer is the address of a float32 device array), the
+        fluid at rest with rho = rho0."""
+        if isinstance(Q5, int):
+            nlc_set_fields_f32(self.ctx, 0, Q5)
+        else:
+            nlc_set_fields_f32(self.ctx, 0, _f32(Q5, (5,) + self.shape))
 
     def get_fields(self):
         sh = self.shape

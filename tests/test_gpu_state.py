@@ -202,3 +202,23 @@ def test_grid_barrier_wait_runs_out_and_context_recovers():
     assert np.array_equal(ga["dQ0"], gb["dQ0"])
     a.close()
     b.close()
+
+
+def test_set_fields_f32_reads_device_arrays_in_place():
+    """nlc_set_fields_f32 takes Q as a float32 host array or a float32
+    device array of the same layout; both give the same state and the same
+    steps, bit for bit."""
+    import torch
+    w = wl.sphere_256().with_(shape=(9, 10, 33), size=3.0, noise=1e-3, seed=12)
+    Q32 = w.initial_q5().astype(np.float32)
+    a = make(w, 1)
+    a.set_fields_f32(Q32)
+    a.step(5)
+    b = make(w, 1)
+    d = torch.tensor(Q32, device="cuda")
+    b.set_fields_f32(d.data_ptr())
+    b.step(5)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    assert np.array_equal(a.get_fields()[0], b.get_fields()[0])
+    a.close()
+    b.close()
