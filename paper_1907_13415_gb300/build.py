@@ -16,7 +16,12 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libnlc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
+# -ftz=true: float32 denormals flush to zero (float64 is unaffected).  The
+# FP32 state (population deviations, Q, u) never comes near the float32
+# denormal range (below 1.2e-38) except through products that vanish either
+# way, and the fused lb kernel runs 1.3% faster (the GPU parity tests pass
+# unchanged).
+NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-ftz=true",
            "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
            "-I", INCLUDE]
 

@@ -98,6 +98,9 @@ struct InstHost {
   // lattice's own tile list and one partial row per tile (+ the total)
   TileRef* obs_tiles = nullptr;
   int obs_ntiles = 0;
+  size_t obs_cap = 0;        // tiles the obs_tiles / obs_part allocations hold
+  int obs_tz = 0;            // chunk list the obs_tiles were built for
+  bool obs_taper = false;
   double* obs_part = nullptr;
   double* prof = nullptr;
   int obs_blocks = 1;
@@ -795,15 +798,30 @@ class Engine final : public EngineBase {
     if (maps_ok_ && !iso_ && ix32_) {
       // one pass of the fused lb kernel in its observing form over this
       // lattice's tiles (the step's tile machinery, nothing stored)
-      if (!I.obs_tiles) {
+      // the lattice's tiles in the chunk list the step runs with (the
+      // autotuner's choice when it ran)
+      if (!I.obs_tiles || I.obs_tz != I.tz || I.obs_taper != taper_) {
         std::vector<TileRef> tl;
-        append_tiles<Lat>(i, I.d, fused_tz<Lat>(I.d, 0), false, &tl);
-        if ((s = alloc(&I.obs_tiles, tl.size())) ||
-            (s = alloc(&I.obs_part, (tl.size() + 1) * OBS_SLOTS)))
-          return s;
+        append_tiles<Lat>(i, I.d, I.tz, taper_, &tl);
+        if (tl.size() > I.obs_cap) {
+          for (void* old : {(void*)I.obs_tiles, (void*)I.obs_part})
+            if (old) {
+              NLC_CK(cudaStreamSynchronize(st));
+              cudaFree(old);
+              allocs_.erase(std::remove(allocs_.begin(), allocs_.end(), old), allocs_.end());
+            }
+          I.obs_tiles = nullptr;
+          I.obs_part = nullptr;
+          if ((s = alloc(&I.obs_tiles, tl.size())) ||
+              (s = alloc(&I.obs_part, (tl.size() + 1) * OBS_SLOTS)))
+            return s;
+          I.obs_cap = tl.size();
+        }
         NLC_CK(cudaMemcpyAsync(I.obs_tiles, tl.data(), sizeof(TileRef) * tl.size(),
                                cudaMemcpyHostToDevice, st));
         I.obs_ntiles = (int)tl.size();
+        I.obs_tz = I.tz;
+        I.obs_taper = taper_;
       }
       cudaError_t e = launch_fused_obs<Lat, T>(insts_dev_, qmaps_dev_, I.obs_tiles, I.obs_ntiles,
                                                cur_, derr_, I.obs_part, st);

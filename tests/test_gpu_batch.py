@@ -207,3 +207,28 @@ def test_persistent_kernel_barrier_runs_out_and_recovers():
         assert np.array_equal(a.get_populations(i), b.get_populations(i))
     a.close()
     b.close()
+
+
+def test_persistent_kernel_with_isotropic_stencils_and_mrt_fallback():
+    """The persistent form with the isotropic stencils gives the two-kernel
+    result bit for bit; with the MRT collision the context keeps the
+    two-kernel form (same result as without persistent steps)."""
+    from paper_1907_13415_gb300 import nlc
+    ws = sweep_members()[:3]
+
+    def run(persist, iso, mrt):
+        b = nlc.Batch(wl.D2Q9, [w.shape for w in ws], [w.params for w in ws],
+                      precision=nlc.NLC_FP32, stream=stream(), persistent_steps=persist)
+        b.set_stencil(1 if iso else 0)
+        if mrt:
+            b.set_mrt(0, np.linspace(0.8, 1.6, 9))
+        for i, w in enumerate(ws):
+            b.set_fields(i, w.initial_q5())
+        b.step(12)
+        out = [b.get_populations(i) for i in range(len(ws))]
+        b.close()
+        return out
+
+    for iso, mrt in ((True, False), (False, True)):
+        for a, c in zip(run(0, iso, mrt), run(6, iso, mrt)):
+            assert np.array_equal(a, c)

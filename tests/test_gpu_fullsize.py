@@ -232,3 +232,35 @@ def test_adjoint_workload_in_full_matches_central_differences(pset):
     assert g64["dgamma"] == pytest.approx(fd, rel=1e-5)
     for k in ("dgamma", "dK", "dGamma"):
         assert g32[k] == pytest.approx(g64[k], rel=1e-4), k
+
+
+def test_whole_256cubed_lattice_fp32_matches_oracle(orc):
+    """Every cell of the 256^3 droplet (the bench's workload and autotuned
+    launch configuration) after 2 FP32 steps against 2 steps of the FP64
+    oracle on the whole lattice (about 1e7 cell updates on the host cores,
+    a few seconds): normwise max |dQ| and max |df| within the FP32 bound,
+    and the droplet radius and mass of the two runs."""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    w = wl.sphere_256()
+    sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP32,
+                         stream=torch.cuda.current_stream().cuda_stream)
+    Q0 = w.initial_q5()
+    sim.set_fields(Q0)
+    sim.autotune(2)
+    sim.step(STEPS)
+    Q, _, _ = sim.get_fields()
+    f = sim.get_populations()
+    og = sim.observables()
+    sim.close()
+    p = wl.param_vector(w.params)
+    fo, Qo = orc.step(w.lattice, p, orc.init_equilibrium(w.lattice, w.shape), Q0, STEPS)
+    perm = perm_to_oracle(orc, w.lattice)
+    tol = fp32_tolerance(STEPS)
+    assert np.abs(Q - Qo).max() < tol * np.abs(Qo).max()
+    del Q
+    assert np.abs(f - fo[perm]).max() < tol * np.abs(fo).max()
+    del f
+    oo = orc.observables(w.lattice, p, fo, Qo)
+    assert abs(og["radius"] - float(oo["radius"])) < 1e-6
+    assert abs(og["mass"] - float(oo["mass"])) < 1e-9 * float(oo["mass"])
