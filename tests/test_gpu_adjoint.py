@@ -172,7 +172,7 @@ def test_torch_autograd_function(orc_cs):
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("shape", [(1, 40, 36), (1, 128, 128)])
+@pytest.mark.parametrize("shape", [(1, 40, 36), (1, 128, 128), (1, 3, 7)])
 def test_tiled_reverse_equals_cell_reverse(monkeypatch, precision, shape):
     """On single-plane lattices the reverse sweep runs as owned tiles with
     recomputed halos (one grid barrier per reverse step); it forms every
@@ -180,7 +180,8 @@ def test_tiled_reverse_equals_cell_reverse(monkeypatch, precision, shape):
     segment kernel (NLC_ADJ_TILED=0), so dL/dQ0 and the parameter adjoints
     agree to rounding (the compiler may fuse multiply-adds differently in
     the two kernels, and the parameter adjoints are summed in another
-    grouping).  40 x 36 leaves partial tiles on both axes."""
+    grouping).  40 x 36 leaves partial tiles on both axes; on 7 x 3 one
+    tile's box wraps around the lattice several times."""
     w = droplet(wl.D2Q9, shape, "paper")
     g_tiled, _ = gpu_adjoint(w, 30, 8, precision)
     monkeypatch.setenv("NLC_ADJ_TILED", "0")
