@@ -77,3 +77,55 @@ def test_disc_256_fp32_20000_steps_against_oracle(orc, delta):
     assert dR < 1e-3
     assert dQ < 1e-3
     assert du < 1e-2
+
+
+def test_sweep_members_fp32_50000_steps_against_oracle(orc):
+    """Two members of the 64-lattice temperature sweep (the smallest lattice
+    and the one nearest coexistence), advanced inside the full batched
+    context for the sweep's 50000 steps in FP32 (graph replay), against the
+    oracle run of the same lattice: max |dQ| (normwise) and the drift of the
+    interface position (Sec. 2.1) every 5000 steps."""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    ws = wl.sweep_64()
+    steps, every = 50000, 5000
+    gam = np.array([w.params["gamma"] for w in ws])
+    picks = sorted({int(np.argmin([w.n_cells for w in ws])), int(np.argmin(np.abs(gam - 2.7)))})
+    b = nlc.Batch(wl.D2Q9, [w.shape for w in ws], [w.params for w in ws],
+                  precision=nlc.NLC_FP32,
+                  stream=torch.cuda.current_stream().cuda_stream, graph_steps=50)
+    for i, w in enumerate(ws):
+        b.set_fields(i, w.initial_q5())
+    state = {}
+    for i in picks:
+        w = ws[i]
+        state[i] = (orc.init_equilibrium(w.lattice, w.shape), w.initial_q5())
+    rows = {i: [] for i in picks}
+    done = 0
+    while done < steps:
+        b.step(every)
+        done += every
+        for i in picks:
+            w = ws[i]
+            p = wl.param_vector(w.params)
+            f, Q = orc.step(w.lattice, p, state[i][0], state[i][1], every)
+            state[i] = (f, Q)
+            og = b.observables(i)
+            oo = orc.observables(w.lattice, p, f, Q)
+            Qg, _, _ = b.get_fields(i)
+            rows[i].append({"step": done,
+                            "max_dQ_rel": float(np.abs(Qg - Q).max() / np.abs(Q).max()),
+                            "x_gpu": og["x_iface"], "x_oracle": float(oo["x_iface"])})
+    b.close()
+    out = os.environ.get("NLC_LONG_OUT")
+    for i in picks:
+        dx = max(abs(r["x_gpu"] - r["x_oracle"]) for r in rows[i])
+        dQ = max(r["max_dQ_rel"] for r in rows[i])
+        if out:
+            with open(out, "a") as fh:
+                fh.write(json.dumps({"case": ws[i].name, "gamma": ws[i].params["gamma"],
+                                     "steps": steps, "precision": "fp32",
+                                     "reference": "FP64 CPU oracle", "max_dQ_rel": dQ,
+                                     "x_iface_drift_max": dx, "trace": rows[i]}) + "\n")
+        assert dx < 1e-2, (ws[i].name, dx)
+        assert dQ < 1e-3, (ws[i].name, dQ)
