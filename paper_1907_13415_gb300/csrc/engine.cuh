@@ -1269,6 +1269,13 @@ class Engine final : public EngineBase {
   // captures len fused steps starting from buffer parity c
   nlc_status capture_steps(int c, int len, cudaGraphExec_t* out) {
     if (!cap_stream_) NLC_CK(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
+    // the persistent kernel's occupancy query and barrier allocation happen
+    // before the capture (no allocation may happen inside one)
+    if (persistent_steps > 0 && !any_mrt_) {
+      int grid;
+      nlc_status ps = persist_grid(&grid);
+      if (ps) return ps;
+    }
     const int saved = cur_;
     cur_ = c;
     NLC_CK(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));

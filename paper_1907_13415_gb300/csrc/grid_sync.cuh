@@ -38,7 +38,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen, unsigne
     if (ld_acquire_gpu(&b->arrived) < target) {
       const uint64_t t0 = global_ns();
       while (ld_acquire_gpu(&b->arrived) < target) {
-        if (global_ns() - t0 > wait_ns) {
+        if (global_ns() - t0 >= wait_ns) {  // wait_ns = 0: give up at once
           ok = 0;
           atomicExch(err, DEV_ERR_GRID_TIMEOUT);
           break;

@@ -192,3 +192,21 @@ def test_tiled_reverse_equals_cell_reverse(monkeypatch, precision, shape):
     assert g_tiled["loss"] == g_cell["loss"]
     for k in ("dgamma", "dK", "dGamma"):
         assert g_tiled[k] == pytest.approx(g_cell[k], rel=tol), k
+
+
+def test_adjoint_with_persistent_forward_sweep():
+    """With the persistent form of the step switched on, the adjoint's forward
+    sweep (graphs of the checkpoint segments) runs the cooperative kernel;
+    the gradients equal those of the two-kernel form to rounding."""
+    from paper_1907_13415_gb300 import nlc
+    w = droplet(wl.D2Q9, (1, 24, 32))
+    out = []
+    for k in (0, 7):
+        s = nlc.Simulation(w.lattice, w.shape, w.params, precision=0, stream=stream())
+        s.set_persistent(k)
+        s.set_fields(w.initial_q5())
+        out.append(s.adjoint(*LOSS, nsteps=30, ckpt_every=10))
+        s.close()
+    for key in ("loss", "dgamma", "dK", "dGamma"):
+        assert out[1][key] == pytest.approx(out[0][key], rel=1e-12), key
+    assert np.abs(out[1]["dQ0"] - out[0]["dQ0"]).max() <= 1e-12 * np.abs(out[0]["dQ0"]).max()
