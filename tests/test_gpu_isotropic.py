@@ -22,11 +22,13 @@ def stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def droplet(lattice, shape):
+def droplet(lattice, shape, pset="tau1"):
+    from helpers import PARAM_SETS
     base = wl.flat_128x8() if lattice == wl.D2Q9 else wl.sphere_256()
     return base.with_(lattice=lattice, shape=shape, geometry="ball",
                       size=0.3 * min(s for s in shape if s > 1), noise=1e-3, seed=23,
-                      director=(0.6, 0.8, 0.0))
+                      director=(0.6, 0.8, 0.0),
+                      params=dict(PARAM_SETS[pset], gamma=base.params["gamma"]))
 
 
 def run_gpu(w, steps, precision, schedule, rates=None):
@@ -60,11 +62,12 @@ def run_oracle(orc, w, steps, rates=None):
     return f, Q, u
 
 
+@pytest.mark.parametrize("pset", ["tau1", "paper"])
 @pytest.mark.parametrize("schedule", [0, 1], ids=["fused", "unfused"])
 @pytest.mark.parametrize("lattice,shape", [(wl.D2Q9, (1, 19, 43)), (wl.D2Q9, (1, 3, 5)),
                                            (wl.D3Q19, (9, 10, 37)), (wl.D3Q19, (3, 3, 3))])
-def test_isotropic_fp64_matches_oracle(orc, lattice, shape, schedule):
-    w = droplet(lattice, shape)
+def test_isotropic_fp64_matches_oracle(orc, lattice, shape, schedule, pset):
+    w = droplet(lattice, shape, pset)
     f, Q, u, _ = run_gpu(w, 40, 0, schedule)
     fo, Qo, uo = run_oracle(orc, w, 40)
     perm = perm_to_oracle(orc, lattice)

@@ -6,7 +6,7 @@ adjoint refuses it."""
 import numpy as np
 import pytest
 
-from helpers import fp32_tolerance, perm_to_oracle, rel
+from helpers import PARAM_SETS, fp32_tolerance, perm_to_oracle, rel
 from paper_1907_13415_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -25,11 +25,12 @@ def stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def droplet(lattice, shape):
+def droplet(lattice, shape, pset="tau1"):
     base = wl.flat_128x8() if lattice == wl.D2Q9 else wl.sphere_256()
     return base.with_(lattice=lattice, shape=shape, geometry="ball",
                       size=0.3 * min(s for s in shape if s > 1), noise=1e-3, seed=29,
-                      director=(0.6, 0.8, 0.0))
+                      director=(0.6, 0.8, 0.0),
+                      params=dict(PARAM_SETS[pset], gamma=base.params["gamma"]))
 
 
 def run(w, steps, precision, schedule=0):
@@ -44,11 +45,12 @@ def run(w, steps, precision, schedule=0):
     return f, Q
 
 
+@pytest.mark.parametrize("pset", ["tau1", "paper"])
 @pytest.mark.parametrize("schedule", [0, 1], ids=["fused", "unfused"])
 @pytest.mark.parametrize("lattice,shape", [(wl.D2Q9, (1, 24, 64)), (wl.D3Q19, (8, 12, 40))])
-def test_mixed_precision_against_oracle(orc, lattice, shape, schedule):
+def test_mixed_precision_against_oracle(orc, lattice, shape, schedule, pset):
     from paper_1907_13415_gb300 import nlc
-    w = droplet(lattice, shape)
+    w = droplet(lattice, shape, pset)
     steps = 60
     f0 = orc.init_equilibrium(lattice, shape)
     fo, Qo = orc.step(lattice, wl.param_vector(w.params), f0, w.initial_q5(), steps)
