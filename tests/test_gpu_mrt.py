@@ -4,7 +4,7 @@ bad rates are rejected."""
 import numpy as np
 import pytest
 
-from helpers import perm_to_oracle, rel
+from helpers import PARAM_SETS, perm_to_oracle, rel
 from paper_1907_13415_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -28,11 +28,12 @@ def rates_for(lattice, seed):
     return np.random.default_rng(seed).uniform(0.7, 1.8, size=q)
 
 
-def droplet(lattice, shape):
+def droplet(lattice, shape, pset="tau1"):
     base = wl.flat_128x8() if lattice == wl.D2Q9 else wl.sphere_256()
     return base.with_(lattice=lattice, shape=shape, geometry="ball",
                       size=0.3 * min(s for s in shape if s > 1), noise=1e-3, seed=21,
-                      director=(0.6, 0.8, 0.0))
+                      director=(0.6, 0.8, 0.0),
+                      params=dict(PARAM_SETS[pset], gamma=base.params["gamma"]))
 
 
 def run_gpu(w, steps, precision, schedule, rates):
@@ -49,11 +50,12 @@ def run_gpu(w, steps, precision, schedule, rates):
     return f, Q
 
 
+@pytest.mark.parametrize("pset", ["tau1", "paper"])
 @pytest.mark.parametrize("schedule", [0, 1], ids=["fused", "unfused"])
 @pytest.mark.parametrize("lattice,shape", [(wl.D2Q9, (1, 19, 43)),
                                            (wl.D3Q19, (9, 10, 37))])
-def test_mrt_fp64_matches_oracle(orc, lattice, shape, schedule):
-    w = droplet(lattice, shape)
+def test_mrt_fp64_matches_oracle(orc, lattice, shape, schedule, pset):
+    w = droplet(lattice, shape, pset)
     r = rates_for(lattice, 3)
     steps = 40
     f, Q = run_gpu(w, steps, 0, schedule, r)
@@ -85,8 +87,11 @@ def test_mrt_fp32_within_bound(orc, lattice, shape):
     assert rel(Q, Qo) < fp32_tolerance(steps)
 
 
-def test_equal_rates_reproduce_bgk_and_reset():
-    w = droplet(wl.D3Q19, (6, 9, 33))
+@pytest.mark.parametrize("pset", ["tau1", "tau0.8", "paper"])
+def test_equal_rates_reproduce_bgk_and_reset(pset):
+    # at tau = 1 the rates 1/tau relax every moment fully; tau = 0.8 and the
+    # paper's 1.5 keep part of the incoming populations
+    w = droplet(wl.D3Q19, (6, 9, 33), pset)
     tau = w.params["tau"]
     f_b, Q_b = run_gpu(w, 25, 0, 0, None)
     f_m, Q_m = run_gpu(w, 25, 0, 0, np.full(19, 1.0 / tau))
