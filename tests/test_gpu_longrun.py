@@ -6,10 +6,13 @@ Sec. 2.2) compared every 2000 steps.
 
 The oracle needs minutes of host time per case (1.3 G lattice updates), so
 these run only with NLC_LONG=1; with NLC_LONG_OUT set, each case appends its
-figures as one JSON line to that file.
+figures as one JSON line to that file, with the host seconds the oracle took
+(OpenMP over all host cores) and the device seconds of the GPU run of the
+same steps.
 """
 import json
 import os
+import time
 
 import numpy as np
 import pytest
@@ -47,9 +50,17 @@ def test_disc_256_fp32_20000_steps_against_oracle(orc, delta):
     Q = Q0
     rows = []
     done = 0
+    t_gpu = t_orc = 0.0
     while done < steps:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         sim.step(EVERY)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         f, Q = orc.step(w.lattice, p, f, Q, EVERY)
+        t2 = time.perf_counter()
+        t_gpu += t1 - t0
+        t_orc += t2 - t1
         done += EVERY
         og = sim.observables()
         oo = orc.observables(w.lattice, p, f, Q)
@@ -67,6 +78,7 @@ def test_disc_256_fp32_20000_steps_against_oracle(orc, delta):
                "radius_drift_max": dR, "max_u_rel_diff_max": du,
                "radius_final_gpu": rows[-1]["radius_gpu"],
                "radius_final_oracle": rows[-1]["radius_oracle"],
+               "gpu_s": t_gpu, "oracle_s": t_orc, "oracle_threads": orc.set_threads(0),
                "trace": rows}
     out = os.environ.get("NLC_LONG_OUT")
     if out:
@@ -129,3 +141,39 @@ def test_sweep_members_fp32_50000_steps_against_oracle(orc):
                                      "x_iface_drift_max": dx, "trace": rows[i]}) + "\n")
         assert dx < 1e-2, (ws[i].name, dx)
         assert dQ < 1e-3, (ws[i].name, dQ)
+
+
+def test_flat_128x8_fp64_2000_steps_timed(orc):
+    """The 128 x 8 flat interface (FP64, 2000 steps) in full on both sides:
+    the state against the oracle's (the FP64 bound) and the time each side
+    takes for the whole run."""
+    import torch
+    from paper_1907_13415_gb300 import nlc
+    w = wl.flat_128x8()
+    p = wl.param_vector(w.params)
+    sim = nlc.Simulation(w.lattice, w.shape, w.params, precision=nlc.NLC_FP64,
+                         stream=torch.cuda.current_stream().cuda_stream)
+    sim.set_graph(50)
+    Q0 = w.initial_q5()
+    sim.set_fields(Q0)
+    sim.step(50)  # warm-up: graph capture, module load
+    sim.set_fields(Q0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.step(w.steps)
+    torch.cuda.synchronize()
+    t_gpu = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, Qo = orc.step(w.lattice, p, orc.init_equilibrium(w.lattice, w.shape), Q0, w.steps)
+    t_orc = time.perf_counter() - t0
+    Qg, _, _ = sim.get_fields()
+    sim.close()
+    dq = float(np.abs(Qg - Qo).max() / np.abs(Qo).max())
+    out = os.environ.get("NLC_LONG_OUT")
+    if out:
+        with open(out, "a") as fh:
+            fh.write(json.dumps({"case": w.name, "steps": w.steps, "precision": "fp64",
+                                 "reference": "FP64 CPU oracle", "max_dQ_rel": dq,
+                                 "gpu_s": t_gpu, "oracle_s": t_orc,
+                                 "oracle_threads": orc.set_threads(0)}) + "\n")
+    assert dq < 1e-12
