@@ -695,12 +695,18 @@ __device__ __forceinline__ bool fused_lb_tile(const TileRef tile,
   return true;
 }
 
+// pdl_early: the launch fits in one wave of resident blocks, so the next
+// kernel of the stream (launched with programmatic serialisation) may be
+// scheduled at once and wait for this one on the device; otherwise its
+// blocks would hold SM slots that this kernel's later waves need.
 template <class Lat, class T, class G, bool MRT, bool ISO, bool IX32, bool OBS = false>
 __global__ void __launch_bounds__(LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::MINB)
     k_fused_lb(const InstDev<T, G>* __restrict__ insts,
                const CUtensorMap* __restrict__ qmaps,
                const TileRef* __restrict__ tiles, int cur,
-               unsigned* __restrict__ err, double* __restrict__ obs_partial) {
+               unsigned* __restrict__ err, double* __restrict__ obs_partial, int pdl_early) {
+  grid_dep_wait();
+  if (pdl_early) grid_dep_trigger();
   (void)fused_lb_tile<Lat, T, G, MRT, ISO, IX32, OBS>(tiles[blockIdx.x], insts, qmaps, cur, err,
                                                       obs_partial);
 }
@@ -1076,7 +1082,9 @@ __global__ void __launch_bounds__(BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::MINB)
                const CUtensorMap* __restrict__ qmaps,
                const CUtensorMap* __restrict__ umaps,
                const TileRef* __restrict__ tiles, int cur,
-               unsigned* __restrict__ err) {
+               unsigned* __restrict__ err, int pdl_early) {
+  grid_dep_wait();
+  if (pdl_early) grid_dep_trigger();
   (void)fused_be_tile<Lat, T, G, ISO>(tiles[blockIdx.x], insts, qmaps, umaps, cur, err);
 }
 
@@ -1191,18 +1199,67 @@ inline cudaError_t set_smem(K kernel, size_t bytes, unsigned long long* done_mas
   return e;
 }
 
+// Blocks of `kernel` resident on the whole device at once (SMs times blocks
+// per SM), found once per kernel and device; 0 if the query fails.
+struct ResidentCache {
+  int v[64];
+  ResidentCache() {
+    for (int& x : v) x = -1;
+  }
+};
+template <class K>
+inline int resident_blocks(K kernel, int threads, size_t smem, ResidentCache& c) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 0;
+  int* cache = c.v;
+  if (cache[dev] < 0) {
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cache[dev] = sms * per_sm;
+  }
+  return cache[dev];
+}
+
+// A step kernel launched with programmatic stream serialisation (see
+// grid_dep_wait): it may be scheduled while the previous kernel of the
+// stream finishes, and waits for it on the device before its first global
+// access.  Inside a stream capture the dependency becomes a programmatic
+// edge of the graph.
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int threads, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <class Lat, class T, class G, bool MRT, bool ISO, bool IX32>
 cudaError_t launch_fused_lb_as(const InstDev<T, G>* insts, const CUtensorMap* qmaps,
                                const TileRef* tiles, int ntiles, int cur, unsigned* err,
                                cudaStream_t st) {
   static unsigned long long configured = 0;
-  cudaError_t e =
-      set_smem(k_fused_lb<Lat, T, G, MRT, ISO, IX32>, LbCfg<Lat, T>::bytes, &configured);
+  static ResidentCache resident;
+  auto kernel = k_fused_lb<Lat, T, G, MRT, ISO, IX32>;
+  constexpr int threads = LbCfg<Lat, T>::THREADS;
+  constexpr size_t smem = LbCfg<Lat, T>::bytes;
+  cudaError_t e = set_smem(kernel, smem, &configured);
   if (e != cudaSuccess) return e;
-  k_fused_lb<Lat, T, G, MRT, ISO, IX32>
-      <<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(insts, qmaps, tiles, cur,
-                                                                      err, nullptr);
-  return cudaGetLastError();
+  const int early = ntiles <= resident_blocks(kernel, threads, smem, resident) ? 1 : 0;
+  return launch_pdl(kernel, ntiles, threads, smem, st, insts, qmaps, tiles, cur, err,
+                    (double*)nullptr, early);
 }
 
 // the observables of the current state (buffers cur) over the tiles given
@@ -1218,7 +1275,7 @@ cudaError_t launch_fused_obs(const InstDev<T, G>* insts, const CUtensorMap* qmap
   if (e != cudaSuccess) return e;
   k_fused_lb<Lat, T, G, false, false, true, true>
       <<<ntiles, LbCfg<Lat, T>::THREADS, LbCfg<Lat, T>::bytes, st>>>(insts, qmaps, tiles, cur,
-                                                                      err, partial);
+                                                                      err, partial, 0);
   return cudaGetLastError();
 }
 
@@ -1248,11 +1305,15 @@ cudaError_t launch_fused_be_as(const InstDev<T, G>* insts, const CUtensorMap* qm
                                const CUtensorMap* umaps, const TileRef* tiles, int ntiles,
                                int cur, unsigned* err, cudaStream_t st) {
   static unsigned long long configured = 0;
-  cudaError_t e = set_smem(k_fused_be<Lat, T, G, ISO>, BeCfg<Lat, T>::bytes, &configured);
+  static ResidentCache resident;
+  auto kernel = k_fused_be<Lat, T, G, ISO>;
+  constexpr int threads = BeCfg<Lat, T>::THREADS;
+  constexpr size_t smem = BeCfg<Lat, T>::bytes;
+  cudaError_t e = set_smem(kernel, smem, &configured);
   if (e != cudaSuccess) return e;
-  k_fused_be<Lat, T, G, ISO><<<ntiles, BeCfg<Lat, T>::THREADS, BeCfg<Lat, T>::bytes, st>>>(
-      insts, qmaps, umaps, tiles, cur, err);
-  return cudaGetLastError();
+  const int early = ntiles <= resident_blocks(kernel, threads, smem, resident) ? 1 : 0;
+  return launch_pdl(kernel, ntiles, threads, smem, st, insts, qmaps, umaps, tiles, cur, err,
+                    early);
 }
 
 template <class Lat, class T, class G>

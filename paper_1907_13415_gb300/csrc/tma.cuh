@@ -75,6 +75,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// the programmatic stream serialisation attribute may be scheduled while the
+// kernel before it in the stream is still running.  grid_dep_wait() returns
+// once that kernel has completed and its memory operations are visible to
+// this grid (at once for a kernel launched without the attribute), so every
+// thread calls it before its first global access; grid_dep_trigger() allows
+// the next such kernel to be scheduled as soon as every block of this grid
+// has called it or exited (the implicit point without it).
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // 4D tiled TMA load of one box into shared memory, completing on bar
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map,
                                             int c0, int c1, int c2, int c3,
