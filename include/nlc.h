@@ -328,7 +328,11 @@ NLC_API nlc_status nlc_get_fields(nlc_ctx* ctx, int32_t inst, double* Q5,
 NLC_API nlc_status nlc_get_populations(nlc_ctx* ctx, int32_t inst, double* f);
 
 /* Advances every lattice of the context by n time steps (n >= 0).  Queued
- * on the context's stream; returns launch errors only. */
+ * on the context's stream; returns launch errors only.  The two kernels of
+ * a step are launched with programmatic dependent launch: each may be
+ * scheduled while the kernel before it in the stream (the caller's own,
+ * too) is finishing, and waits on the device for that kernel to complete
+ * before it touches memory, so stream order holds for every buffer. */
 NLC_API nlc_status nlc_step(nlc_ctx* ctx, int64_t n);
 
 /* Computes the observables of the current state of instance inst into *out
