@@ -14,6 +14,7 @@ With N > 1 (launched by torchrun) every rank advances its own lattice
 Prints one JSON line on rank 0.
 """
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -105,18 +106,24 @@ def hbm_peak():
 # -- clocks -----------------------------------------------------------------
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    """nvidia-smi sampling of SM clocks and throttle reasons while running.
+    Each sample carries nvidia-smi's timestamp; `region()` marks the timed
+    region on the same (local) wall clock, and the summary takes the
+    samples inside it (all samples if the region is shorter than the
+    sampling interval, flagged in `window`)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,"
               "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -125,7 +132,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev),
                  f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"),
+                 "-lms", str(self.INTERVAL_MS)], stdout=open(self.path, "w"),
                 stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -140,30 +147,55 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
+    def start(self):
+        self.t0 = datetime.datetime.now()
+
+    def stop(self):
+        self.t1 = datetime.datetime.now()
+
     def summary(self):
         if self.proc is None or not self.path:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
-                 "sw_power_cap"]
         with open(self.path) as fh:
-            for line in fh:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for name, val in zip(names, parts[5:9]):
-                    if val.lower().startswith("active"):
-                        reasons.add(name)
+            lines = fh.readlines()
         os.unlink(self.path)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return summarize_clock_samples(lines, self.t0, self.t1)
+
+
+CLOCK_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+
+
+def summarize_clock_samples(lines, t0=None, t1=None):
+    """Median SM clock, maximum clock and the throttle reasons seen, from
+    nvidia-smi lines of ClockSampler.FIELDS; the samples stamped within
+    [t0, t1] when there are any, else every sample (window "run")."""
+    samples = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+        except ValueError:
+            ts = None
+        try:
+            sm, smax = float(parts[2]), float(parts[3])
+        except ValueError:
+            continue
+        active = {n for n, v in zip(CLOCK_REASONS, parts[6:10])
+                  if v.lower().startswith("active")}
+        samples.append((ts, sm, smax, active))
+    inside = [x for x in samples
+              if t0 is not None and t1 is not None and x[0] is not None and t0 <= x[0] <= t1]
+    use, window = (inside, "timed region") if inside else (samples, "run")
+    if not use:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    reasons = set().union(*(x[3] for x in use))
+    return {"sm_mhz": statistics.median(x[1] for x in use),
+            "sm_max_mhz": max(x[2] for x in use), "reasons": sorted(reasons),
+            "samples": len(use), "window": window,
+            "interval_ms": ClockSampler.INTERVAL_MS}
 
 
 # -- distributed helpers -------------------------------------------------------
@@ -426,6 +458,7 @@ def run_ours(args, w):
         torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
+        clk.start()
         ev0.record(stream)
         if args.persist > 0:
             # the persistent form: cooperative launches of args.persist steps
@@ -435,6 +468,7 @@ def run_ours(args, w):
                 sim.step(1)
         ev1.record(stream)
         torch.cuda.synchronize()
+        clk.stop()
         barrier(ws)
     elapsed_ms = ev0.elapsed_time(ev1)
     kt = nlc.nlc_get_timing(sim.ctx)
@@ -798,7 +832,7 @@ def run_adjoint(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=10)
